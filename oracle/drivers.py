@@ -1,0 +1,108 @@
+"""Drivers: fixed-Sigma Dyson solve and self-consistent second-Born (oracle).
+
+* solve_fixed_sigma: dyson_mat, dyson_start, then dyson_timestep for n = k+1..N
+  (Sec. "Test of accuracy and scaling analysis", generic three-step procedure).
+* run_2b: the self-consistent second-Born loop of Sec. "Hubbard chain", generalised to a
+  batch of problems (k-points) coupled only through the local Green's function
+  G_loc = (1/N_k) sum_k G_k (Sec. "GW for the translationally invariant Hubbard model"):
+    1. Matsubara loop: {G_loc, eps^MF, Sigma_2B(-1), dyson_mat} until the distance of
+       successive G^M (summed over k) is below mats_tol, at most mats_maxiter times;
+    2. bootstrapping: {G_loc, eps^MF, Sigma_2B(0..k), dyson_start} until the summed distance
+       of slices 0..k is below boot_tol and more than two iterations were made;
+    3. time stepping n = k+1..N: extrapolate_timestep(n-1), then exactly ``corrector``
+       iterations of {G_loc(n), eps^MF_n, Sigma_2B(n), dyson_timestep(n)}.
+  A problem with N_k = 1 and d = 2 is the Hubbard dimer in real space.
+  The second-Born dynamics has no closed form: its parity with the CUDA path is pinned
+  only by invariants and by the pinned building blocks (parity partially unpinned).
+"""
+import numpy as np
+
+from . import bubble, dyson, extrap
+from .contour import Func, Herm
+
+
+def solve_fixed_sigma(G, S, eps, mu, beta, h, W, schedule="mixed", nmax=None):
+    dyson.dyson_mat(G, S, eps, mu, beta, W)
+    dyson.dyson_start(G, S, eps, mu, beta, h, W)
+    for n in range(W.k + 1, (G.nt if nmax is None else nmax) + 1):
+        dyson.dyson_timestep(n, G, S, eps, mu, beta, h, W, schedule)
+    return G
+
+
+class TwoBState:
+    def __init__(self, nk, nt, ntau, d):
+        self.G = [Herm(nt, ntau, d) for _ in range(nk)]
+        self.Gloc = Herm(nt, ntau, d)
+        self.S = Herm(nt, ntau, d)
+        self.epsmf = [Func(nt, d) for _ in range(nk)]
+        self.log = {}
+
+
+def _update_mf(n, st, eps0, U, nbar):
+    rho = bubble.density_matrix(n, st.Gloc)
+    for kk, e0 in enumerate(eps0):
+        st.epsmf[kk].set(n, bubble.hartree(n, rho, e0(n), U, nbar))
+
+
+def run_2b(eps0, U, nt, ntau, beta, h, W, mu=0.0, nbar=0.5, corrector=3, schedule="mixed",
+           mats_tol=1e-13, mats_maxiter=200, boot_tol=1e-13, boot_maxiter=200, nmax=None,
+           state=None):
+    """Self-consistent second-Born for the problems with bare Hamiltonians eps0[k] (Funcs)."""
+    nk = len(eps0)
+    d = eps0[0].d
+    st = state or TwoBState(nk, nt, ntau, d)
+    # ---- Matsubara -------------------------------------------------------------------
+    for kk in range(nk):  # initial guess: free G^M of the bare Hamiltonian
+        st.epsmf[kk].set(-1, eps0[kk](-1))
+        dyson.dyson_mat(st.G[kk], st.S, st.epsmf[kk], mu, beta, W)
+    it_m = 0
+    for it_m in range(mats_maxiter):
+        bubble.kreduce(-1, st.G, st.Gloc)
+        _update_mf(-1, st, eps0, U, nbar)
+        bubble.sigma_2b(-1, st.Gloc, U, st.S)
+        err = 0.0
+        for kk in range(nk):
+            old = st.G[kk].mat.copy()
+            dyson.dyson_mat(st.G[kk], st.S, st.epsmf[kk], mu, beta, W)
+            err += float(np.abs(st.G[kk].mat - old).sum())
+        if err < mats_tol:
+            break
+    st.log["mats_iter"] = it_m + 1
+    st.log["mats_err"] = err
+    bubble.kreduce(-1, st.G, st.Gloc)
+    _update_mf(-1, st, eps0, U, nbar)
+    bubble.sigma_2b(-1, st.Gloc, U, st.S)
+    # ---- bootstrapping ---------------------------------------------------------------
+    k = W.k
+    for n in range(k + 1):  # initial guess for slices 0..k: the equilibrium Matsubara state
+        for kk in range(nk):
+            st.epsmf[kk].set(n, st.epsmf[kk](-1) - eps0[kk](-1) + eps0[kk](n))
+    for kk in range(nk):
+        dyson.dyson_start(st.G[kk], st.S, st.epsmf[kk], mu, beta, h, W)
+    it_b = 0
+    for it_b in range(boot_maxiter):
+        for n in range(k + 1):
+            bubble.kreduce(n, st.G, st.Gloc)
+            _update_mf(n, st, eps0, U, nbar)
+            bubble.sigma_2b(n, st.Gloc, U, st.S)
+        err = 0.0
+        for kk in range(nk):
+            old = st.G[kk].copy()
+            dyson.dyson_start(st.G[kk], st.S, st.epsmf[kk], mu, beta, h, W)
+            err += sum(extrap.distance_norm2(n, st.G[kk], old) for n in range(k + 1))
+        if err < boot_tol and it_b > 2:
+            break
+    st.log["boot_iter"] = it_b + 1
+    st.log["boot_err"] = err
+    # ---- time stepping ---------------------------------------------------------------
+    for n in range(k + 1, (nt if nmax is None else nmax) + 1):
+        for kk in range(nk):
+            extrap.extrapolate_timestep(n - 1, st.G[kk], W)
+        for _ in range(corrector):
+            bubble.kreduce(n, st.G, st.Gloc)
+            _update_mf(n, st, eps0, U, nbar)
+            bubble.sigma_2b(n, st.Gloc, U, st.S)
+            for kk in range(nk):
+                dyson.dyson_timestep(n, st.G[kk], st.S, st.epsmf[kk], mu, beta, h, W, schedule)
+    bubble.kreduce(-1, st.G, st.Gloc)
+    return st
