@@ -1,0 +1,325 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 contour Dyson time-stepper.
+
+Workload (default): the chain_kspace model -- 1D Hubbard chain in momentum space, nk = 512
+k-points, eps_k(t) = -2 cos(k - A(t)) with a Peierls pulse, local second-Born self-energy
+(U = 2) from the k-summed G_loc; beta = 10, ntau = 800, nt = 2000, h = 0.01, order k = 5,
+3 corrector iterations per time step, FP64 complex arithmetic.
+
+Metric: k-point timesteps per second.  A "step" is one time step n of the whole hot path
+for all k-points: predictor (extrapolation of slice n), then 3 corrector passes of
+{k-reduction of slice n, Hartree mean field, second-Born slice, Dyson time step}.
+The Matsubara loop, the bootstrapping and the steps before the timed window run untimed;
+the timed window is the LAST K steps of the nt = 2000 propagation (default: every step after
+the W warm-up steps), so a short window measures the most expensive steps.
+
+Lines printed: one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on the
+host cores for the same metric (a bounded sample of k-point steps of the same workload).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# FP64 (DFMA) throughput of one GB300 measured with a dependent-chain-free DFMA loop over all
+# SMs (profiles/fp64_peak_gb300.md): 1.195 TFLOP/s; nominal 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz.
+FP64_PEAK_TFLOPS = 1.195
+FP64_PEAK_NOTE = "measured DFMA loop, all 152 SMs (profiles/fp64_peak_gb300.md)"
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=0, help="timed time steps (0: all after warm-up)")
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    # development overrides (a run with any of these is not the headline workload)
+    ap.add_argument("--nk", type=int, default=512)
+    ap.add_argument("--nt", type=int, default=2000)
+    ap.add_argument("--ntau", type=int, default=800)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(a):
+    from paper_1911_01211_gb300 import workloads as wl
+    return wl.chain_kspace(nk=a.nk, nt=a.nt, ntau=a.ntau)
+
+
+def config_of(w, K, W):
+    return {
+        "workload": f"chain_kspace nk={w.nbatch} nt={w.nt} ntau={w.ntau} h={w.h} beta={w.beta} U={w.U[1]:g} "
+                    f"k={w.korder} corrector={w.corrector} (1D Hubbard chain, local second-Born, Peierls pulse)",
+        "global_batch": w.nbatch, "nt": w.nt, "ntau": w.ntau, "nf": w.nf,
+        "timed_steps": f"last {K} of {w.nt - w.korder} time steps (n = {w.nt - K + 1}..{w.nt}), {W} warm-up",
+        "l2": "inputs larger than L2 (per-k history of tens of GB re-read every step)",
+        "parallelism": "single GPU, all k-points in one batch",
+    }
+
+
+# ------------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ------------------------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if not self.p:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        out, _ = self.p.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------------------------------
+# the oracle's k-point time step, used by the cpu_baseline and the reference arm
+# ------------------------------------------------------------------------------------------
+_ORACLE = {}
+
+
+def _oracle_init(nt, ntau, korder, seed):
+    """Worker set-up: a seeded synthetic history of the workload's shape (values do not
+    change the oracle's operation count)."""
+    import numpy as np
+    from oracle.contour import Func, Herm
+    from oracle.weights import Weights
+    rng = np.random.default_rng(seed)
+    G, S = Herm(nt, ntau, 1), Herm(nt, ntau, 1)
+    for X, sc in ((G, 0.3), (S, 0.05)):
+        for c in ("mat", "ret", "les", "tv"):
+            a = getattr(X, c)
+            a[...] = sc * (rng.standard_normal(a.shape) + 1j * rng.standard_normal(a.shape))
+    eps = Func(nt, 1)
+    eps.val[:] = -2.0 * np.cos(0.3)
+    _ORACLE.update(G=G, S=S, eps=eps, W=Weights(korder))
+
+
+def _oracle_kstep(args):
+    """One k-point time step of the oracle at step n: `corrector` solves of slice n."""
+    n, beta, h, corrector = args
+    from oracle import dyson
+    o = _ORACLE
+    t = time.perf_counter()
+    for _ in range(corrector):
+        dyson.dyson_timestep(n, o["G"], o["S"], o["eps"], 0.0, beta, h, o["W"])
+    return time.perf_counter() - t
+
+
+def oracle_rate(w, ns, workers):
+    """Aggregate k-point steps/s of `workers` oracle processes (spawn) over the steps ns:
+    workers x jobs / summed per-job compute time (history synthesis excluded)."""
+    import multiprocessing as mp
+    nmax = max(ns)
+    jobs = [(n, w.beta, w.h, w.corrector) for n in ns]
+    ctx = mp.get_context("spawn")
+    t = time.perf_counter()
+    with ctx.Pool(workers, initializer=_oracle_init, initargs=(nmax, w.ntau, w.korder, 7)) as pool:
+        times = pool.map(_oracle_kstep, jobs, chunksize=1)
+    wall = time.perf_counter() - t
+    return workers * len(jobs) / sum(times), wall, sum(times)
+
+
+def cpu_baseline(w, ns_window):
+    """Bounded sample (~10-30 s of CPU work): k-point steps at the window's mean-cost step."""
+    import numpy as np
+    T = w.ntau
+    cost = lambda n: 2 * n * n + 2 * n * T + T * T
+    mean_cost = float(np.mean([cost(n) for n in ns_window]))
+    n_ref = min(ns_window, key=lambda n: abs(cost(n) - mean_cost))
+    workers = max(1, min(16, os.cpu_count() or 1))
+    rate, wall, cpu = oracle_rate(w, [n_ref] * (3 * workers), workers)
+    return {"value": rate, "unit": "k-point timesteps/s", "cores": workers, "kind": "oracle",
+            "sample": f"{3 * workers} k-point time steps of the workload at n={n_ref} (the step whose cost equals "
+                      f"the timed window's mean), {w.corrector} corrector solves each, seeded synthetic history, "
+                      f"{workers} oracle processes; {cpu:.1f} s of CPU, wall {wall:.1f} s"}
+
+
+# ------------------------------------------------------------------------------------------
+def run_reference(a):
+    w = workload(a)
+    K = a.steps if a.steps > 0 else w.nt - w.korder - a.warmup
+    W = a.warmup
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    ns = list(range(w.nt - K + 1, w.nt + 1))
+    ns_warm = list(range(w.nt - K - W + 1, w.nt - K + 1))
+    workers = max(1, min(16, os.cpu_count() or 1))
+    if ns_warm:
+        oracle_rate(w, ns_warm, workers)
+    rate, wall, cpu = oracle_rate(w, ns, workers)
+    line = {"metric": "k-point timesteps/s", "value": rate, "unit": "k-point timesteps/s", "impl": "reference",
+            "n_gpus": a.gpus, "steps": K, "warmup": W, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_of(w, K, W),
+            "cpu_baseline": {"value": rate, "unit": "k-point timesteps/s", "cores": workers, "kind": "oracle",
+                             "sample": f"one k-point time step per bench step for each of the timed steps "
+                                       f"n={ns[0]}..{ns[-1]} (3 corrector solves, synthetic history), "
+                                       f"{workers} processes"},
+            "e2e": {"value": rate, "unit": "k-point timesteps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "ms_per_step": 1000.0 * wall / len(ns)}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(a):
+    import numpy as np
+    import torch
+    import paper_1911_01211_gb300 as ng
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = world > 1
+    if dist:
+        import torch.distributed as td
+        td.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    w = workload(a)
+    k = w.korder
+    W = a.warmup
+    K = a.steps if a.steps > 0 else w.nt - k - W
+    if K + W > w.nt - k:
+        raise SystemExit(f"steps + warmup must be <= {w.nt - k}")
+    n_first_timed = w.nt - K + 1
+
+    g = ng.Grid(nt=w.nt, ntau=w.ntau, nf=w.nf, nbatch=w.nbatch, korder=k, h=w.h, beta=w.beta, mu=w.mu)
+    ctx = ng.Context(k, local)
+    G = ng.Herm(g, zero=False)
+    L, S = ng.Herm(g, ldk=1), ng.Herm(g, ldk=1)
+    e0, mf = ng.Func(g), ng.Func(g)
+    U = ng.Func(g, scalar=True)
+    # inputs in pinned host memory; slices of eps_k are copied to the device step by step
+    eps_host = torch.from_numpy(np.ascontiguousarray(w.eps0)).pin_memory()
+    U_host = torch.from_numpy(w.U.astype(np.complex128)).pin_memory()
+    rho_host = torch.zeros(w.nt + 1, dtype=torch.complex128).pin_memory()
+    stream = torch.cuda.current_stream()
+    dd = w.nf * w.nf
+    les_diag = [ng.tri(n) + n for n in range(w.nt + 1)]
+    h2d_bytes = eps_host[0].numel() * 16
+    d2h_bytes = 16
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    t_job0 = time.perf_counter()
+    # ---- setup inputs and the untimed Matsubara loop + bootstrapping --------------------
+    e0.val[:k + 2].copy_(eps_host[:k + 2], non_blocking=True)
+    U.val[:, 0, 0, 0].copy_(U_host, non_blocking=True)
+    ctx.run_2b(g, G, L, S, e0, mf, U, corrector=w.corrector, n_from=k + 1, n_to=k, do_setup=True)
+
+    def step(n):
+        e0.val[n + 1].copy_(eps_host[n + 1], non_blocking=True)            # this step's input
+        ctx.run_2b(g, G, L, S, e0, mf, U, corrector=w.corrector, n_from=n, n_to=n, do_setup=False)
+        rho_host[n].copy_(L.les[les_diag[n], 0, 0, 0], non_blocking=True)  # this step's result
+
+    for n in range(k + 1, n_first_timed - W):
+        step(n)
+    for n in range(n_first_timed - W, n_first_timed):
+        step(n)
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ctx.profile_enable(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for n in range(n_first_timed, w.nt + 1):
+        step(n)
+    ev1.record(stream)
+    barrier()
+    t_job1 = time.perf_counter()
+    ctx.profile_enable(False)
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    prof = ctx.profile_read()
+    st, flags = ctx.status_sync()
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * w.nbatch * K / (ms / 1e3)
+    e2e_value = world * w.nbatch * (w.nt - k) / (t_job1 - t_job0)
+    launches = int(prof["bulk_launches"] + prof["boundary_launches"]) + K * (1 + 3 * 3)
+    achieved = prof["bulk_flops"] / (prof["bulk_ms"] / 1e3) / 1e12
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            tr = json.load(f)
+        src = open(os.path.join(ROOT, "paper_1911_01211_gb300", "csrc", "ng_step.cuh"), "rb").read()
+        import hashlib
+        if tr.get("ng_step_sha1") == hashlib.sha1(src).hexdigest():
+            traffic = tr.get("bulk_bytes_per_launch_timed_window")
+    except (OSError, ValueError):
+        traffic = None
+    rho = rho_host[k + 1:].numpy()
+    if rank != 0:
+        return
+    line = {
+        "metric": "k-point timesteps/s", "value": value, "unit": "k-point timesteps/s",
+        "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": ms / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_of(w, K, W),
+        "e2e": {"value": e2e_value, "unit": "k-point timesteps/s", "h2d_bytes_per_step": h2d_bytes,
+                "d2h_bytes_per_step": d2h_bytes,
+                "scope": "whole job through the public API: setup (Matsubara loop, bootstrapping) and every "
+                         "time step, per-step H2D of eps_k(t_n) from pinned host memory and D2H of rho_loc(t_n)"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": "k_step_bulk<1>",
+                     "peak_source": FP64_PEAK_NOTE,
+                     "avg_launch_ms": prof["bulk_ms"] / max(1, prof["bulk_launches"]),
+                     "share_of_timed": prof["bulk_ms"] / ms},
+        "gpu_launches": launches, "clocks": clk,
+        "device_status": {"status": st, "flags": flags},
+        "observables": {"N_loc_first_timed": float(np.real(-1j * rho[n_first_timed - k - 1])),
+                        "N_loc_last": float(np.real(-1j * rho[-1]))},
+    }
+    if world == 1 and not a.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, list(range(n_first_timed, w.nt + 1)))
+    print(json.dumps(line), flush=True)
+    if dist:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)

@@ -1,0 +1,236 @@
+/*
+ * ng.h -- C ABI of the GB300 contour Dyson time-stepper (libng.so).
+ *
+ * The library solves the Dyson equation in integro-differential form on the L-shaped
+ * Kadanoff-Baym contour, i d/dt G - eps(t) G - Sigma * G = delta_C (paper Eq. dyson),
+ * for a batch of problems (k-points or independent embedded clusters) with the k-th order
+ * BDF/Gregory scheme of the paper (Sec. "Numerical details: Volterra integral equations",
+ * Sec. "Implementation: dyson"), and evaluates the second-Born self-energy that couples
+ * the batch through the local Green's function (Eq. sigma_hubb_2b).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - C linkage; every call returns ng_status and never throws, aborts or exits.
+ *  - Statistics: fermions only (grid.sig = -1).  Orders korder = 1..5.
+ *  - All contour data are caller-owned DEVICE buffers of complex128 stored as interleaved
+ *    (re, im) double pairs.  The library never frees caller memory.
+ *  - A contour function (struct ng_herm) holds the minimal component set of the paper's
+ *    herm_matrix (Eq. storage_herm) for nbatch problems, problem index innermost:
+ *        mat[m][a][b][kb]             m = 0..ntau                   C^M(m h_tau)
+ *        ret[tri(n)+j][a][b][kb]      0 <= j <= n <= nt             C^R(n h, j h)
+ *        les[tri(n)+j][a][b][kb]      0 <= j <= n <= nt             C^<(j h, n h)
+ *        tv [n*(ntau+1)+m][a][b][kb]  n = 0..nt, m = 0..ntau         C^tv(n h, m h_tau)
+ *    with tri(n) = n(n+1)/2, a, b = 0..nf-1 orbital indices and kb = 0..ldk-1.
+ *    ldk is nbatch for per-problem data, or 1 for data shared by the whole batch
+ *    (e.g. a local self-energy Sigma_loc).  Problem kb of a shared function is kb = 0.
+ *  - A single-time contour function (struct ng_func) stores f_n, n = -1..nt,
+ *    as val[n+1][a][b][kb] (f_{-1} = f(0^-), paper Sec. "Numerical representation").
+ *  - The real-time grid is t_n = n h, the imaginary-time grid tau_m = m beta/ntau.
+ *    The chemical potential mu enters as eps - mu.
+ *  - stream is a cudaStream_t passed as void*; NULL is the legacy default stream.
+ *    Every compute entry point is asynchronous and stream-ordered unless stated.
+ *  - Argument errors are detected on the host before any launch and return NG_EINVAL
+ *    (the text is available from ng_last_error).  Device-side conditions (non-finite
+ *    values, a singular per-step matrix) set bits in a device status word that
+ *    ng_status_sync reads back.
+ *  - Preconditions follow the paper's Table tab:dyson: a call at time step tstp reads
+ *    slices < tstp of G and slices <= tstp of Sigma and eps.
+ *  - Thread safety: one context per host thread.  A context may be used with several
+ *    streams, but calls that share its workspace (ng_dyson_mat, ng_dyson_start,
+ *    ng_distance) must not overlap on the device.
+ */
+#ifndef NG_H
+#define NG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NG_OK = 0,
+    NG_EINVAL = 1,        /* invalid argument (host-side check, nothing launched)        */
+    NG_ENOMEM = 2,        /* workspace allocation failed                                 */
+    NG_ECUDA = 3,         /* a CUDA runtime call failed                                  */
+    NG_ENOCONV = 4,       /* a self-consistency loop hit its iteration limit             */
+    NG_ETIMEOUT = 5,      /* reserved: a bounded device wait gave up                     */
+    NG_ENONFINITE = 6,    /* a non-finite value was produced (device status word)        */
+    NG_EUNSUPPORTED = 7   /* valid but not implemented here (e.g. nf > 2)                */
+} ng_status;
+
+/* device status word bits (ng_status_sync) */
+#define NG_FLAG_NONFINITE 1
+#define NG_FLAG_SINGULAR 2
+
+typedef struct ng_ctx ng_ctx;
+
+typedef struct {
+    int nt;        /* number of real-time steps N_t (slices 0..nt)                       */
+    int ntau;      /* number of imaginary-time intervals N_tau (points 0..ntau)            */
+    int nf;        /* orbital dimension d (1 or 2 in this build)                            */
+    int nbatch;    /* number of problems stored innermost                                   */
+    int korder;    /* solve order k, 1..5; requires nt >= 2k+2 and ntau >= 2k+2             */
+    int sig;       /* -1: fermions (only value accepted)                                    */
+    double h;      /* real-time step                                                        */
+    double beta;   /* inverse temperature                                                   */
+    double mu;     /* chemical potential                                                    */
+} ng_grid;
+
+typedef struct {
+    void *mat, *ret, *les, *tv;  /* device pointers, complex128, layout above          */
+    int ldk;                     /* nbatch (per problem) or 1 (shared by the batch)     */
+} ng_herm;
+
+typedef struct {
+    void *val;                   /* device pointer, complex128 [nt+2][nf][nf][ldk]      */
+    int ldk;                     /* nbatch or 1                                          */
+} ng_func;
+
+typedef enum { NG_FP64 = 0 } ng_precision;
+
+/* Parameters of the self-consistent second-Born driver (ng_run_2b). */
+typedef struct {
+    int corrector;       /* corrector iterations per time step (paper: CorrectorSteps)   */
+    double mats_tol;     /* Matsubara loop stops when the G^M distance is below this     */
+    int mats_maxiter;
+    double boot_tol;     /* bootstrapping stops when the distance of slices 0..k is below */
+    int boot_maxiter;    /* this and more than two iterations were made                   */
+    double nbar;         /* Hartree reference filling (1/2 at half filling)               */
+    int n_from;          /* first time step to propagate (k+1 for a full run)             */
+    int n_to;            /* last time step to propagate (<= nt)                            */
+    int do_setup;        /* 1: run the Matsubara loop and bootstrapping first              */
+} ng_run_params;
+
+/* ---- context ------------------------------------------------------------------------ */
+
+/* Create a context for solve order korder (1..5) on CUDA device `device`.  The context
+ * owns the integration weights (exact rationals rounded to FP64: Sec. "Basic integration
+ * and differentiation rules"), device workspaces and the device status word.
+ * *out receives the context; NG_EINVAL for a bad order, NG_ECUDA if the device fails. */
+ng_status ng_create(int korder, int device, ng_ctx **out);
+
+/* Release a context and its workspaces (synchronises the device first). NULL is a no-op. */
+void ng_destroy(ng_ctx *ctx);
+
+/* Text of the last error recorded on ctx (static storage owned by ctx; never NULL). */
+const char *ng_last_error(const ng_ctx *ctx);
+
+/* Synchronise `stream`, read and clear the device status word (NG_FLAG_* bits) into
+ * *device_flags.  Returns NG_ENONFINITE if NG_FLAG_NONFINITE was set, NG_OK otherwise. */
+ng_status ng_status_sync(ng_ctx *ctx, void *stream, int *device_flags);
+
+/* Host copy of the FP64 integration weights for the context's order k, for inspection:
+ * out[0..k] = BDF a_j (Eq. integrator_bd); out[6..6+k] = Gregory end weights omega_j
+ * (Eq. integrator_greg); out[12..12+k] = extrapolation C_l (Eq. polyextrap).
+ * `out` must hold 18 doubles. */
+ng_status ng_weights(const ng_ctx *ctx, double *out);
+
+/* ---- inputs ------------------------------------------------------------------------- */
+
+/* Free Green's function of a constant hermitian Hamiltonian for every problem, all
+ * components, times `scale` (Sec. "Implementation: Free Green's functions", Eq. G0_free,
+ * exact for constant eps).  eps_host: host array [nbatch][nf][nf] complex128 (interleaved).
+ * G must have ldk = nbatch.  Use scale = V^2 with nf = 1 for an embedding self-energy
+ * Sigma = V^2 g0 (Sec. "Test of accuracy and scaling analysis"). */
+ng_status ng_green_from_H_const(ng_ctx *ctx, const ng_grid *grid, ng_herm G,
+                                const double *eps_host, double scale, void *stream);
+
+/* ---- Dyson solver (Table tab:dyson) ------------------------------------------------- */
+
+/* Matsubara slice T[G]_{-1} for every problem: the exact root of the k-th order
+ * discretised integral equation G^M = g^M + [g^M * Sigma^M * G^M]^M
+ * (Sec. "Matsubara", Eq. Gmat_dyson_integ, convolutions Eqs. cm1/cm2), found by a dense
+ * LU solve per problem.  Reads Sigma.mat, eps at n = -1; writes G.mat.
+ * Workspace: 16 (ntau+1)^2 nf^2 nbatch bytes, allocated on first use. */
+ng_status ng_dyson_mat(ng_ctx *ctx, const ng_grid *grid, ng_herm G, ng_herm Sigma,
+                       ng_func eps, void *stream);
+
+/* Start-up slices T[G]_n, n = 0..k (Sec. "Start", Eq. vdiff_start): retarded column
+ * systems, left-mixing and lesser VIDE start-up.  Reads G.mat and Sigma, eps on
+ * slices -1..k; writes slices 0..k of G. */
+ng_status ng_dyson_start(ng_ctx *ctx, const ng_grid *grid, ng_herm G, ng_herm Sigma,
+                         ng_func eps, void *stream);
+
+/* Time step tstp > k (Sec. "Time stepping"), the paper's parallel (mixed) schedule:
+ * retarded row by single VIDE steps for columns m <= tstp-k-1 (implementation (B)) and the
+ * conjugate start-up for m = tstp-k..tstp (implementation (A)); left-mixing row by one VIDE
+ * step per tau_m; lesser column by conjugate single steps for 1 <= m <= tstp-k-1 (B) and
+ * serial VIDE steps (A) for m >= tstp-k (the whole column by (A) when tstp <= 2k).
+ * Reads slices < tstp of G, slices <= tstp of Sigma and eps; writes slice tstp of G.
+ * precision must be NG_FP64. */
+ng_status ng_dyson_timestep(ng_ctx *ctx, const ng_grid *grid, int tstp, ng_herm G,
+                            ng_herm Sigma, ng_func eps, int precision, void *stream);
+
+/* ---- slice operations ----------------------------------------------------------------- */
+
+/* Local Green's function slice tstp (-1 = Matsubara): Gloc = (1/nbatch) sum_kb Gk
+ * (Sec. "GW for the translationally invariant Hubbard model", get_loc), summed in a fixed
+ * order (deterministic).  Gloc must have ldk = 1, Gk ldk = nbatch. */
+ng_status ng_kreduce_timestep(ng_ctx *ctx, const ng_grid *grid, int tstp, ng_herm Gloc,
+                              ng_herm Gk, void *stream);
+
+/* Second-Born self-energy slice tstp (-1 = Matsubara) from a local G (Eq. sigma_hubb_2b):
+ * Sigma_ab(t,t') = U(t)U(t') G_ab(t,t')^2 G_ba(t',t), components by the Langreth product
+ * rules (Eqs. def_bubble1/2); Sigma^M(tau) = -U_{-1}^2 G^M(tau)^2 G^M(-tau).
+ * U: scalar single-time function (nf = 1 layout, ldk = 1).  Sigma and G share ldk = 1. */
+ng_status ng_sigma2b_timestep(ng_ctx *ctx, const ng_grid *grid, int tstp, ng_herm Sigma,
+                              ng_herm Gloc, ng_func U, void *stream);
+
+/* Hartree mean field (Sec. "Hubbard chain"): eps_mf_kb(n) = eps0_kb(n)
+ * + U_n diag(Re rho_ii - nbar), rho = -i Gloc^<(n,n) (n >= 0) or -Gloc^M(beta^-) (n = -1).
+ * eps_mf and eps0 have ldk = nbatch (or both 1); Gloc ldk = 1. */
+ng_status ng_hartree_timestep(ng_ctx *ctx, const ng_grid *grid, int tstp, ng_func eps_mf,
+                              ng_func eps0, ng_herm Gloc, ng_func U, double nbar,
+                              void *stream);
+
+/* Predictor: fill slice tstp+1 of G from slices tstp-k..tstp by polynomial extrapolation
+ * (Appendix "Extrapolation of contour functions", Eq. polyextrap).  Requires tstp >= k. */
+ng_status ng_extrapolate_timestep(ng_ctx *ctx, const ng_grid *grid, int tstp, ng_herm G,
+                                  void *stream);
+
+/* out_dev[0] += sum over problems of ||A - B||_tstp (Eq. distancenorm; tstp = -1:
+ * Matsubara).  out_dev is a device double the caller zeroes; A and B have equal ldk. */
+ng_status ng_distance_timestep(ng_ctx *ctx, const ng_grid *grid, int tstp, ng_herm A,
+                               ng_herm B, double *out_dev, void *stream);
+
+/* ---- measurement ---------------------------------------------------------------------- */
+
+/* Start (enable = 1, clearing any previous record) or stop (enable = 0) per-launch timing of
+ * the two time-step kernels of ng_dyson_timestep: CUDA events are recorded on the launching
+ * stream around every launch of the merged bulk kernel and of the boundary kernel. */
+ng_status ng_profile_enable(ng_ctx *ctx, int enable);
+
+/* Read the record (synchronises on the last recorded event).  out[0] = total bulk-kernel
+ * time in ms, out[1] = number of bulk launches, out[2] = algorithmic FP64 flops of those
+ * launches (8 real flops per complex multiply-add of the history and source sums, nf^3
+ * complex multiply-adds per d x d block product), out[3] = total boundary-kernel time in ms,
+ * out[4] = number of boundary launches.  `out` must hold 5 doubles. */
+ng_status ng_profile_read(ng_ctx *ctx, double *out);
+
+/* ---- driver --------------------------------------------------------------------------- */
+
+/* Self-consistent second-Born run for a batch of problems coupled through
+ * Gloc = (1/nbatch) sum_kb G_kb (Sec. "Hubbard chain" program structure):
+ *  setup (if p->do_setup): Matsubara loop {Gloc, Hartree, Sigma^M, dyson_mat} to
+ *  p->mats_tol; bootstrapping {Gloc, Hartree, Sigma on slices 0..k, dyson_start} to
+ *  p->boot_tol with more than two iterations;
+ *  stepping for n = p->n_from..p->n_to: extrapolate slice n, then p->corrector iterations of
+ *  {Gloc(n), Hartree(n), Sigma(n), dyson_timestep(n)}.
+ * G: ldk = nbatch; Gloc, Sigma: ldk = 1; eps0, eps_mf: ldk = nbatch; U: ldk = 1 scalar.
+ * Host-synchronous in the setup loops (convergence checks), asynchronous in the stepping.
+ * Returns NG_ENOCONV if a setup loop hit its iteration limit (results are still written).
+ * iters_out (host, may be NULL) receives {Matsubara iterations, bootstrap iterations}. */
+ng_status ng_run_2b(ng_ctx *ctx, const ng_grid *grid, ng_herm G, ng_herm Gloc, ng_herm Sigma,
+                    ng_func eps0, ng_func eps_mf, ng_func U, const ng_run_params *p,
+                    int *iters_out, void *stream);
+
+/* Fixed-Sigma solve: dyson_mat, dyson_start, then dyson_timestep for n = k+1..n_to
+ * (Sec. "Test of accuracy and scaling analysis", three-step procedure). */
+ng_status ng_solve_fixed(ng_ctx *ctx, const ng_grid *grid, ng_herm G, ng_herm Sigma,
+                         ng_func eps, int n_to, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NG_H */

@@ -45,7 +45,7 @@ def _update_mf(n, st, eps0, U, nbar):
 
 
 def run_2b(eps0, U, nt, ntau, beta, h, W, mu=0.0, nbar=0.5, corrector=3, schedule="mixed",
-           mats_tol=1e-13, mats_maxiter=200, boot_tol=1e-13, boot_maxiter=200, nmax=None,
+           mats_tol=1e-12, mats_maxiter=200, boot_tol=1e-12, boot_maxiter=200, nmax=None,
            state=None):
     """Self-consistent second-Born for the problems with bare Hamiltonians eps0[k] (Funcs)."""
     nk = len(eps0)

@@ -307,8 +307,9 @@ def les_bulk_B(G, S, eps, mu, h, beta, W, n, Mn_dag_inv):
         acc = q_les_B(G, S, m, n, W, h, beta)
         for l in range(1, k + 1):
             acc = acc - W.a[l] / h * G.les[m, n - l]
-        Gml = np.stack([conv.lesx(G, G, m, l) for l in range(n)])
-        Sadv = np.stack([dag(S.ret[n, l]) for l in range(n)])          # Sigma^A(l,n)
+        # G^<(m,l) for l < m from the hermitian conjugate, stored for l >= m (Eq. hermconjg_gtrless)
+        Gml = np.concatenate([-dag(G.les[:m, m]), G.les[m, m:n]])
+        Sadv = dag(S.ret[n, :n])                                          # Sigma^A(l,n), l < n
         acc = acc - h * np.einsum("l,lab,lbc->ac", w[:n], Gml, -1j * Sadv)
         G.les[m, n] = acc @ Mn_dag_inv
 

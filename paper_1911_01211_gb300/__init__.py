@@ -1,0 +1,265 @@
+"""GB300 contour Dyson time-stepper: thin Python binding of libng.so (C ABI in include/ng.h).
+
+Every computation runs in the CUDA kernels of libng.so; this module only marshals
+arguments.  PyTorch supplies device memory and streams.  Importing fails loudly when
+the compiled library is missing: there is no CPU fallback.
+
+Storage (see include/ng.h): a contour function for ``nbatch`` problems is four complex128
+device tensors with the problem index innermost,
+    mat [ntau+1,            nf, nf, ldk]
+    ret [tri(nt+1),         nf, nf, ldk]   element (n, j), j <= n at tri(n) + j
+    les [tri(nt+1),         nf, nf, ldk]   element (j, n), j <= n at tri(n) + j
+    tv  [(nt+1)*(ntau+1),   nf, nf, ldk]   element (n, m) at n*(ntau+1) + m
+and a single-time function is val [nt+2, nf, nf, ldk] with f_n at index n+1.
+"""
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libng.so")
+
+NG_OK, NG_EINVAL, NG_ENOMEM, NG_ECUDA, NG_ENOCONV, NG_ETIMEOUT, NG_ENONFINITE, NG_EUNSUPPORTED = range(8)
+NG_FP64 = 0
+_STATUS_NAMES = ["NG_OK", "NG_EINVAL", "NG_ENOMEM", "NG_ECUDA", "NG_ENOCONV", "NG_ETIMEOUT",
+                 "NG_ENONFINITE", "NG_EUNSUPPORTED"]
+
+
+class NgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+class ng_grid(ctypes.Structure):
+    _fields_ = [("nt", ctypes.c_int), ("ntau", ctypes.c_int), ("nf", ctypes.c_int), ("nbatch", ctypes.c_int),
+                ("korder", ctypes.c_int), ("sig", ctypes.c_int), ("h", ctypes.c_double),
+                ("beta", ctypes.c_double), ("mu", ctypes.c_double)]
+
+
+class ng_herm(ctypes.Structure):
+    _fields_ = [("mat", ctypes.c_void_p), ("ret", ctypes.c_void_p), ("les", ctypes.c_void_p),
+                ("tv", ctypes.c_void_p), ("ldk", ctypes.c_int)]
+
+
+class ng_func(ctypes.Structure):
+    _fields_ = [("val", ctypes.c_void_p), ("ldk", ctypes.c_int)]
+
+
+class ng_run_params(ctypes.Structure):
+    _fields_ = [("corrector", ctypes.c_int), ("mats_tol", ctypes.c_double), ("mats_maxiter", ctypes.c_int),
+                ("boot_tol", ctypes.c_double), ("boot_maxiter", ctypes.c_int), ("nbar", ctypes.c_double),
+                ("n_from", ctypes.c_int), ("n_to", ctypes.c_int), ("do_setup", ctypes.c_int)]
+
+
+# every symbol the header declares, with its ctypes signature
+_P = ctypes.c_void_p
+_G = ctypes.POINTER(ng_grid)
+SIGNATURES = {
+    "ng_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(_P)]),
+    "ng_destroy": (None, [_P]),
+    "ng_last_error": (ctypes.c_char_p, [_P]),
+    "ng_status_sync": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int)]),
+    "ng_weights": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
+    "ng_green_from_H_const": (ctypes.c_int, [_P, _G, ng_herm, ctypes.POINTER(ctypes.c_double), ctypes.c_double, _P]),
+    "ng_dyson_mat": (ctypes.c_int, [_P, _G, ng_herm, ng_herm, ng_func, _P]),
+    "ng_dyson_start": (ctypes.c_int, [_P, _G, ng_herm, ng_herm, ng_func, _P]),
+    "ng_dyson_timestep": (ctypes.c_int, [_P, _G, ctypes.c_int, ng_herm, ng_herm, ng_func, ctypes.c_int, _P]),
+    "ng_kreduce_timestep": (ctypes.c_int, [_P, _G, ctypes.c_int, ng_herm, ng_herm, _P]),
+    "ng_sigma2b_timestep": (ctypes.c_int, [_P, _G, ctypes.c_int, ng_herm, ng_herm, ng_func, _P]),
+    "ng_hartree_timestep": (ctypes.c_int, [_P, _G, ctypes.c_int, ng_func, ng_func, ng_herm, ng_func,
+                                           ctypes.c_double, _P]),
+    "ng_extrapolate_timestep": (ctypes.c_int, [_P, _G, ctypes.c_int, ng_herm, _P]),
+    "ng_distance_timestep": (ctypes.c_int, [_P, _G, ctypes.c_int, ng_herm, ng_herm, _P, _P]),
+    "ng_run_2b": (ctypes.c_int, [_P, _G, ng_herm, ng_herm, ng_herm, ng_func, ng_func, ng_func,
+                                 ctypes.POINTER(ng_run_params), ctypes.POINTER(ctypes.c_int), _P]),
+    "ng_solve_fixed": (ctypes.c_int, [_P, _G, ng_herm, ng_herm, ng_func, ctypes.c_int, _P]),
+    "ng_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
+    "ng_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
+}
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libng.so and attach the signatures; raises if it is missing (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libng.so not found at {path}: build it with __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def tri(n):
+    return n * (n + 1) // 2
+
+
+@dataclass
+class Grid:
+    nt: int
+    ntau: int
+    nf: int
+    nbatch: int
+    korder: int
+    h: float
+    beta: float
+    mu: float = 0.0
+    sig: int = -1
+
+    def c(self):
+        return ng_grid(self.nt, self.ntau, self.nf, self.nbatch, self.korder, self.sig, self.h, self.beta, self.mu)
+
+
+class Herm:
+    """Device storage of a contour function for a batch (ldk = nbatch) or shared (ldk = 1)."""
+
+    def __init__(self, grid, ldk=None, device="cuda", zero=True):
+        g = grid
+        self.grid = g
+        self.ldk = g.nbatch if ldk is None else ldk
+        d, L = g.nf, self.ldk
+        alloc = torch.zeros if zero else torch.empty
+        kw = dict(dtype=torch.complex128, device=device)
+        self.mat = alloc((g.ntau + 1, d, d, L), **kw)
+        self.ret = alloc((tri(g.nt + 1), d, d, L), **kw)
+        self.les = alloc((tri(g.nt + 1), d, d, L), **kw)
+        self.tv = alloc(((g.nt + 1) * (g.ntau + 1), d, d, L), **kw)
+
+    def c(self):
+        return ng_herm(self.mat.data_ptr(), self.ret.data_ptr(), self.les.data_ptr(), self.tv.data_ptr(), self.ldk)
+
+    def tensors(self):
+        return {"mat": self.mat, "ret": self.ret, "les": self.les, "tv": self.tv}
+
+
+class Func:
+    """Device storage of a single-time function f_n, n = -1..nt, index n+1.
+    scalar=True gives the nf = 1, ldk = 1 layout of an interaction profile U_n."""
+
+    def __init__(self, grid, ldk=None, device="cuda", values=None, scalar=False):
+        g = grid
+        nf = 1 if scalar else g.nf
+        self.ldk = 1 if scalar else (g.nbatch if ldk is None else ldk)
+        if values is not None:
+            self.val = values.to(device=device, dtype=torch.complex128).contiguous()
+            assert tuple(self.val.shape) == (g.nt + 2, nf, nf, self.ldk)
+        else:
+            self.val = torch.zeros((g.nt + 2, nf, nf, self.ldk), dtype=torch.complex128, device=device)
+
+    def c(self):
+        return ng_func(self.val.data_ptr(), self.ldk)
+
+
+def _stream(stream):
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """One libng context (integration weights of order k, workspaces, status word)."""
+
+    def __init__(self, korder, device=0):
+        self.lib = load_library()
+        h = ctypes.c_void_p()
+        st = self.lib.ng_create(korder, device, ctypes.byref(h))
+        if st != NG_OK:
+            raise NgError(st, "ng_create failed")
+        self.h = h
+        self.k = korder
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ng_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _chk(self, st):
+        if st != NG_OK:
+            raise NgError(st, self.lib.ng_last_error(self.h).decode())
+
+    def weights(self):
+        out = (ctypes.c_double * 18)()
+        self._chk(self.lib.ng_weights(self.h, out))
+        return list(out)
+
+    def profile_enable(self, on=True):
+        self._chk(self.lib.ng_profile_enable(self.h, 1 if on else 0))
+
+    def profile_read(self):
+        """{bulk_ms, bulk_launches, bulk_flops, boundary_ms, boundary_launches}"""
+        out = (ctypes.c_double * 5)()
+        self._chk(self.lib.ng_profile_read(self.h, out))
+        return dict(zip(("bulk_ms", "bulk_launches", "bulk_flops", "boundary_ms", "boundary_launches"), list(out)))
+
+    def status_sync(self, stream=None):
+        f = ctypes.c_int()
+        st = self.lib.ng_status_sync(self.h, _stream(stream), ctypes.byref(f))
+        return st, f.value
+
+    # ---- entry points (same names as the C ABI, minus the ng_ prefix) ----------------
+    def green_from_H_const(self, grid, G, eps, scale=1.0, stream=None):
+        import numpy as np
+        e = np.ascontiguousarray(np.asarray(eps, dtype=np.complex128).reshape(grid.nbatch, grid.nf, grid.nf))
+        ptr = e.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        self._chk(self.lib.ng_green_from_H_const(self.h, ctypes.byref(grid.c()), G.c(), ptr, scale, _stream(stream)))
+        torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+
+    def dyson_mat(self, grid, G, S, eps, stream=None):
+        self._chk(self.lib.ng_dyson_mat(self.h, ctypes.byref(grid.c()), G.c(), S.c(), eps.c(), _stream(stream)))
+
+    def dyson_start(self, grid, G, S, eps, stream=None):
+        self._chk(self.lib.ng_dyson_start(self.h, ctypes.byref(grid.c()), G.c(), S.c(), eps.c(), _stream(stream)))
+
+    def dyson_timestep(self, grid, tstp, G, S, eps, precision=NG_FP64, stream=None):
+        self._chk(self.lib.ng_dyson_timestep(self.h, ctypes.byref(grid.c()), tstp, G.c(), S.c(), eps.c(),
+                                             precision, _stream(stream)))
+
+    def kreduce_timestep(self, grid, tstp, Gloc, Gk, stream=None):
+        self._chk(self.lib.ng_kreduce_timestep(self.h, ctypes.byref(grid.c()), tstp, Gloc.c(), Gk.c(), _stream(stream)))
+
+    def sigma2b_timestep(self, grid, tstp, S, Gloc, U, stream=None):
+        self._chk(self.lib.ng_sigma2b_timestep(self.h, ctypes.byref(grid.c()), tstp, S.c(), Gloc.c(), U.c(),
+                                               _stream(stream)))
+
+    def hartree_timestep(self, grid, tstp, eps_mf, eps0, Gloc, U, nbar, stream=None):
+        self._chk(self.lib.ng_hartree_timestep(self.h, ctypes.byref(grid.c()), tstp, eps_mf.c(), eps0.c(), Gloc.c(),
+                                               U.c(), nbar, _stream(stream)))
+
+    def extrapolate_timestep(self, grid, tstp, G, stream=None):
+        self._chk(self.lib.ng_extrapolate_timestep(self.h, ctypes.byref(grid.c()), tstp, G.c(), _stream(stream)))
+
+    def distance_timestep(self, grid, tstp, A, B, out, stream=None):
+        self._chk(self.lib.ng_distance_timestep(self.h, ctypes.byref(grid.c()), tstp, A.c(), B.c(),
+                                                ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+
+    def solve_fixed(self, grid, G, S, eps, n_to=None, stream=None):
+        n_to = grid.nt if n_to is None else n_to
+        self._chk(self.lib.ng_solve_fixed(self.h, ctypes.byref(grid.c()), G.c(), S.c(), eps.c(), n_to, _stream(stream)))
+
+    def run_2b(self, grid, G, Gloc, S, eps0, eps_mf, U, corrector=3, mats_tol=1e-12, mats_maxiter=200,
+               boot_tol=1e-12, boot_maxiter=200, nbar=0.5, n_from=None, n_to=None, do_setup=True,
+               stream=None, allow_noconv=False):
+        p = ng_run_params(corrector, mats_tol, mats_maxiter, boot_tol, boot_maxiter, nbar,
+                          grid.korder + 1 if n_from is None else n_from,
+                          grid.nt if n_to is None else n_to, 1 if do_setup else 0)
+        iters = (ctypes.c_int * 2)()
+        st = self.lib.ng_run_2b(self.h, ctypes.byref(grid.c()), G.c(), Gloc.c(), S.c(), eps0.c(), eps_mf.c(), U.c(),
+                                ctypes.byref(p), iters, _stream(stream))
+        if not (allow_noconv and st == NG_ENOCONV):
+            self._chk(st)
+        return list(iters)

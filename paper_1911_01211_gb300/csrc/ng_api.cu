@@ -1,0 +1,607 @@
+// C ABI of libng (include/ng.h): argument validation, workspaces and kernel launches.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/ng.h"
+#include "ng_setup.cuh"
+#include "ng_slice.cuh"
+
+
+struct ng_ctx {
+    int k = 0;
+    int device = 0;
+    NgWeights W;
+    char err[512] = {0};
+    int* d_status = nullptr;
+    double* d_scalar = nullptr;      // one device double for distances
+    cplx* d_eps = nullptr;           // scratch for host eps arrays
+    size_t d_eps_bytes = 0;
+    void* ws_mat = nullptr;          // Matsubara workspace
+    size_t ws_mat_bytes = 0;
+    void* ws_st = nullptr;           // start-up workspace
+    size_t ws_st_bytes = 0;
+    void* ws_prev = nullptr;         // previous iterate for the driver's convergence checks
+    size_t ws_prev_bytes = 0;
+    // per-launch timing of the time-step kernels (ng_profile_enable / ng_profile_read)
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    double prof_flops = 0.0;
+    std::vector<int> ev_kind;        // 0 bulk, 1 boundary, per event pair
+};
+
+namespace {
+
+bool g_weights_loaded[64] = {false};
+
+ng_status fail(ng_ctx* c, ng_status s, const char* fmt, ...) {
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof(c->err), fmt, ap);
+        va_end(ap);
+    }
+    return s;
+}
+
+#define CUDA_TRY(ctx, call)                                                                   \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(ctx, NG_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));       \
+    } while (0)
+
+ng_status check_launch(ng_ctx* c, const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(c, NG_ECUDA, "launch of %s failed: %s", what, cudaGetErrorString(e));
+    return NG_OK;
+}
+
+ng_status ensure(ng_ctx* c, void** p, size_t* have, size_t need) {
+    if (*have >= need) return NG_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *have = 0;
+    if (cudaMalloc(p, need) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, NG_ENOMEM, "workspace allocation of %zu bytes failed", need);
+    }
+    *have = need;
+    return NG_OK;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+ng_status check_grid(ng_ctx* c, const ng_grid* g, Grid* out) {
+    if (!c) return NG_EINVAL;
+    if (!g) return fail(c, NG_EINVAL, "grid is NULL");
+    if (g->korder != c->k) return fail(c, NG_EINVAL, "grid korder %d differs from the context order %d", g->korder, c->k);
+    if (g->sig != -1) return fail(c, NG_EINVAL, "only fermions (sig = -1) are supported");
+    if (g->nt < 2 * c->k + 2) return fail(c, NG_EINVAL, "nt = %d must be >= 2k+2 = %d", g->nt, 2 * c->k + 2);
+    if (g->ntau < 2 * c->k + 2) return fail(c, NG_EINVAL, "ntau = %d must be >= 2k+2 = %d", g->ntau, 2 * c->k + 2);
+    if (g->nbatch < 1) return fail(c, NG_EINVAL, "nbatch must be >= 1");
+    if (!(g->h > 0.0) || !(g->beta > 0.0)) return fail(c, NG_EINVAL, "h and beta must be positive");
+    if (g->nf < 1) return fail(c, NG_EINVAL, "nf must be >= 1");
+    if (g->nf > 2) return fail(c, NG_EUNSUPPORTED, "nf = %d: this build supports nf = 1, 2", g->nf);
+    out->nt = g->nt;
+    out->ntau = g->ntau;
+    out->nf = g->nf;
+    out->nb = g->nbatch;
+    out->k = c->k;
+    out->sig = g->sig;
+    out->h = g->h;
+    out->beta = g->beta;
+    out->mu = g->mu;
+    out->htau = g->beta / g->ntau;
+    return NG_OK;
+}
+
+ng_status check_herm(ng_ctx* c, const Grid& g, const ng_herm& X, const char* name, bool need_rt, HermV* out,
+                     int want_ldk /* 0: either */) {
+    if (X.ldk != 1 && X.ldk != g.nb) return fail(c, NG_EINVAL, "%s.ldk = %d must be 1 or nbatch = %d", name, X.ldk, g.nb);
+    if (want_ldk && X.ldk != want_ldk && !(g.nb == 1))
+        return fail(c, NG_EINVAL, "%s.ldk = %d must be %d", name, X.ldk, want_ldk);
+    if (!X.mat || !aligned16(X.mat)) return fail(c, NG_EINVAL, "%s.mat is NULL or not 16-byte aligned", name);
+    if (need_rt) {
+        if (!X.ret || !X.les || !X.tv || !aligned16(X.ret) || !aligned16(X.les) || !aligned16(X.tv))
+            return fail(c, NG_EINVAL, "%s.ret/les/tv is NULL or not 16-byte aligned", name);
+    }
+    const int dd = g.nf * g.nf;
+    out->mat = Comp{(cplx*)X.mat, X.ldk, dd};
+    out->ret = Comp{(cplx*)X.ret, X.ldk, dd};
+    out->les = Comp{(cplx*)X.les, X.ldk, dd};
+    out->tv = Comp{(cplx*)X.tv, X.ldk, dd};
+    return NG_OK;
+}
+
+ng_status check_func(ng_ctx* c, const Grid& g, const ng_func& f, const char* name, FuncV* out) {
+    if (!f.val || !aligned16(f.val)) return fail(c, NG_EINVAL, "%s.val is NULL or not 16-byte aligned", name);
+    if (f.ldk != 1 && f.ldk != g.nb) return fail(c, NG_EINVAL, "%s.ldk = %d must be 1 or nbatch", name, f.ldk);
+    out->p = (cplx*)f.val;
+    out->ldk = f.ldk;
+    return NG_OK;
+}
+
+inline unsigned nblocks(int64_t items, int threads) { return (unsigned)((items + threads - 1) / threads); }
+
+// event pair for one profiled launch; returns the index of the start event or -1
+long prof_pair(ng_ctx* c, int kind) {
+    if (!c->prof) return -1;
+    while (c->ev_pool.size() < c->ev_used + 2) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return -1; }
+        c->ev_pool.push_back(e);
+    }
+    long i = (long)c->ev_used;
+    c->ev_used += 2;
+    c->ev_kind.push_back(kind);
+    return i;
+}
+
+// algorithmic complex block multiply-adds of one bulk launch at step n (history and source
+// sums of the three bulk tasks; the BDF terms and the per-item matrix inverse are not counted)
+double bulk_cmacs(const Grid& g, int n) {
+    const int k = g.k, T = g.ntau;
+    double per_tv = 0.0;
+    for (int m = 0; m <= T; ++m) {
+        per_tv += n;                                              // history j = 0..n-1
+        per_tv += (m <= k) ? (k + 1) * (k + 1) : (m + 1);         // C^tv_2
+        per_tv += (m >= T - k) ? (k + 1) * (k + 1) : (T - m + 1); // C^tv_3
+    }
+    double per_ret = 0.0;
+    for (int m = 0; m <= n - k - 1; ++m) per_ret += n - m;
+    double per_les = 0.0;
+    if (n >= 2 * k + 1)
+        for (int m = 1; m <= n - k - 1; ++m) per_les += (m <= k ? k + 1 : m + 1) + (T + 1) + n;
+    return (double)g.nb * (per_tv + per_ret + per_les);
+}
+
+// ---------------------------------------------------------------------------------------
+// launch bodies templated on the orbital dimension
+// ---------------------------------------------------------------------------------------
+template <int D>
+ng_status launch_timestep(ng_ctx* c, const Grid& g, int n, const HermV& G, const HermV& S, const FuncV& eps,
+                          cudaStream_t s) {
+    const int k = g.k, thr = 128;
+    const int64_t it_les = (n >= 2 * k + 1) ? (int64_t)g.nb * (n - k - 1) : 0;
+    const int64_t it_tv = (int64_t)g.nb * (g.ntau + 1);
+    const int64_t it_ret = (int64_t)g.nb * (n - k);
+    const int b_les = (int)nblocks(it_les, thr), b_tv = (int)nblocks(it_tv, thr), b_ret = (int)nblocks(it_ret, thr);
+    long e0 = prof_pair(c, 0);
+    if (e0 >= 0) cudaEventRecord(c->ev_pool[e0], s);
+    k_step_bulk<D><<<b_les + b_tv + b_ret, thr, 0, s>>>(g, n, G, S, eps, b_les, b_tv, b_ret, c->d_status);
+    ng_status st = check_launch(c, "k_step_bulk");
+    if (st) return st;
+    if (e0 >= 0) {
+        cudaEventRecord(c->ev_pool[e0 + 1], s);
+        c->prof_flops += 8.0 * D * D * D * bulk_cmacs(g, n);
+    }
+    long e1 = prof_pair(c, 1);
+    if (e1 >= 0) cudaEventRecord(c->ev_pool[e1], s);
+    k_step_boundary<D><<<g.nb, NG_BND_THREADS, 0, s>>>(g, n, G, S, eps, c->d_status);
+    if (e1 >= 0) cudaEventRecord(c->ev_pool[e1 + 1], s);
+    return check_launch(c, "k_step_boundary");
+}
+
+template <int D>
+ng_status launch_mat(ng_ctx* c, const Grid& g, const HermV& G, const HermV& S, const FuncV& eps, cudaStream_t s) {
+    const int T = g.ntau, N = (T + 1) * D, ld = N + D;
+    const size_t b_g = sizeof(cplx) * (size_t)g.nb * (T + 1) * D * D;
+    const size_t b_A = sizeof(cplx) * (size_t)g.nb * N * ld;
+    ng_status st = ensure(c, &c->ws_mat, &c->ws_mat_bytes, 2 * b_g + b_A);
+    if (st) return st;
+    cplx* ws_g = (cplx*)c->ws_mat;
+    cplx* ws_K = ws_g + b_g / sizeof(cplx);
+    cplx* ws_A = ws_K + b_g / sizeof(cplx);
+    const int64_t items = (int64_t)(T + 1) * g.nb;
+    k_mat_g<D><<<nblocks(items, 128), 128, 0, s>>>(g, eps, ws_g);
+    if ((st = check_launch(c, "k_mat_g"))) return st;
+    k_mat_K<D><<<nblocks(items, 128), 128, 0, s>>>(g, S, ws_g, ws_K);
+    if ((st = check_launch(c, "k_mat_K"))) return st;
+    const int64_t ab = (int64_t)(T + 1) * (T + 2) * g.nb;
+    k_mat_assemble<D><<<nblocks(ab, 256), 256, 0, s>>>(g, ws_g, ws_K, ws_A);
+    if ((st = check_launch(c, "k_mat_assemble"))) return st;
+    const size_t smem = sizeof(cplx) * (size_t)(ld + N) + NG_LU_THREADS * (sizeof(double) + sizeof(int));
+    CUDA_TRY(c, cudaFuncSetAttribute(k_lu_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_lu_solve<<<g.nb, NG_LU_THREADS, smem, s>>>(N, D, ws_A, c->d_status);
+    if ((st = check_launch(c, "k_lu_solve"))) return st;
+    k_mat_store<D><<<nblocks(items, 128), 128, 0, s>>>(g, ws_A, G, c->d_status);
+    return check_launch(c, "k_mat_store");
+}
+
+template <int D>
+ng_status launch_start(ng_ctx* c, const Grid& g, const HermV& G, const HermV& S, const FuncV& eps, cudaStream_t s) {
+    const int k = g.k, N = k * D;
+    const size_t need = sizeof(cplx) * (size_t)g.nb * (N * N + k * D * D);
+    ng_status st = ensure(c, &c->ws_st, &c->ws_st_bytes, need);
+    if (st) return st;
+    cplx* ws = (cplx*)c->ws_st;
+    k_start_ret<D><<<nblocks(g.nb, 64), 64, 0, s>>>(g, G, S, eps, ws, c->d_status);
+    if ((st = check_launch(c, "k_start_ret"))) return st;
+    k_start_tv<D><<<nblocks((int64_t)(g.ntau + 1) * g.nb, 128), 128, 0, s>>>(g, G, S, ws, c->d_status);
+    if ((st = check_launch(c, "k_start_tv"))) return st;
+    k_start_les<D><<<nblocks((int64_t)(k + 1) * g.nb, 64), 64, 0, s>>>(g, G, S, ws, c->d_status);
+    return check_launch(c, "k_start_les");
+}
+
+template <int D>
+ng_status launch_free(ng_ctx* c, const Grid& g, const HermV& G, const cplx* eps_dev, double scale, cudaStream_t s) {
+    const int64_t nel = (g.ntau + 1) + 2 * tri(g.nt + 1) + (int64_t)(g.nt + 1) * (g.ntau + 1);
+    k_free_gf<D><<<nblocks(nel * g.nb, 128), 128, 0, s>>>(g, G, eps_dev, scale);
+    return check_launch(c, "k_free_gf");
+}
+
+ng_status do_kreduce(ng_ctx* c, const Grid& g, int tstp, const HermV& L, const HermV& Gk, cudaStream_t s) {
+    const int cnt = tstp < 0 ? g.ntau + 1 : 2 * (tstp + 1) + g.ntau + 1;
+    const int64_t warps = (int64_t)cnt * g.nf * g.nf;
+    k_kreduce<<<nblocks(warps * 32, 256), 256, 0, s>>>(g, tstp, L, Gk);
+    return check_launch(c, "k_kreduce");
+}
+ng_status do_sigma(ng_ctx* c, const Grid& g, int tstp, const HermV& S, const HermV& L, const FuncV& U, cudaStream_t s) {
+    const int cnt = tstp < 0 ? g.ntau + 1 : 2 * (tstp + 1) + g.ntau + 1;
+    k_sigma2b<<<nblocks((int64_t)cnt * g.nf * g.nf, 128), 128, 0, s>>>(g, tstp, S, L, U);
+    return check_launch(c, "k_sigma2b");
+}
+ng_status do_hartree(ng_ctx* c, const Grid& g, int tstp, const FuncV& mf, const FuncV& e0, const HermV& L, const FuncV& U,
+                     double nbar, cudaStream_t s) {
+    k_hartree<<<nblocks((int64_t)mf.ldk * g.nf * g.nf, 128), 128, 0, s>>>(g, tstp, mf, e0, L, U, nbar);
+    return check_launch(c, "k_hartree");
+}
+ng_status do_timestep(ng_ctx* c, const Grid& g, int n, const HermV& G, const HermV& S, const FuncV& eps, cudaStream_t s) {
+    return g.nf == 1 ? launch_timestep<1>(c, g, n, G, S, eps, s) : launch_timestep<2>(c, g, n, G, S, eps, s);
+}
+ng_status do_mat(ng_ctx* c, const Grid& g, const HermV& G, const HermV& S, const FuncV& eps, cudaStream_t s) {
+    return g.nf == 1 ? launch_mat<1>(c, g, G, S, eps, s) : launch_mat<2>(c, g, G, S, eps, s);
+}
+ng_status do_start(ng_ctx* c, const Grid& g, const HermV& G, const HermV& S, const FuncV& eps, cudaStream_t s) {
+    return g.nf == 1 ? launch_start<1>(c, g, G, S, eps, s) : launch_start<2>(c, g, G, S, eps, s);
+}
+ng_status do_extrap(ng_ctx* c, const Grid& g, int n, const HermV& G, cudaStream_t s) {
+    const int64_t items = (int64_t)(2 * (n + 2) + g.ntau + 1) * g.nf * g.nf * G.ret.ldk;
+    k_extrapolate<<<nblocks(items, 128), 128, 0, s>>>(g, n, G);
+    return check_launch(c, "k_extrapolate");
+}
+ng_status do_distance(ng_ctx* c, const Grid& g, int tstp, const HermV& A, const HermV& B, double* out, cudaStream_t s) {
+    k_distance<<<4 * 152, 256, 0, s>>>(g, tstp, A, B, out);
+    return check_launch(c, "k_distance");
+}
+
+}  // namespace
+
+// =========================================================================================
+// C ABI
+// =========================================================================================
+extern "C" {
+
+ng_status ng_create(int korder, int device, ng_ctx** out) {
+    if (!out) return NG_EINVAL;
+    *out = nullptr;
+    if (korder < 1 || korder > NG_KMAX) return NG_EINVAL;
+    if (cudaSetDevice(device) != cudaSuccess) { cudaGetLastError(); return NG_ECUDA; }
+    ng_ctx* c = new ng_ctx();
+    c->k = korder;
+    c->device = device;
+    ng_make_weights(korder, &c->W);
+    if (device >= 0 && device < 64 && !g_weights_loaded[device]) {
+        NgWeights all[NG_KMAX];
+        for (int k = 1; k <= NG_KMAX; ++k) ng_make_weights(k, &all[k - 1]);
+        if (cudaMemcpyToSymbol(c_W, all, sizeof(all)) != cudaSuccess) { cudaGetLastError(); delete c; return NG_ECUDA; }
+        g_weights_loaded[device] = true;
+    }
+    if (cudaMalloc(&c->d_status, sizeof(int)) != cudaSuccess || cudaMalloc(&c->d_scalar, sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return NG_ENOMEM;
+    }
+    cudaMemset(c->d_status, 0, sizeof(int));
+    *out = c;
+    return NG_OK;
+}
+
+void ng_destroy(ng_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    cudaFree(c->d_status);
+    cudaFree(c->d_scalar);
+    cudaFree(c->d_eps);
+    cudaFree(c->ws_mat);
+    cudaFree(c->ws_st);
+    cudaFree(c->ws_prev);
+    delete c;
+}
+
+const char* ng_last_error(const ng_ctx* c) { return c ? c->err : "NULL context"; }
+
+ng_status ng_status_sync(ng_ctx* c, void* stream, int* flags) {
+    if (!c) return NG_EINVAL;
+    CUDA_TRY(c, cudaStreamSynchronize((cudaStream_t)stream));
+    int f = 0;
+    CUDA_TRY(c, cudaMemcpy(&f, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    CUDA_TRY(c, cudaMemset(c->d_status, 0, sizeof(int)));
+    if (flags) *flags = f;
+    if (f & NGF_NONFINITE) return fail(c, NG_ENONFINITE, "device reported non-finite values (flags %d)", f);
+    return NG_OK;
+}
+
+ng_status ng_profile_enable(ng_ctx* c, int enable) {
+    if (!c) return NG_EINVAL;
+    if (enable) {
+        c->ev_used = 0;
+        c->ev_kind.clear();
+        c->prof_flops = 0.0;
+    }
+    c->prof = enable != 0;
+    return NG_OK;
+}
+
+ng_status ng_profile_read(ng_ctx* c, double* out) {
+    if (!c || !out) return NG_EINVAL;
+    for (int i = 0; i < 5; ++i) out[i] = 0.0;
+    if (c->ev_used) CUDA_TRY(c, cudaEventSynchronize(c->ev_pool[c->ev_used - 1]));
+    for (size_t p = 0; p < c->ev_kind.size(); ++p) {
+        float ms = 0.f;
+        CUDA_TRY(c, cudaEventElapsedTime(&ms, c->ev_pool[2 * p], c->ev_pool[2 * p + 1]));
+        if (c->ev_kind[p] == 0) { out[0] += ms; out[1] += 1; }
+        else { out[3] += ms; out[4] += 1; }
+    }
+    out[2] = c->prof_flops;
+    return NG_OK;
+}
+
+ng_status ng_weights(const ng_ctx* c, double* out) {
+    if (!c || !out) return NG_EINVAL;
+    for (int i = 0; i < 18; ++i) out[i] = 0.0;
+    for (int j = 0; j <= c->k; ++j) {
+        out[j] = c->W.a[j];
+        out[6 + j] = c->W.omega[j];
+        out[12 + j] = c->W.C[j];
+    }
+    return NG_OK;
+}
+
+ng_status ng_green_from_H_const(ng_ctx* c, const ng_grid* grid, ng_herm G, const double* eps_host, double scale,
+                                void* stream) {
+    Grid g;
+    HermV Gv;
+    ng_status st;
+    if ((st = check_grid(c, grid, &g))) return st;
+    if ((st = check_herm(c, g, G, "G", true, &Gv, g.nb))) return st;
+    if (!eps_host) return fail(c, NG_EINVAL, "eps_host is NULL");
+    const size_t bytes = sizeof(cplx) * (size_t)g.nb * g.nf * g.nf;
+    if ((st = ensure(c, (void**)&c->d_eps, &c->d_eps_bytes, bytes))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_eps, eps_host, bytes, cudaMemcpyHostToDevice, s));
+    return g.nf == 1 ? launch_free<1>(c, g, Gv, c->d_eps, scale, s) : launch_free<2>(c, g, Gv, c->d_eps, scale, s);
+}
+
+ng_status ng_dyson_mat(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm S, ng_func eps, void* stream) {
+    Grid g;
+    HermV Gv, Sv;
+    FuncV ev;
+    ng_status st;
+    if ((st = check_grid(c, grid, &g))) return st;
+    if ((st = check_herm(c, g, G, "G", false, &Gv, g.nb))) return st;
+    if ((st = check_herm(c, g, S, "Sigma", false, &Sv, 0))) return st;
+    if ((st = check_func(c, g, eps, "eps", &ev))) return st;
+    return do_mat(c, g, Gv, Sv, ev, (cudaStream_t)stream);
+}
+
+ng_status ng_dyson_start(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm S, ng_func eps, void* stream) {
+    Grid g;
+    HermV Gv, Sv;
+    FuncV ev;
+    ng_status st;
+    if ((st = check_grid(c, grid, &g))) return st;
+    if ((st = check_herm(c, g, G, "G", true, &Gv, g.nb))) return st;
+    if ((st = check_herm(c, g, S, "Sigma", true, &Sv, 0))) return st;
+    if ((st = check_func(c, g, eps, "eps", &ev))) return st;
+    return do_start(c, g, Gv, Sv, ev, (cudaStream_t)stream);
+}
+
+ng_status ng_dyson_timestep(ng_ctx* c, const ng_grid* grid, int tstp, ng_herm G, ng_herm S, ng_func eps, int precision,
+                            void* stream) {
+    Grid g;
+    HermV Gv, Sv;
+    FuncV ev;
+    ng_status st;
+    if ((st = check_grid(c, grid, &g))) return st;
+    if (tstp <= g.k || tstp > g.nt) return fail(c, NG_EINVAL, "tstp = %d must be in k+1..nt = %d..%d", tstp, g.k + 1, g.nt);
+    if (precision != NG_FP64) return fail(c, NG_EUNSUPPORTED, "precision %d is not available", precision);
+    if ((st = check_herm(c, g, G, "G", true, &Gv, g.nb))) return st;
+    if ((st = check_herm(c, g, S, "Sigma", true, &Sv, 0))) return st;
+    if ((st = check_func(c, g, eps, "eps", &ev))) return st;
+    return do_timestep(c, g, tstp, Gv, Sv, ev, (cudaStream_t)stream);
+}
+
+ng_status ng_kreduce_timestep(ng_ctx* c, const ng_grid* grid, int tstp, ng_herm Gloc, ng_herm Gk, void* stream) {
+    Grid g;
+    HermV L, K;
+    ng_status st;
+    if ((st = check_grid(c, grid, &g))) return st;
+    if (tstp < -1 || tstp > g.nt) return fail(c, NG_EINVAL, "tstp = %d out of range", tstp);
+    if (Gloc.ldk != 1) return fail(c, NG_EINVAL, "Gloc.ldk must be 1");
+    if ((st = check_herm(c, g, Gloc, "Gloc", tstp >= 0, &L, 1))) return st;
+    if ((st = check_herm(c, g, Gk, "Gk", tstp >= 0, &K, g.nb))) return st;
+    return do_kreduce(c, g, tstp, L, K, (cudaStream_t)stream);
+}
+
+ng_status ng_sigma2b_timestep(ng_ctx* c, const ng_grid* grid, int tstp, ng_herm S, ng_herm Gloc, ng_func U, void* stream) {
+    Grid g;
+    HermV Sv, L;
+    FuncV uv;
+    ng_status st;
+    if ((st = check_grid(c, grid, &g))) return st;
+    if (tstp < -1 || tstp > g.nt) return fail(c, NG_EINVAL, "tstp = %d out of range", tstp);
+    if (S.ldk != 1 || Gloc.ldk != 1) return fail(c, NG_EINVAL, "Sigma and Gloc must have ldk = 1");
+    if ((st = check_herm(c, g, S, "Sigma", tstp >= 0, &Sv, 1))) return st;
+    if ((st = check_herm(c, g, Gloc, "Gloc", tstp >= 0, &L, 1))) return st;
+    if ((st = check_func(c, g, U, "U", &uv))) return st;
+    if (U.ldk != 1) return fail(c, NG_EINVAL, "U.ldk must be 1");
+    return do_sigma(c, g, tstp, Sv, L, uv, (cudaStream_t)stream);
+}
+
+ng_status ng_hartree_timestep(ng_ctx* c, const ng_grid* grid, int tstp, ng_func epsmf, ng_func eps0, ng_herm Gloc,
+                              ng_func U, double nbar, void* stream) {
+    Grid g;
+    HermV L;
+    FuncV mf, e0, uv;
+    ng_status st;
+    if ((st = check_grid(c, grid, &g))) return st;
+    if (tstp < -1 || tstp > g.nt) return fail(c, NG_EINVAL, "tstp = %d out of range", tstp);
+    if ((st = check_func(c, g, epsmf, "eps_mf", &mf))) return st;
+    if ((st = check_func(c, g, eps0, "eps0", &e0))) return st;
+    if ((st = check_func(c, g, U, "U", &uv))) return st;
+    if ((st = check_herm(c, g, Gloc, "Gloc", tstp >= 0, &L, 1))) return st;
+    return do_hartree(c, g, tstp, mf, e0, L, uv, nbar, (cudaStream_t)stream);
+}
+
+ng_status ng_extrapolate_timestep(ng_ctx* c, const ng_grid* grid, int tstp, ng_herm G, void* stream) {
+    Grid g;
+    HermV Gv;
+    ng_status st;
+    if ((st = check_grid(c, grid, &g))) return st;
+    if (tstp < g.k || tstp + 1 > g.nt) return fail(c, NG_EINVAL, "tstp = %d must be in k..nt-1", tstp);
+    if ((st = check_herm(c, g, G, "G", true, &Gv, 0))) return st;
+    return do_extrap(c, g, tstp, Gv, (cudaStream_t)stream);
+}
+
+ng_status ng_distance_timestep(ng_ctx* c, const ng_grid* grid, int tstp, ng_herm A, ng_herm B, double* out_dev,
+                               void* stream) {
+    Grid g;
+    HermV Av, Bv;
+    ng_status st;
+    if ((st = check_grid(c, grid, &g))) return st;
+    if (tstp < -1 || tstp > g.nt) return fail(c, NG_EINVAL, "tstp = %d out of range", tstp);
+    if (A.ldk != B.ldk) return fail(c, NG_EINVAL, "A and B must have the same ldk");
+    if ((st = check_herm(c, g, A, "A", tstp >= 0, &Av, 0))) return st;
+    if ((st = check_herm(c, g, B, "B", tstp >= 0, &Bv, 0))) return st;
+    if (!out_dev) return fail(c, NG_EINVAL, "out_dev is NULL");
+    return do_distance(c, g, tstp, Av, Bv, out_dev, (cudaStream_t)stream);
+}
+
+ng_status ng_solve_fixed(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm S, ng_func eps, int n_to, void* stream) {
+    Grid g;
+    HermV Gv, Sv;
+    FuncV ev;
+    ng_status st;
+    if ((st = check_grid(c, grid, &g))) return st;
+    if (n_to < g.k || n_to > g.nt) return fail(c, NG_EINVAL, "n_to = %d must be in k..nt", n_to);
+    if ((st = check_herm(c, g, G, "G", true, &Gv, g.nb))) return st;
+    if ((st = check_herm(c, g, S, "Sigma", true, &Sv, 0))) return st;
+    if ((st = check_func(c, g, eps, "eps", &ev))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = do_mat(c, g, Gv, Sv, ev, s))) return st;
+    if ((st = do_start(c, g, Gv, Sv, ev, s))) return st;
+    for (int n = g.k + 1; n <= n_to; ++n)
+        if ((st = do_timestep(c, g, n, Gv, Sv, ev, s))) return st;
+    return NG_OK;
+}
+
+ng_status ng_run_2b(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm Gloc, ng_herm S, ng_func eps0, ng_func epsmf,
+                    ng_func U, const ng_run_params* p, int* iters_out, void* stream) {
+    Grid g;
+    HermV Gv, Lv, Sv;
+    FuncV e0, mf, uv;
+    ng_status st;
+    if ((st = check_grid(c, grid, &g))) return st;
+    if (!p) return fail(c, NG_EINVAL, "params is NULL");
+    if ((st = check_herm(c, g, G, "G", true, &Gv, g.nb))) return st;
+    if (Gloc.ldk != 1 || S.ldk != 1) return fail(c, NG_EINVAL, "Gloc and Sigma must have ldk = 1");
+    if ((st = check_herm(c, g, Gloc, "Gloc", true, &Lv, 1))) return st;
+    if ((st = check_herm(c, g, S, "Sigma", true, &Sv, 1))) return st;
+    if ((st = check_func(c, g, eps0, "eps0", &e0))) return st;
+    if ((st = check_func(c, g, epsmf, "eps_mf", &mf))) return st;
+    if ((st = check_func(c, g, U, "U", &uv))) return st;
+    if (U.ldk != 1) return fail(c, NG_EINVAL, "U.ldk must be 1");
+    if (epsmf.ldk != G.ldk) return fail(c, NG_EINVAL, "eps_mf.ldk must equal G.ldk");
+    if (p->corrector < 1) return fail(c, NG_EINVAL, "corrector must be >= 1");
+    if (p->n_to > g.nt || (p->n_to >= p->n_from && p->n_from <= g.k))
+        return fail(c, NG_EINVAL, "stepping range %d..%d invalid (k = %d, nt = %d)", p->n_from, p->n_to, g.k, g.nt);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int k = g.k, dd = g.nf * g.nf, T = g.ntau;
+    int mats_it = 0, boot_it = 0;
+    bool noconv = false;
+    if (p->do_setup) {
+        // previous-iterate buffer shaped like slices 0..k of G plus mat
+        const size_t el_mat = (size_t)(T + 1), el_tri = (size_t)tri(k + 1), el_tv = (size_t)(k + 1) * (T + 1);
+        const size_t per = sizeof(cplx) * dd * (size_t)G.ldk;
+        if ((st = ensure(c, &c->ws_prev, &c->ws_prev_bytes, per * (el_mat + 2 * el_tri + el_tv)))) return st;
+        cplx* pb = (cplx*)c->ws_prev;
+        HermV Pv;
+        Pv.mat = Comp{pb, G.ldk, dd};
+        Pv.ret = Comp{pb + el_mat * dd * G.ldk, G.ldk, dd};
+        Pv.les = Comp{Pv.ret.p + el_tri * dd * G.ldk, G.ldk, dd};
+        // tv rows 0..k are contiguous in G.tv, so the previous copy keeps the same row stride
+        Pv.tv = Comp{Pv.les.p + el_tri * dd * G.ldk, G.ldk, dd};
+        const size_t fslice = sizeof(cplx) * dd * (size_t)epsmf.ldk;
+        // ---- Matsubara loop ----
+        CUDA_TRY(c, cudaMemcpyAsync(epsmf.val, eps0.val, fslice, cudaMemcpyDeviceToDevice, s));
+        CUDA_TRY(c, cudaMemsetAsync(S.mat, 0, sizeof(cplx) * dd * el_mat, s));
+        if ((st = do_mat(c, g, Gv, Sv, mf, s))) return st;
+        double err = 0.0;
+        for (mats_it = 0; mats_it < p->mats_maxiter; ++mats_it) {
+            if ((st = do_kreduce(c, g, -1, Lv, Gv, s))) return st;
+            if ((st = do_hartree(c, g, -1, mf, e0, Lv, uv, p->nbar, s))) return st;
+            if ((st = do_sigma(c, g, -1, Sv, Lv, uv, s))) return st;
+            CUDA_TRY(c, cudaMemcpyAsync(Pv.mat.p, Gv.mat.p, per * el_mat, cudaMemcpyDeviceToDevice, s));
+            if ((st = do_mat(c, g, Gv, Sv, mf, s))) return st;
+            CUDA_TRY(c, cudaMemsetAsync(c->d_scalar, 0, sizeof(double), s));
+            if ((st = do_distance(c, g, -1, Gv, Pv, c->d_scalar, s))) return st;
+            CUDA_TRY(c, cudaMemcpyAsync(&err, c->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, s));
+            CUDA_TRY(c, cudaStreamSynchronize(s));
+            if (err < p->mats_tol) break;
+        }
+        if (mats_it == p->mats_maxiter) noconv = true;
+        ++mats_it;
+        if ((st = do_kreduce(c, g, -1, Lv, Gv, s))) return st;
+        if ((st = do_hartree(c, g, -1, mf, e0, Lv, uv, p->nbar, s))) return st;
+        if ((st = do_sigma(c, g, -1, Sv, Lv, uv, s))) return st;
+        // ---- bootstrapping ----
+        for (int n = 0; n <= k; ++n) {
+            k_mf_init<<<nblocks((int64_t)dd * epsmf.ldk, 128), 128, 0, s>>>(g, n, mf, e0);
+            if ((st = check_launch(c, "k_mf_init"))) return st;
+        }
+        if ((st = do_start(c, g, Gv, Sv, mf, s))) return st;
+        for (boot_it = 0; boot_it < p->boot_maxiter; ++boot_it) {
+            for (int n = 0; n <= k; ++n) {
+                if ((st = do_kreduce(c, g, n, Lv, Gv, s))) return st;
+                if ((st = do_hartree(c, g, n, mf, e0, Lv, uv, p->nbar, s))) return st;
+                if ((st = do_sigma(c, g, n, Sv, Lv, uv, s))) return st;
+            }
+            CUDA_TRY(c, cudaMemcpyAsync(Pv.ret.p, Gv.ret.p, per * el_tri, cudaMemcpyDeviceToDevice, s));
+            CUDA_TRY(c, cudaMemcpyAsync(Pv.les.p, Gv.les.p, per * el_tri, cudaMemcpyDeviceToDevice, s));
+            CUDA_TRY(c, cudaMemcpyAsync(Pv.tv.p, Gv.tv.p, per * el_tv, cudaMemcpyDeviceToDevice, s));
+            if ((st = do_start(c, g, Gv, Sv, mf, s))) return st;
+            CUDA_TRY(c, cudaMemsetAsync(c->d_scalar, 0, sizeof(double), s));
+            for (int n = 0; n <= k; ++n)
+                if ((st = do_distance(c, g, n, Gv, Pv, c->d_scalar, s))) return st;
+            CUDA_TRY(c, cudaMemcpyAsync(&err, c->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, s));
+            CUDA_TRY(c, cudaStreamSynchronize(s));
+            if (err < p->boot_tol && boot_it > 2) break;
+        }
+        if (boot_it == p->boot_maxiter) noconv = true;
+        ++boot_it;
+    }
+    // ---- time stepping: predictor, then fixed corrector iterations ----
+    for (int n = p->n_from; n <= p->n_to; ++n) {
+        if ((st = do_extrap(c, g, n - 1, Gv, s))) return st;
+        for (int it = 0; it < p->corrector; ++it) {
+            if ((st = do_kreduce(c, g, n, Lv, Gv, s))) return st;
+            if ((st = do_hartree(c, g, n, mf, e0, Lv, uv, p->nbar, s))) return st;
+            if ((st = do_sigma(c, g, n, Sv, Lv, uv, s))) return st;
+            if ((st = do_timestep(c, g, n, Gv, Sv, mf, s))) return st;
+        }
+    }
+    if (iters_out) {
+        iters_out[0] = mats_it;
+        iters_out[1] = boot_it;
+    }
+    if (noconv) return fail(c, NG_ENOCONV, "setup loop reached its iteration limit (mats %d, boot %d)", mats_it, boot_it);
+    return NG_OK;
+}
+
+}  // extern "C"

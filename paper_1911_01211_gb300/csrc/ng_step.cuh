@@ -1,0 +1,410 @@
+// Time-step kernels of libng: slice n > k of G for a batch of problems (mixed schedule).
+//
+// Sec. "Time stepping" of the NESSi paper:
+//   retarded row   : (B) single VIDE steps for columns m <= n-k-1 (Eq. MBCVSAMx_t with
+//                    y(t) = G^R(mh+t, mh), kernel i Sigma^R), (A) conjugate start-up for
+//                    m = n-k..n (Eq. MBCVSAMx_cc_start along the row);
+//   left-mixing row: one VIDE step per tau_m (Eq. dyson_langreth_tv), source
+//                    -i (C^tv_2 + C^tv_3)[Sigma, 1, G^M] (Eqs. ctv2, ctv3);
+//   lesser column  : (B) conjugate single steps for 1 <= m <= n-k-1 (Eq. MBCVSAMx_cc_t with
+//                    y(t) = G^<(mh, t), kernel -i Sigma^A, source i (C^<_1 + C^<_3)[G,1,Sigma]),
+//                    G^<(0,n) from Eq. dyson_ini_les, then serial VIDE steps (A) for
+//                    m = n-k..n (source -i (C^<_2 + C^<_3)[Sigma,1,G]); the whole column by
+//                    (A) when n <= 2k.
+// All steps with implementation (B) and the left-mixing row share
+//   M_n = a_0/h + i(eps_n - mu) + h w_{n,n} i Sigma^R(n,n).
+#pragma once
+
+#include "ng_common.cuh"
+
+
+// calls f(l, w_{L,l}) for l = 0..lmax (lmax <= L), for a Gregory row L > k
+template <class F>
+__device__ __forceinline__ void greg_for(const NgWeights& W, int L, int lmax, F&& f) {
+    const int k = W.k;
+    if (L <= 2 * k + 1) {
+        for (int l = 0; l <= lmax; ++l) f(l, W.greg[L][l]);
+        return;
+    }
+    const int e1 = min(k, lmax);
+    for (int l = 0; l <= e1; ++l) f(l, W.omega[l]);
+    const int e2 = min(L - k - 1, lmax);
+    for (int l = k + 1; l <= e2; ++l) f(l, 1.0);
+    for (int l = L - k; l <= lmax; ++l) f(l, W.omega[L - l]);
+}
+
+// acc += x * y^dagger
+template <int D>
+__device__ __forceinline__ void mfma_db(Mat<D>& acc, const Mat<D>& x, const Mat<D>& y) {
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+#pragma unroll
+            for (int b = 0; b < D; ++b) acc.v[a][b] = cfma(x.v[a][c], cconj(y.v[b][c]), acc.v[a][b]);
+}
+
+template <int D>
+__device__ __forceinline__ Mat<D> step_matrix(const NgWeights& W, const Grid& g, const HermV& S,
+                                              const FuncV& eps, int n, int kb) {
+    Mat<D> e = ldf<D>(eps, n, kb);
+    Mat<D> M = meye<D>(cr(W.a[0] / g.h));
+#pragma unroll
+    for (int a = 0; a < D; ++a) e.v[a][a].x -= g.mu;
+    M = madd<D>(M, mmuli<D>(e));
+    M = madd<D>(M, mscal<D>(g.h * gw(W, n, n), mmuli<D>(gret<D>(S, n, n, kb))));
+    return M;
+}
+
+// -i (C^tv_2 + C^tv_3)[Sigma, 1, G^M](n, m)   (Eqs. ctv2, ctv3)
+template <int D>
+__device__ Mat<D> q_tv(const NgWeights& W, const Grid& g, const HermV& G, const HermV& S, int n, int m,
+                       int kb) {
+    const int k = W.k, T = g.ntau;
+    const double xi = (double)g.sig;
+    Mat<D> c2 = mzero<D>(), c3 = mzero<D>();
+    if (m <= k) {
+        for (int j = 0; j <= k; ++j) {
+            Mat<D> gm = mscal<D>(xi, gmat<D>(G, T - j, kb));
+            for (int l = 0; l <= k; ++l) {
+                Mat<D> s = mscal<D>(W.R[m][j][l], gtv<D>(S, g, n, l, kb));
+                mfma<D>(c2, s, gm);
+            }
+        }
+    } else {
+        greg_for(W, m, m, [&](int l, double w) {
+            mfma<D>(c2, mscal<D>(w, gtv<D>(S, g, n, m - l, kb)), gmat<D>(G, T - l, kb));
+        });
+        c2 = mscal<D>(xi, c2);
+    }
+    if (m >= T - k) {
+        for (int j = 0; j <= k; ++j) {
+            Mat<D> gm = gmat<D>(G, j, kb);
+            for (int l = 0; l <= k; ++l) {
+                Mat<D> s = mscal<D>(W.R[T - m][j][l], gtv<D>(S, g, n, T - l, kb));
+                mfma<D>(c3, s, gm);
+            }
+        }
+    } else {
+        greg_for(W, T - m, T - m, [&](int l, double w) {
+            mfma<D>(c3, mscal<D>(w, gtv<D>(S, g, n, m + l, kb)), gmat<D>(G, l, kb));
+        });
+    }
+    return mscal<D>(g.htau, mmuli<D>(mscal<D>(-1.0, madd<D>(c2, c3))));
+}
+
+// Partial sums of the (A)-source of the lesser column, -i (C^<_2 + C^<_3)[Sigma,1,G](m,n)
+// (Eqs. cles2, cles3), over the terms j = j0, j0+js, ...  (j0 = 0, js = 1 for the full sum).
+template <int D>
+__device__ Mat<D> q_lesA_part(const NgWeights& W, const Grid& g, const HermV& G, const HermV& S, int m,
+                              int n, int kb, int j0, int js) {
+    const int k = W.k, T = g.ntau;
+    Mat<D> c2 = mzero<D>(), c3 = mzero<D>();
+    if (n <= k) {
+        // s weights over j = 0..k with G~^A(j,n) = [G~^R(n,j)]^dagger
+        for (int j = j0; j <= k; j += js)
+            mfma_db<D>(c2, mscal<D>(W.greg[n][j], gles<D>(S, m, j, kb)), gretx<D>(G, n, j, kb));
+    } else {
+        for (int j = j0; j <= n; j += js)
+            mfma_db<D>(c2, mscal<D>(gw(W, n, j), gles<D>(S, m, j, kb)), gret<D>(G, n, j, kb));
+    }
+    for (int j = j0; j <= T; j += js)   // Sigma^tv(m,j) G^vt(j,n), G^vt = -xi [G^tv(n, T-j)]^dag
+        mfma_db<D>(c3, mscal<D>(gw(W, T, j), gtv<D>(S, g, m, j, kb)), gtv<D>(G, g, n, T - j, kb));
+    // -i [h c2 - i htau (-xi) c3] = -i h c2 + xi htau c3
+    return madd<D>(mscal<D>(g.h, mmuli<D>(mscal<D>(-1.0, c2))), mscal<D>((double)g.sig * g.htau, c3));
+}
+
+// ----------------------------------------------------------------------------------------
+// bulk items
+// ----------------------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ void ret_item(const NgWeights& W, const Grid& g, const HermV& G, const HermV& S,
+                                         const Mat<D>& Minv, int n, int m, int kb, int* status) {
+    const int L = n - m;  // > k
+    Mat<D> acc = mzero<D>();
+    greg_for(W, L, L - 1, [&](int l, double w) {
+        mfma<D>(acc, mscal<D>(w, gret<D>(S, n, m + l, kb)), gret<D>(G, m + l, m, kb));
+    });
+    Mat<D> bdf = mzero<D>();
+    for (int l = 1; l <= W.k; ++l) bdf = madd<D>(bdf, mscal<D>(W.a[l], gret<D>(G, n - l, m, kb)));
+    Mat<D> rhs = msub<D>(mscal<D>(-1.0 / g.h, bdf), mscal<D>(g.h, mmuli<D>(acc)));
+    Mat<D> y = mmul<D>(Minv, rhs);
+    if (!mfinite<D>(y)) atomicOr(status, NGF_NONFINITE);
+    st<D>(G.ret, tri(n) + m, kb, y);
+}
+
+template <int D>
+__device__ __forceinline__ void tv_item(const NgWeights& W, const Grid& g, const HermV& G, const HermV& S,
+                                        const Mat<D>& Minv, int n, int m, int kb, int* status) {
+    Mat<D> acc = mzero<D>();
+    greg_for(W, n, n - 1, [&](int j, double w) {
+        mfma<D>(acc, mscal<D>(w, gret<D>(S, n, j, kb)), gtv<D>(G, g, j, m, kb));
+    });
+    Mat<D> bdf = mzero<D>();
+    for (int l = 1; l <= W.k; ++l) bdf = madd<D>(bdf, mscal<D>(W.a[l], gtv<D>(G, g, n - l, m, kb)));
+    Mat<D> rhs = q_tv<D>(W, g, G, S, n, m, kb);
+    rhs = msub<D>(rhs, mscal<D>(1.0 / g.h, bdf));
+    rhs = msub<D>(rhs, mscal<D>(g.h, mmuli<D>(acc)));
+    Mat<D> y = mmul<D>(Minv, rhs);
+    if (!mfinite<D>(y)) atomicOr(status, NGF_NONFINITE);
+    st<D>(G.tv, (int64_t)n * (g.ntau + 1) + m, kb, y);
+}
+
+template <int D>
+__device__ __forceinline__ void les_item(const NgWeights& W, const Grid& g, const HermV& G, const HermV& S,
+                                         const Mat<D>& Minv, int n, int m, int kb, int* status) {
+    const int k = W.k, T = g.ntau;
+    // C^<_1[G,1,Sigma](m,n) = int_0^{t_m} G^R(m,s) Sigma^<(s,n)
+    Mat<D> c1 = mzero<D>();
+    if (m <= k) {
+        for (int j = 0; j <= k; ++j)
+            mfma<D>(c1, mscal<D>(W.greg[m][j], gretx<D>(G, m, j, kb)), ld<D>(S.les, tri(n) + j, kb));
+    } else {
+        greg_for(W, m, m, [&](int j, double w) {
+            mfma<D>(c1, mscal<D>(w, gret<D>(G, m, j, kb)), ld<D>(S.les, tri(n) + j, kb));
+        });
+    }
+    // sum_j w_{T,j} G^tv(m,j) [Sigma^tv(n,T-j)]^dagger ;  C^<_3 = -i htau (-xi) * that
+    Mat<D> c3 = mzero<D>();
+    greg_for(W, T, T, [&](int j, double w) {
+        mfma_db<D>(c3, mscal<D>(w, gtv<D>(G, g, m, j, kb)), gtv<D>(S, g, n, T - j, kb));
+    });
+    // source q = i (C1 + C3) = i h c1 + i (-i htau)(-xi) c3 = i h c1 - xi htau c3
+    Mat<D> q = msub<D>(mscal<D>(g.h, mmuli<D>(c1)), mscal<D>((double)g.sig * g.htau, c3));
+    // history sum_{l<n} w_{n,l} G^<(m,l) [Sigma^R(n,l)]^dagger  (kernel -i Sigma^A(l,n))
+    Mat<D> hist = mzero<D>();
+    greg_for(W, n, n - 1, [&](int l, double w) {
+        Mat<D> gl = (l >= m) ? ld<D>(G.les, tri(l) + m, kb)
+                             : mscal<D>(-1.0, mdag<D>(ld<D>(G.les, tri(m) + l, kb)));
+        mfma_db<D>(hist, mscal<D>(w, gl), gret<D>(S, n, l, kb));
+    });
+    Mat<D> bdf = mzero<D>();
+    for (int l = 1; l <= k; ++l) bdf = madd<D>(bdf, mscal<D>(W.a[l], ld<D>(G.les, tri(n - l) + m, kb)));
+    // rhs = q - bdf/h - h * (-i) hist
+    Mat<D> rhs = msub<D>(q, mscal<D>(1.0 / g.h, bdf));
+    rhs = madd<D>(rhs, mscal<D>(g.h, mmuli<D>(hist)));
+    Mat<D> y = mmul<D>(rhs, mdag<D>(Minv));   // (M_n^dagger)^-1 = (M_n^-1)^dagger
+    if (!mfinite<D>(y)) atomicOr(status, NGF_NONFINITE);
+    st<D>(G.les, tri(n) + m, kb, y);
+}
+
+// One launch for the three independent bulk tasks of step n; blocks [0, nb_les) do the
+// lesser (B) items, then the left-mixing row, then the retarded (B) items.  Items are
+// (column, problem) pairs with the problem index fastest, so a warp reads contiguous
+// problem vectors of each history element.
+template <int D>
+__global__ void __launch_bounds__(128) k_step_bulk(Grid g, int n, HermV G, HermV S, FuncV eps,
+                                                   int nb_les, int nb_tv, int nb_ret, int* status) {
+    const NgWeights& W = c_W[g.k - 1];
+    int blk = blockIdx.x;
+    int task;
+    if (blk < nb_les) task = 0;
+    else if ((blk -= nb_les) < nb_tv) task = 1;
+    else { blk -= nb_tv; task = 2; }
+    const int64_t item = (int64_t)blk * blockDim.x + threadIdx.x;
+    const int kb = (int)(item % g.nb);
+    const int64_t col = item / g.nb;
+    int ncol;
+    if (task == 0) ncol = n - W.k - 1;      // m = 1..n-k-1
+    else if (task == 1) ncol = g.ntau + 1;  // m = 0..ntau
+    else ncol = n - W.k;                    // m = 0..n-k-1
+    if (col >= ncol) return;
+    int sing = 0;
+    Mat<D> Minv = minv<D>(step_matrix<D>(W, g, S, eps, n, kb), &sing);
+    if (sing) atomicOr(status, NGF_SINGULAR);
+    if (task == 0) les_item<D>(W, g, G, S, Minv, n, (int)col + 1, kb, status);
+    else if (task == 1) tv_item<D>(W, g, G, S, Minv, n, (int)col, kb, status);
+    else ret_item<D>(W, g, G, S, Minv, n, (int)col, kb, status);
+}
+
+// ----------------------------------------------------------------------------------------
+// small dense solver (Gaussian elimination with partial pivoting), row-major A[N][N],
+// right-hand sides B[N][nrhs]; one thread.
+// ----------------------------------------------------------------------------------------
+__device__ inline int dense_solve(cplx* A, int N, cplx* B, int nrhs) {
+    for (int c = 0; c < N; ++c) {
+        int p = c;
+        double best = cabs2(A[c * N + c]);
+        for (int r = c + 1; r < N; ++r)
+            if (cabs2(A[r * N + c]) > best) { best = cabs2(A[r * N + c]); p = r; }
+        if (best == 0.0) return 1;
+        if (p != c) {
+            for (int j = 0; j < N; ++j) { cplx t = A[c * N + j]; A[c * N + j] = A[p * N + j]; A[p * N + j] = t; }
+            for (int j = 0; j < nrhs; ++j) { cplx t = B[c * nrhs + j]; B[c * nrhs + j] = B[p * nrhs + j]; B[p * nrhs + j] = t; }
+        }
+        cplx inv = cdiv(cr(1.0), A[c * N + c]);
+        for (int r = c + 1; r < N; ++r) {
+            cplx f = cmul(A[r * N + c], inv);
+            if (f.x == 0.0 && f.y == 0.0) continue;
+            for (int j = c; j < N; ++j) A[r * N + j] = csub(A[r * N + j], cmul(f, A[c * N + j]));
+            for (int j = 0; j < nrhs; ++j) B[r * nrhs + j] = csub(B[r * nrhs + j], cmul(f, B[c * nrhs + j]));
+        }
+    }
+    for (int c = N - 1; c >= 0; --c) {
+        cplx inv = cdiv(cr(1.0), A[c * N + c]);
+        for (int j = 0; j < nrhs; ++j) {
+            cplx s = B[c * nrhs + j];
+            for (int q = c + 1; q < N; ++q) s = csub(s, cmul(A[c * N + q], B[q * nrhs + j]));
+            B[c * nrhs + j] = cmul(s, inv);
+        }
+    }
+    return 0;
+}
+
+// block-wide sum of a Mat<D> in a fixed order (deterministic); result valid in thread 0
+template <int D>
+__device__ Mat<D> block_sum(Mat<D> x, cplx* red /* blockDim.x * D*D */) {
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = 0; b < D; ++b) red[(a * D + b) * blockDim.x + t] = x.v[a][b];
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (t < s)
+#pragma unroll
+            for (int e = 0; e < D * D; ++e)
+                red[e * blockDim.x + t] = cadd(red[e * blockDim.x + t], red[e * blockDim.x + t + s]);
+        __syncthreads();
+    }
+    Mat<D> r;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = 0; b < D; ++b) r.v[a][b] = red[(a * D + b) * blockDim.x];
+    __syncthreads();
+    return r;
+}
+
+#define NG_BND_THREADS 128
+#define NG_MAXQ (2 * NG_KMAX + 1)
+
+// Per-problem boundary of step n: retarded start-up (A) for m = n-k..n, then the lesser
+// column's G^<(0,n) and serial (A) part.  One block per problem.
+template <int D>
+__global__ void __launch_bounds__(NG_BND_THREADS) k_step_boundary(Grid g, int n, HermV G, HermV S, FuncV eps,
+                                                                  int* status) {
+    const NgWeights& W = c_W[g.k - 1];
+    const int k = W.k;
+    const int kb = blockIdx.x;
+    const int t = threadIdx.x;
+    __shared__ cplx red[NG_BND_THREADS * D * D];
+    __shared__ cplx qsrc[NG_MAXQ + 1][D][D];   // sources per boundary row
+    __shared__ cplx hsrc[NG_MAXQ + 1][D][D];   // partial histories per boundary row
+    __shared__ cplx Ash[(NG_KMAX * D) * (NG_KMAX * D)];
+    __shared__ cplx Bsh[(NG_KMAX * D) * D];
+
+    // ---- retarded: conjugate start-up along row n (implementation (A)) -------------
+    if (t == 0) {
+        // unknowns y_1..y_k (y_j = G^R(n, n-j)), y_0 = -i; sum_{l>=1} y_l Mh[l][j] = -y_0 Mh[0][j]
+        // with Mh[l][j] = D_{j,l}/h + delta_{lj} i(eps_{n-j} - mu) + h s_{j,l} i Sigma~^R(n-l, n-j).
+        // Transposed: sum_l Mh[l][j]^T y_l^T = -(y_0 Mh[0][j])^T.
+        const int N = k * D;
+        for (int j = 1; j <= k; ++j) {
+            for (int l = 0; l <= k; ++l) {
+                Mat<D> Mh = meye<D>(cr(W.D[j][l] / g.h));
+                Mh = madd<D>(Mh, mscal<D>(g.h * W.greg[j][l], mmuli<D>(gretx<D>(S, n - l, n - j, kb))));
+                if (l == j) {
+                    Mat<D> e = ldf<D>(eps, n - j, kb);
+                    for (int a = 0; a < D; ++a) e.v[a][a].x -= g.mu;
+                    Mh = madd<D>(Mh, mmuli<D>(e));
+                }
+                if (l == 0) {
+                    Mat<D> r = mmul<D>(meye<D>(make_double2(0.0, -1.0)), Mh);  // y_0 Mh[0][j]
+                    for (int a = 0; a < D; ++a)
+                        for (int c = 0; c < D; ++c) Bsh[((j - 1) * D + a) * D + c] = cneg(r.v[c][a]);
+                } else {
+                    for (int a = 0; a < D; ++a)
+                        for (int b = 0; b < D; ++b) Ash[((j - 1) * D + a) * N + (l - 1) * D + b] = Mh.v[b][a];
+                }
+            }
+        }
+        if (dense_solve(Ash, N, Bsh, D)) atomicOr(status, NGF_SINGULAR);
+        st<D>(G.ret, tri(n) + n, kb, meye<D>(make_double2(0.0, -1.0)));
+        for (int l = 1; l <= k; ++l) {
+            Mat<D> y;
+            for (int a = 0; a < D; ++a)
+                for (int c = 0; c < D; ++c) y.v[c][a] = Bsh[((l - 1) * D + a) * D + c];
+            if (!mfinite<D>(y)) atomicOr(status, NGF_NONFINITE);
+            st<D>(G.ret, tri(n) + n - l, kb, y);
+        }
+        // G^<(0,n) = -[G^tv(n,0)]^dagger  (Eq. dyson_ini_les)
+        st<D>(G.les, tri(n) + 0, kb, mscal<D>(-1.0, mdag<D>(gtv<D>(G, g, n, 0, kb))));
+    }
+    __syncthreads();
+
+    // ---- lesser: rows handled by (A) ------------------------------------------------
+    const bool full = (n <= 2 * k);           // whole column by (A)
+    const int m0 = full ? 1 : n - k;          // first (A) row
+    const int nq = n - m0 + 1;                // number of (A) rows
+    for (int r = 0; r < nq; ++r) {
+        const int m = m0 + r;
+        Mat<D> part = q_lesA_part<D>(W, g, G, S, m, n, kb, t, blockDim.x);
+        Mat<D> q = block_sum<D>(part, red);
+        // partial history over the rows below m0 (known values): sum_{l<m0} w_{m,l} Sigma^R(m,l) G^<(l,n)
+        Mat<D> hp = mzero<D>();
+        if (!full && m > k) {
+            for (int l = t; l < m0; l += blockDim.x)
+                mfma<D>(hp, mscal<D>(gw(W, m, l), gret<D>(S, m, l, kb)), ld<D>(G.les, tri(n) + l, kb));
+        }
+        Mat<D> hsum = block_sum<D>(hp, red);
+        if (t == 0)
+            for (int a = 0; a < D; ++a)
+                for (int b = 0; b < D; ++b) { qsrc[r][a][b] = q.v[a][b]; hsrc[r][a][b] = hsum.v[a][b]; }
+    }
+    __syncthreads();
+    if (t != 0) return;
+    int sing = 0;
+    int mstep = m0;
+    if (full) {
+        // VIDE start-up for m = 1..k (Eq. vdiff_start): sum_l M_{m,l} y_l = q_m - M_{m,0} y_0
+        const int N = k * D;
+        Mat<D> y0 = ld<D>(G.les, tri(n) + 0, kb);
+        for (int m = 1; m <= k; ++m) {
+            Mat<D> e = ldf<D>(eps, m, kb);
+            for (int a = 0; a < D; ++a) e.v[a][a].x -= g.mu;
+            Mat<D> rhs;
+            for (int a = 0; a < D; ++a)
+                for (int b = 0; b < D; ++b) rhs.v[a][b] = qsrc[m - 1][a][b];
+            for (int l = 0; l <= k; ++l) {
+                Mat<D> M = meye<D>(cr(W.D[m][l] / g.h));
+                M = madd<D>(M, mscal<D>(g.h * W.greg[m][l], mmuli<D>(gretx<D>(S, m, l, kb))));
+                if (l == m) M = madd<D>(M, mmuli<D>(e));
+                if (l == 0) rhs = msub<D>(rhs, mmul<D>(M, y0));
+                else
+                    for (int a = 0; a < D; ++a)
+                        for (int b = 0; b < D; ++b) Ash[((m - 1) * D + a) * N + (l - 1) * D + b] = M.v[a][b];
+            }
+            for (int a = 0; a < D; ++a)
+                for (int c = 0; c < D; ++c) Bsh[((m - 1) * D + a) * D + c] = rhs.v[a][c];
+        }
+        if (dense_solve(Ash, N, Bsh, D)) atomicOr(status, NGF_SINGULAR);
+        for (int m = 1; m <= k; ++m) {
+            Mat<D> y;
+            for (int a = 0; a < D; ++a)
+                for (int c = 0; c < D; ++c) y.v[a][c] = Bsh[((m - 1) * D + a) * D + c];
+            if (!mfinite<D>(y)) atomicOr(status, NGF_NONFINITE);
+            st<D>(G.les, tri(n) + m, kb, y);
+        }
+        mstep = k + 1;
+    }
+    // serial VIDE steps (Eq. MBCVSAMx_t) in the first argument, m = mstep..n
+    for (int m = mstep; m <= n; ++m) {
+        const int r = m - m0;
+        Mat<D> acc, h0;
+        for (int a = 0; a < D; ++a)
+            for (int b = 0; b < D; ++b) { acc.v[a][b] = qsrc[r][a][b]; h0.v[a][b] = hsrc[r][a][b]; }
+        const int lfrom = full ? 0 : m0;
+        for (int l = lfrom; l < m; ++l)
+            mfma<D>(h0, mscal<D>(gw(W, m, l), gret<D>(S, m, l, kb)), ld<D>(G.les, tri(n) + l, kb));
+        Mat<D> bdf = mzero<D>();
+        for (int l = 1; l <= k; ++l) bdf = madd<D>(bdf, mscal<D>(W.a[l], ld<D>(G.les, tri(n) + m - l, kb)));
+        acc = msub<D>(acc, mscal<D>(1.0 / g.h, bdf));
+        acc = msub<D>(acc, mscal<D>(g.h, mmuli<D>(h0)));
+        Mat<D> Mm = step_matrix<D>(W, g, S, eps, m, kb);
+        Mat<D> y = mmul<D>(minv<D>(Mm, &sing), acc);
+        if (!mfinite<D>(y)) atomicOr(status, NGF_NONFINITE);
+        st<D>(G.les, tri(n) + m, kb, y);
+    }
+    if (sing) atomicOr(status, NGF_SINGULAR);
+}
