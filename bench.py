@@ -27,10 +27,16 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# FP64 (DFMA) throughput of one GB300 measured with a dependent-chain-free DFMA loop over all
-# SMs (profiles/fp64_peak_gb300.md): 1.195 TFLOP/s; nominal 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz.
-FP64_PEAK_TFLOPS = 1.195
-FP64_PEAK_NOTE = "measured DFMA loop, all 152 SMs (profiles/fp64_peak_gb300.md)"
+# FP64 (DFMA, non-tensor) peak of one GB300 from its unit counts: 152 SMs x 2 DFMA per clock
+# per SM x 2 flop, times the SM clock (1.2586 TFLOP/s at the 2070 MHz maximum, the nominal
+# 1.25 TFLOP/s).  The clock is the median sampled during the timed region.
+GB300_SMS = 152
+FP64_FLOP_PER_CLK_PER_SM = 4
+SM_MAX_MHZ = 2070.0
+
+
+def fp64_peak_tflops(sm_mhz):
+    return GB300_SMS * FP64_FLOP_PER_CLK_PER_SM * (sm_mhz or SM_MAX_MHZ) * 1e6 / 1e12
 
 
 def parse():
@@ -44,6 +50,8 @@ def parse():
     ap.add_argument("--nt", type=int, default=2000)
     ap.add_argument("--ntau", type=int, default=800)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", choices=["f64", "both"], default="both",
+                    help="f64: the FP64 headline only; both: also time the FP32-compensated mode")
     return ap.parse_args()
 
 
@@ -245,30 +253,32 @@ def run_ours(a):
     U.val[:, 0, 0, 0].copy_(U_host, non_blocking=True)
     ctx.run_2b(g, G, L, S, e0, mf, U, corrector=w.corrector, n_from=k + 1, n_to=k, do_setup=True)
 
-    def step(n):
+    def step(n, precision):
         e0.val[n + 1].copy_(eps_host[n + 1], non_blocking=True)            # this step's input
-        ctx.run_2b(g, G, L, S, e0, mf, U, corrector=w.corrector, n_from=n, n_to=n, do_setup=False)
+        ctx.run_2b(g, G, L, S, e0, mf, U, corrector=w.corrector, n_from=n, n_to=n, do_setup=False,
+                   precision=precision)
         rho_host[n].copy_(L.les[les_diag[n], 0, 0, 0], non_blocking=True)  # this step's result
 
-    for n in range(k + 1, n_first_timed - W):
-        step(n)
-    for n in range(n_first_timed - W, n_first_timed):
-        step(n)
-    barrier()
-    clocks = ClockSampler(local)
-    clocks.start()
-    ctx.profile_enable(True)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for n in range(n_first_timed, w.nt + 1):
-        step(n)
-    ev1.record(stream)
-    barrier()
-    t_job1 = time.perf_counter()
-    ctx.profile_enable(False)
-    clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
-    prof = ctx.profile_read()
+    def propagate(precision):
+        """Steps k+1..nt; the last K are timed (CUDA events, synchronised on both sides)."""
+        for n in range(k + 1, n_first_timed):
+            step(n, precision)
+        barrier()
+        clocks = ClockSampler(local)
+        clocks.start()
+        ctx.profile_enable(True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for n in range(n_first_timed, w.nt + 1):
+            step(n, precision)
+        ev1.record(stream)
+        barrier()
+        t_end = time.perf_counter()
+        ctx.profile_enable(False)
+        clk = clocks.stop()
+        return ev0.elapsed_time(ev1), ctx.profile_read(), clk, t_end
+
+    ms, prof, clk, t_job1 = propagate(ng.NG_FP64)
     st, flags = ctx.status_sync()
     if dist:
         t = torch.tensor([ms], device="cuda")
@@ -278,6 +288,7 @@ def run_ours(a):
     e2e_value = world * w.nbatch * (w.nt - k) / (t_job1 - t_job0)
     launches = int(prof["bulk_launches"] + prof["boundary_launches"]) + K * (1 + 3 * 3)
     achieved = prof["bulk_flops"] / (prof["bulk_ms"] / 1e3) / 1e12
+    peak = fp64_peak_tflops(clk.get("sm_mhz"))
     traffic = None
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
@@ -288,7 +299,34 @@ def run_ours(a):
             traffic = tr.get("bulk_bytes_per_launch_timed_window")
     except (OSError, ValueError):
         traffic = None
-    rho = rho_host[k + 1:].numpy()
+    rho = rho_host[k + 1:].numpy().copy()
+    f32c = None
+    if a.precision == "both":
+        # FP32-compensated time steps from the same setup (slices 0..k are not touched by the
+        # stepping), same timed window; error against the FP64 run on the final slice n = nt
+        # (all k-points, ret row / les column / tv row) and on rho_loc(t) for every t.
+        nt = w.nt
+        ref = {"ret": G.ret[ng.tri(nt):ng.tri(nt) + nt + 1].clone(), "les": G.les[ng.tri(nt):ng.tri(nt) + nt + 1].clone(),
+               "tv": G.tv[nt * (w.ntau + 1):(nt + 1) * (w.ntau + 1)].clone()}
+        ms32, prof32, clk32, _ = propagate(ng.NG_F32C)
+        st32, flags32 = ctx.status_sync()
+        err = {}
+        for c, r in ref.items():
+            x = {"ret": G.ret[ng.tri(nt):ng.tri(nt) + nt + 1], "les": G.les[ng.tri(nt):ng.tri(nt) + nt + 1],
+                 "tv": G.tv[nt * (w.ntau + 1):(nt + 1) * (w.ntau + 1)]}[c]
+            err[c] = float((x - r).abs().max() / r.abs().max())
+        rho32 = rho_host[k + 1:].numpy()
+        err["rho_loc_abs"] = float(np.abs(rho32 - rho).max())
+        v32 = world * w.nbatch * K / (ms32 / 1e3)
+        ach32 = prof32["bulk_flops"] / (prof32["bulk_ms"] / 1e3) / 1e12
+        f32c = {"value": v32, "unit": "k-point timesteps/s", "ms_per_step": ms32 / K, "dtype": "f32c",
+                "speedup_vs_f64": v32 / (world * w.nbatch * K / (ms / 1e3)),
+                "max_rel_err_vs_f64_final_slice": err,
+                "bulk_kernel": {"kernel": "k_step_bulk32<1>", "algorithmic_fp64_equiv_tflops": ach32,
+                                "avg_launch_ms": prof32["bulk_ms"] / max(1, prof32["bulk_launches"]),
+                                "share_of_timed": prof32["bulk_ms"] / ms32,
+                                "history_gbs": prof32["bulk_flops"] / 8.0 * 8.0 / (prof32["bulk_ms"] / 1e3) / 1e9},
+                "clocks": clk32, "device_status": {"status": st32, "flags": flags32}}
     if rank != 0:
         return
     line = {
@@ -300,9 +338,10 @@ def run_ours(a):
                 "d2h_bytes_per_step": d2h_bytes,
                 "scope": "whole job through the public API: setup (Matsubara loop, bootstrapping) and every "
                          "time step, per-step H2D of eps_k(t_n) from pinned host memory and D2H of rho_loc(t_n)"},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": "k_step_bulk<1>",
-                     "peak_source": FP64_PEAK_NOTE,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": "k_step_bulk<1>",
+                     "peak_source": f"FP64 DFMA from unit counts: {GB300_SMS} SMs x {FP64_FLOP_PER_CLK_PER_SM} "
+                                    f"flop/clk x median SM clock {clk.get('sm_mhz')} MHz",
                      "avg_launch_ms": prof["bulk_ms"] / max(1, prof["bulk_launches"]),
                      "share_of_timed": prof["bulk_ms"] / ms},
         "gpu_launches": launches, "clocks": clk,
@@ -310,6 +349,8 @@ def run_ours(a):
         "observables": {"N_loc_first_timed": float(np.real(-1j * rho[n_first_timed - k - 1])),
                         "N_loc_last": float(np.real(-1j * rho[-1]))},
     }
+    if f32c is not None:
+        line["f32c"] = f32c
     if world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, list(range(n_first_timed, w.nt + 1)))
     print(json.dumps(line), flush=True)
