@@ -87,7 +87,11 @@ typedef struct {
     int ldk;                     /* nbatch or 1                                          */
 } ng_func;
 
-typedef enum { NG_FP64 = 0 } ng_precision;
+/* NG_FP64: every sum in FP64.  NG_F32C: the O(n) and O(ntau) history and source sums of the
+ * time step read FP32 copies of the history and accumulate exact FP32 products with Kahan
+ * compensation (rounded once to FP64); BDF terms, the per-step matrix inverses, the (A)
+ * boundary steps, the start-up and the Matsubara solve stay FP64. */
+typedef enum { NG_FP64 = 0, NG_F32C = 1 } ng_precision;
 
 /* Parameters of the self-consistent second-Born driver (ng_run_2b). */
 typedef struct {
@@ -100,6 +104,7 @@ typedef struct {
     int n_from;          /* first time step to propagate (k+1 for a full run)             */
     int n_to;            /* last time step to propagate (<= nt)                            */
     int do_setup;        /* 1: run the Matsubara loop and bootstrapping first              */
+    int precision;       /* ng_precision of the time steps                                   */
 } ng_run_params;
 
 /* ---- context ------------------------------------------------------------------------ */
@@ -158,9 +163,16 @@ ng_status ng_dyson_start(ng_ctx *ctx, const ng_grid *grid, ng_herm G, ng_herm Si
  * step per tau_m; lesser column by conjugate single steps for 1 <= m <= tstp-k-1 (B) and
  * serial VIDE steps (A) for m >= tstp-k (the whole column by (A) when tstp <= 2k).
  * Reads slices < tstp of G, slices <= tstp of Sigma and eps; writes slice tstp of G.
- * precision must be NG_FP64. */
+ * precision: NG_FP64 or NG_F32C.  With NG_F32C the context keeps FP32 copies of G (ldk =
+ * nbatch) and Sigma: slices < tstp are converted once when tstp first reaches them, Sigma's
+ * slice tstp on every call.  Call ng_precision_reset after changing slices < tstp of G or
+ * Sigma in place (the copies are also rebuilt when the buffers or the grid change).
+ * Workspace: 8 bytes per complex element of G and Sigma. */
 ng_status ng_dyson_timestep(ng_ctx *ctx, const ng_grid *grid, int tstp, ng_herm G,
                             ng_herm Sigma, ng_func eps, int precision, void *stream);
+
+/* Forget the FP32 copies kept for NG_F32C time steps (they are rebuilt on the next call). */
+ng_status ng_precision_reset(ng_ctx *ctx);
 
 /* ---- slice operations ----------------------------------------------------------------- */
 

@@ -22,7 +22,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libng.so")
 
 NG_OK, NG_EINVAL, NG_ENOMEM, NG_ECUDA, NG_ENOCONV, NG_ETIMEOUT, NG_ENONFINITE, NG_EUNSUPPORTED = range(8)
-NG_FP64 = 0
+NG_FP64, NG_F32C = 0, 1
 _STATUS_NAMES = ["NG_OK", "NG_EINVAL", "NG_ENOMEM", "NG_ECUDA", "NG_ENOCONV", "NG_ETIMEOUT",
                  "NG_ENONFINITE", "NG_EUNSUPPORTED"]
 
@@ -51,7 +51,8 @@ class ng_func(ctypes.Structure):
 class ng_run_params(ctypes.Structure):
     _fields_ = [("corrector", ctypes.c_int), ("mats_tol", ctypes.c_double), ("mats_maxiter", ctypes.c_int),
                 ("boot_tol", ctypes.c_double), ("boot_maxiter", ctypes.c_int), ("nbar", ctypes.c_double),
-                ("n_from", ctypes.c_int), ("n_to", ctypes.c_int), ("do_setup", ctypes.c_int)]
+                ("n_from", ctypes.c_int), ("n_to", ctypes.c_int), ("do_setup", ctypes.c_int),
+                ("precision", ctypes.c_int)]
 
 
 # every symbol the header declares, with its ctypes signature
@@ -76,6 +77,7 @@ SIGNATURES = {
     "ng_run_2b": (ctypes.c_int, [_P, _G, ng_herm, ng_herm, ng_herm, ng_func, ng_func, ng_func,
                                  ctypes.POINTER(ng_run_params), ctypes.POINTER(ctypes.c_int), _P]),
     "ng_solve_fixed": (ctypes.c_int, [_P, _G, ng_herm, ng_herm, ng_func, ctypes.c_int, _P]),
+    "ng_precision_reset": (ctypes.c_int, [_P]),
     "ng_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "ng_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
 }
@@ -197,6 +199,9 @@ class Context:
         self._chk(self.lib.ng_weights(self.h, out))
         return list(out)
 
+    def precision_reset(self):
+        self._chk(self.lib.ng_precision_reset(self.h))
+
     def profile_enable(self, on=True):
         self._chk(self.lib.ng_profile_enable(self.h, 1 if on else 0))
 
@@ -253,10 +258,10 @@ class Context:
 
     def run_2b(self, grid, G, Gloc, S, eps0, eps_mf, U, corrector=3, mats_tol=1e-12, mats_maxiter=200,
                boot_tol=1e-12, boot_maxiter=200, nbar=0.5, n_from=None, n_to=None, do_setup=True,
-               stream=None, allow_noconv=False):
+               stream=None, allow_noconv=False, precision=NG_FP64):
         p = ng_run_params(corrector, mats_tol, mats_maxiter, boot_tol, boot_maxiter, nbar,
                           grid.korder + 1 if n_from is None else n_from,
-                          grid.nt if n_to is None else n_to, 1 if do_setup else 0)
+                          grid.nt if n_to is None else n_to, 1 if do_setup else 0, precision)
         iters = (ctypes.c_int * 2)()
         st = self.lib.ng_run_2b(self.h, ctypes.byref(grid.c()), G.c(), Gloc.c(), S.c(), eps0.c(), eps_mf.c(), U.c(),
                                 ctypes.byref(p), iters, _stream(stream))

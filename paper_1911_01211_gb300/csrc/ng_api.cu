@@ -1,4 +1,5 @@
 // C ABI of libng (include/ng.h): argument validation, workspaces and kernel launches.
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -7,6 +8,18 @@
 #include "../../include/ng.h"
 #include "ng_setup.cuh"
 #include "ng_slice.cuh"
+#include "ng_step32.cuh"
+
+// FP32 copy of one contour function (NG_F32C time steps): the buffer, the identity of the
+// FP64 source it mirrors and the last slice converted (-2: nothing, -1: mat only).
+struct Shadow {
+    void* buf = nullptr;
+    size_t bytes = 0;
+    const void* key_ret = nullptr;
+    int key_nt = -1, key_ntau = -1, key_nf = -1, key_ldk = -1;
+    int upto = -2;
+    HermV32 v;
+};
 
 
 struct ng_ctx {
@@ -30,6 +43,7 @@ struct ng_ctx {
     size_t ev_used = 0;
     double prof_flops = 0.0;
     std::vector<int> ev_kind;        // 0 bulk, 1 boundary, per event pair
+    Shadow shG, shS;                 // FP32 copies of G and Sigma for NG_F32C
 };
 
 namespace {
@@ -185,6 +199,70 @@ ng_status launch_timestep(ng_ctx* c, const Grid& g, int n, const HermV& G, const
     return check_launch(c, "k_step_boundary");
 }
 
+// Bring the FP32 copy of X up to date for a time step at n: slices <= n-1 once (they are
+// final), slice n always when `current` (Sigma's slice n changes between corrector passes).
+ng_status update_shadow(ng_ctx* c, Shadow& sh, const Grid& g, const HermV& X, int n, bool current, cudaStream_t s) {
+    const int dd = g.nf * g.nf, ldk = X.ret.ldk, T1 = g.ntau + 1;
+    if (sh.key_ret != X.ret.p || sh.key_nt != g.nt || sh.key_ntau != g.ntau || sh.key_nf != g.nf || sh.key_ldk != ldk) {
+        const size_t el = (size_t)T1 + 2 * (size_t)tri(g.nt + 1) + (size_t)(g.nt + 1) * T1;
+        ng_status st = ensure(c, &sh.buf, &sh.bytes, sizeof(cplx32) * el * dd * ldk);
+        if (st) return st;
+        cplx32* p = (cplx32*)sh.buf;
+        sh.v.mat = Comp32{p, ldk};
+        sh.v.ret = Comp32{p + (size_t)T1 * dd * ldk, ldk};
+        sh.v.les = Comp32{sh.v.ret.p + (size_t)tri(g.nt + 1) * dd * ldk, ldk};
+        sh.v.tv = Comp32{sh.v.les.p + (size_t)tri(g.nt + 1) * dd * ldk, ldk};
+        sh.key_ret = X.ret.p;
+        sh.key_nt = g.nt;
+        sh.key_ntau = g.ntau;
+        sh.key_nf = g.nf;
+        sh.key_ldk = ldk;
+        sh.upto = -2;
+    }
+    auto conv = [&](int n0, int n1) -> ng_status {
+        if (n1 < n0 || n1 < -1) return NG_OK;
+        const int a = n0 < 0 ? 0 : n0;
+        const int64_t items = (2 * (tri(n1 + 1) - tri(a)) + (int64_t)(n1 - a + 1) * T1 + (n0 < 0 ? T1 : 0)) * dd * ldk;
+        const unsigned blocks = (unsigned)std::min<int64_t>((items + 255) / 256, 152 * 16);
+        k_shadow<<<blocks, 256, 0, s>>>(g, n0, n1, X, sh.v, ldk);
+        return check_launch(c, "k_shadow");
+    };
+    ng_status st;
+    if (sh.upto < n - 1) {
+        if ((st = conv(sh.upto + 1, n - 1))) return st;
+        sh.upto = n - 1;
+    }
+    if (current && (st = conv(n, n))) return st;
+    return NG_OK;
+}
+
+template <int D>
+ng_status launch_timestep32(ng_ctx* c, const Grid& g, int n, const HermV& G, const HermV& S, const FuncV& eps,
+                            cudaStream_t s) {
+    ng_status st;
+    if ((st = update_shadow(c, c->shG, g, G, n, false, s))) return st;
+    if ((st = update_shadow(c, c->shS, g, S, n, true, s))) return st;
+    const int k = g.k, thr = 128;
+    const int64_t it_les = (n >= 2 * k + 1) ? (int64_t)g.nb * (n - k - 1) : 0;
+    const int64_t it_tv = (int64_t)g.nb * (g.ntau + 1);
+    const int64_t it_ret = (int64_t)g.nb * (n - k);
+    const int b_les = (int)nblocks(it_les, thr), b_tv = (int)nblocks(it_tv, thr), b_ret = (int)nblocks(it_ret, thr);
+    long e0 = prof_pair(c, 0);
+    if (e0 >= 0) cudaEventRecord(c->ev_pool[e0], s);
+    k_step_bulk32<D><<<b_les + b_tv + b_ret, thr, 0, s>>>(g, n, G, S, c->shG.v, c->shS.v, eps, b_les, b_tv, b_ret,
+                                                          c->d_status);
+    if ((st = check_launch(c, "k_step_bulk32"))) return st;
+    if (e0 >= 0) {
+        cudaEventRecord(c->ev_pool[e0 + 1], s);
+        c->prof_flops += 8.0 * D * D * D * bulk_cmacs(g, n);
+    }
+    long e1 = prof_pair(c, 1);
+    if (e1 >= 0) cudaEventRecord(c->ev_pool[e1], s);
+    k_step_boundary<D><<<g.nb, NG_BND_THREADS, 0, s>>>(g, n, G, S, eps, c->d_status);
+    if (e1 >= 0) cudaEventRecord(c->ev_pool[e1 + 1], s);
+    return check_launch(c, "k_step_boundary");
+}
+
 template <int D>
 ng_status launch_mat(ng_ctx* c, const Grid& g, const HermV& G, const HermV& S, const FuncV& eps, cudaStream_t s) {
     const int T = g.ntau, N = (T + 1) * D, ld = N + D;
@@ -249,7 +327,10 @@ ng_status do_hartree(ng_ctx* c, const Grid& g, int tstp, const FuncV& mf, const 
     k_hartree<<<nblocks((int64_t)mf.ldk * g.nf * g.nf, 128), 128, 0, s>>>(g, tstp, mf, e0, L, U, nbar);
     return check_launch(c, "k_hartree");
 }
-ng_status do_timestep(ng_ctx* c, const Grid& g, int n, const HermV& G, const HermV& S, const FuncV& eps, cudaStream_t s) {
+ng_status do_timestep(ng_ctx* c, const Grid& g, int n, const HermV& G, const HermV& S, const FuncV& eps, cudaStream_t s,
+                      int precision = NG_FP64) {
+    if (precision == NG_F32C)
+        return g.nf == 1 ? launch_timestep32<1>(c, g, n, G, S, eps, s) : launch_timestep32<2>(c, g, n, G, S, eps, s);
     return g.nf == 1 ? launch_timestep<1>(c, g, n, G, S, eps, s) : launch_timestep<2>(c, g, n, G, S, eps, s);
 }
 ng_status do_mat(ng_ctx* c, const Grid& g, const HermV& G, const HermV& S, const FuncV& eps, cudaStream_t s) {
@@ -311,6 +392,8 @@ void ng_destroy(ng_ctx* c) {
     cudaFree(c->ws_mat);
     cudaFree(c->ws_st);
     cudaFree(c->ws_prev);
+    cudaFree(c->shG.buf);
+    cudaFree(c->shS.buf);
     delete c;
 }
 
@@ -410,11 +493,20 @@ ng_status ng_dyson_timestep(ng_ctx* c, const ng_grid* grid, int tstp, ng_herm G,
     ng_status st;
     if ((st = check_grid(c, grid, &g))) return st;
     if (tstp <= g.k || tstp > g.nt) return fail(c, NG_EINVAL, "tstp = %d must be in k+1..nt = %d..%d", tstp, g.k + 1, g.nt);
-    if (precision != NG_FP64) return fail(c, NG_EUNSUPPORTED, "precision %d is not available", precision);
+    if (precision != NG_FP64 && precision != NG_F32C) return fail(c, NG_EINVAL, "unknown precision %d", precision);
     if ((st = check_herm(c, g, G, "G", true, &Gv, g.nb))) return st;
     if ((st = check_herm(c, g, S, "Sigma", true, &Sv, 0))) return st;
     if ((st = check_func(c, g, eps, "eps", &ev))) return st;
-    return do_timestep(c, g, tstp, Gv, Sv, ev, (cudaStream_t)stream);
+    return do_timestep(c, g, tstp, Gv, Sv, ev, (cudaStream_t)stream, precision);
+}
+
+ng_status ng_precision_reset(ng_ctx* c) {
+    if (!c) return NG_EINVAL;
+    c->shG.upto = -2;
+    c->shG.key_ret = nullptr;
+    c->shS.upto = -2;
+    c->shS.key_ret = nullptr;
+    return NG_OK;
 }
 
 ng_status ng_kreduce_timestep(ng_ctx* c, const ng_grid* grid, int tstp, ng_herm Gloc, ng_herm Gk, void* stream) {
@@ -519,6 +611,7 @@ ng_status ng_run_2b(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm Gloc, ng_
     if (U.ldk != 1) return fail(c, NG_EINVAL, "U.ldk must be 1");
     if (epsmf.ldk != G.ldk) return fail(c, NG_EINVAL, "eps_mf.ldk must equal G.ldk");
     if (p->corrector < 1) return fail(c, NG_EINVAL, "corrector must be >= 1");
+    if (p->precision != NG_FP64 && p->precision != NG_F32C) return fail(c, NG_EINVAL, "unknown precision %d", p->precision);
     if (p->n_to > g.nt || (p->n_to >= p->n_from && p->n_from <= g.k))
         return fail(c, NG_EINVAL, "stepping range %d..%d invalid (k = %d, nt = %d)", p->n_from, p->n_to, g.k, g.nt);
     cudaStream_t s = (cudaStream_t)stream;
@@ -593,7 +686,7 @@ ng_status ng_run_2b(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm Gloc, ng_
             if ((st = do_kreduce(c, g, n, Lv, Gv, s))) return st;
             if ((st = do_hartree(c, g, n, mf, e0, Lv, uv, p->nbar, s))) return st;
             if ((st = do_sigma(c, g, n, Sv, Lv, uv, s))) return st;
-            if ((st = do_timestep(c, g, n, Gv, Sv, mf, s))) return st;
+            if ((st = do_timestep(c, g, n, Gv, Sv, mf, s, p->precision))) return st;
         }
     }
     if (iters_out) {
