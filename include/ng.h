@@ -56,7 +56,9 @@ typedef enum {
     NG_ENOCONV = 4,       /* a self-consistency loop hit its iteration limit             */
     NG_ETIMEOUT = 5,      /* reserved: a bounded device wait gave up                     */
     NG_ENONFINITE = 6,    /* a non-finite value was produced (device status word)        */
-    NG_EUNSUPPORTED = 7   /* valid but not implemented here (e.g. nf > 2)                */
+    NG_EUNSUPPORTED = 7,  /* valid but not implemented here (e.g. nf > 2)                */
+    NG_ESCRATCH = 8       /* the problem needs more than the fixed static scratch of the  */
+                          /* allocation-free entry point (nothing launched)              */
 } ng_status;
 
 /* device status word bits (ng_status_sync) */
@@ -170,6 +172,34 @@ ng_status ng_dyson_start(ng_ctx *ctx, const ng_grid *grid, ng_herm G, ng_herm Si
  * Workspace: 8 bytes per complex element of G and Sigma. */
 ng_status ng_dyson_timestep(ng_ctx *ctx, const ng_grid *grid, int tstp, ng_herm G,
                             ng_herm Sigma, ng_func eps, int precision, void *stream);
+
+/* Allocation-free start-up: the same computation as ng_dyson_start, for callers that must
+ * not allocate device memory.  Examples: a host application whose caching allocator already
+ * owns all free device memory (a cudaMalloc would fail, or fragment that pool); a latency-
+ * critical loop that cannot afford cudaFree's implicit device synchronisation; a plug-in
+ * whose host forbids libraries from managing device memory.  The paper has no counterpart to
+ * this entry point.
+ *  - No context is needed and none is created.  The start-up workspace (the inverted
+ *    (k nf)^2 start-up matrix and k blocks of nf x nf per problem) lives in one file-scope
+ *    static device array of NG_NOALLOC_SCRATCH_BYTES = 2 MiB, which every GPU that loads the
+ *    library holds until the process exits; its first 256 bytes hold a status word.
+ *  - Size limit: the call needs 256 + 16 nbatch ((k nf)^2 + k nf^2) bytes and returns
+ *    NG_ESCRATCH, launching nothing, above 2 MiB (at k = 5: at most 4369 problems with nf = 1,
+ *    1092 with nf = 2).  Other argument errors return NG_EINVAL / NG_EUNSUPPORTED.
+ *  - It calls no cudaMalloc, cudaFree or allocating library routine.
+ *  - The first call on a device does one-time set-up with that device current: it copies the
+ *    integration weights to constant memory (unless ng_create already did on that device) and
+ *    looks up the array's device address with cudaGetSymbolAddress.  Make that first call from
+ *    one host thread, before any stream capture.
+ *  - Every call uses the same array and leaves its contents there; the status word is cleared
+ *    at the start of each call, and everything else is written before it is read.  Calls whose
+ *    work overlaps on the GPU (different streams, or concurrent host threads) race on the
+ *    array: serialise them.
+ *  - Device-side flags (non-finite values, a singular start-up matrix) land in the array's
+ *    status word and are not reported.
+ * Arguments as for ng_dyson_start (G with ldk = nbatch; Sigma and eps with ldk = 1 or
+ * nbatch); runs on the device that is current when it is called, stream-ordered on `stream`. */
+ng_status ng_dyson_start_noalloc(const ng_grid *grid, ng_herm G, ng_herm Sigma, ng_func eps, void *stream);
 
 /* Forget the FP32 copies kept for NG_F32C time steps (they are rebuilt on the next call). */
 ng_status ng_precision_reset(ng_ctx *ctx);

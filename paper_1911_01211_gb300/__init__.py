@@ -21,15 +21,15 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libng.so")
 
-NG_OK, NG_EINVAL, NG_ENOMEM, NG_ECUDA, NG_ENOCONV, NG_ETIMEOUT, NG_ENONFINITE, NG_EUNSUPPORTED = range(8)
+NG_OK, NG_EINVAL, NG_ENOMEM, NG_ECUDA, NG_ENOCONV, NG_ETIMEOUT, NG_ENONFINITE, NG_EUNSUPPORTED, NG_ESCRATCH = range(9)
 NG_FP64, NG_F32C = 0, 1
 _STATUS_NAMES = ["NG_OK", "NG_EINVAL", "NG_ENOMEM", "NG_ECUDA", "NG_ENOCONV", "NG_ETIMEOUT",
-                 "NG_ENONFINITE", "NG_EUNSUPPORTED"]
+                 "NG_ENONFINITE", "NG_EUNSUPPORTED", "NG_ESCRATCH"]
 
 
 class NgError(RuntimeError):
     def __init__(self, status, msg):
-        super().__init__(f"{_STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        super().__init__(f"{_STATUS_NAMES[status] if 0 <= status < len(_STATUS_NAMES) else status}: {msg}")
         self.status = status
 
 
@@ -78,6 +78,7 @@ SIGNATURES = {
                                  ctypes.POINTER(ng_run_params), ctypes.POINTER(ctypes.c_int), _P]),
     "ng_solve_fixed": (ctypes.c_int, [_P, _G, ng_herm, ng_herm, ng_func, ctypes.c_int, _P]),
     "ng_precision_reset": (ctypes.c_int, [_P]),
+    "ng_dyson_start_noalloc": (ctypes.c_int, [_G, ng_herm, ng_herm, ng_func, _P]),
     "ng_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "ng_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
 }
@@ -159,6 +160,14 @@ class Func:
 
     def c(self):
         return ng_func(self.val.data_ptr(), self.ldk)
+
+
+def dyson_start_noalloc(grid, G, S, eps, stream=None):
+    """ng_dyson_start_noalloc: the start-up slices without any device allocation (no context;
+    fixed 2 MiB static device scratch).  Returns the ng_status code (NG_ESCRATCH when the
+    problem does not fit the static scratch)."""
+    lib = load_library()
+    return lib.ng_dyson_start_noalloc(ctypes.byref(grid.c()), G.c(), S.c(), eps.c(), _stream(stream))
 
 
 def _stream(stream):

@@ -698,3 +698,86 @@ ng_status ng_run_2b(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm Gloc, ng_
 }
 
 }  // extern "C"
+
+// =========================================================================================
+// Allocation-free start-up (ng_dyson_start_noalloc): the start-up workspace is a file-scope
+// static device array instead of context-owned memory; the kernels are those of
+// ng_dyson_start.
+// =========================================================================================
+#define NG_NOALLOC_SCRATCH_BYTES (2u << 20)
+#define NG_NOALLOC_STATUS_BYTES 256u
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NG_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+// device address of g_noalloc_scratch per device, looked up once with that device current
+void* g_noalloc_addr[64] = {nullptr};
+
+template <int D>
+ng_status noalloc_start(const Grid& g, const HermV& G, const HermV& S, const FuncV& eps, cplx* ws, int* status,
+                        cudaStream_t s) {
+    k_start_ret<D><<<nblocks(g.nb, 64), 64, 0, s>>>(g, G, S, eps, ws, status);
+    if (cudaGetLastError() != cudaSuccess) return NG_ECUDA;
+    k_start_tv<D><<<nblocks((int64_t)(g.ntau + 1) * g.nb, 128), 128, 0, s>>>(g, G, S, ws, status);
+    if (cudaGetLastError() != cudaSuccess) return NG_ECUDA;
+    k_start_les<D><<<nblocks((int64_t)(g.k + 1) * g.nb, 64), 64, 0, s>>>(g, G, S, ws, status);
+    if (cudaGetLastError() != cudaSuccess) return NG_ECUDA;
+    return NG_OK;
+}
+}  // namespace
+
+extern "C" ng_status ng_dyson_start_noalloc(const ng_grid* grid, ng_herm G, ng_herm S, ng_func eps, void* stream) {
+    // argument checks (no context, so status codes only)
+    if (!grid) return NG_EINVAL;
+    const ng_grid& q = *grid;
+    if (q.korder < 1 || q.korder > NG_KMAX || q.sig != -1 || q.nbatch < 1 || !(q.h > 0.0) || !(q.beta > 0.0))
+        return NG_EINVAL;
+    if (q.nt < 2 * q.korder + 2 || q.ntau < 2 * q.korder + 2 || q.nf < 1) return NG_EINVAL;
+    if (q.nf > 2) return NG_EUNSUPPORTED;
+    if (G.ldk != q.nbatch || (S.ldk != 1 && S.ldk != q.nbatch) || (eps.ldk != 1 && eps.ldk != q.nbatch))
+        return NG_EINVAL;
+    const void* ptrs[] = {G.mat, G.ret, G.les, G.tv, S.mat, S.ret, S.les, S.tv, eps.val};
+    for (const void* p : ptrs)
+        if (!p || !aligned16(p)) return NG_EINVAL;
+    const size_t N = (size_t)q.korder * q.nf;
+    const size_t need =
+        NG_NOALLOC_STATUS_BYTES + sizeof(cplx) * (size_t)q.nbatch * (N * N + (size_t)q.korder * q.nf * q.nf);
+    if (need > NG_NOALLOC_SCRATCH_BYTES) return NG_ESCRATCH;
+    // one-time set-up per device, with that device current
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return NG_ECUDA; }
+    if (dev < 0 || dev >= 64) return NG_EUNSUPPORTED;
+    if (!g_weights_loaded[dev]) {
+        NgWeights all[NG_KMAX];
+        for (int k = 1; k <= NG_KMAX; ++k) ng_make_weights(k, &all[k - 1]);
+        if (cudaMemcpyToSymbol(c_W, all, sizeof(all)) != cudaSuccess) { cudaGetLastError(); return NG_ECUDA; }
+        g_weights_loaded[dev] = true;
+    }
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) { cudaGetLastError(); return NG_ECUDA; }
+        g_noalloc_addr[dev] = p;
+    }
+    Grid g;
+    g.nt = q.nt;
+    g.ntau = q.ntau;
+    g.nf = q.nf;
+    g.nb = q.nbatch;
+    g.k = q.korder;
+    g.sig = q.sig;
+    g.h = q.h;
+    g.beta = q.beta;
+    g.mu = q.mu;
+    g.htau = q.beta / q.ntau;
+    const int dd = q.nf * q.nf;
+    HermV Gv{Comp{(cplx*)G.mat, G.ldk, dd}, Comp{(cplx*)G.ret, G.ldk, dd}, Comp{(cplx*)G.les, G.ldk, dd},
+             Comp{(cplx*)G.tv, G.ldk, dd}};
+    HermV Sv{Comp{(cplx*)S.mat, S.ldk, dd}, Comp{(cplx*)S.ret, S.ldk, dd}, Comp{(cplx*)S.les, S.ldk, dd},
+             Comp{(cplx*)S.tv, S.ldk, dd}};
+    FuncV ev{(cplx*)eps.val, eps.ldk};
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned char* base = (unsigned char*)g_noalloc_addr[dev];
+    int* status = (int*)base;
+    cplx* ws = (cplx*)(base + NG_NOALLOC_STATUS_BYTES);
+    if (cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess) { cudaGetLastError(); return NG_ECUDA; }
+    return q.nf == 1 ? noalloc_start<1>(g, Gv, Sv, ev, ws, status, s) : noalloc_start<2>(g, Gv, Sv, ev, ws, status, s);
+}
