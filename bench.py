@@ -295,11 +295,27 @@ def run_ours(a):
             tr = json.load(f)
         src = open(os.path.join(ROOT, "paper_1911_01211_gb300", "csrc", "ng_step.cuh"), "rb").read()
         import hashlib
-        if tr.get("ng_step_sha1") == hashlib.sha1(src).hexdigest():
+        window = f"nk={w.nbatch} nt={w.nt} ntau={w.ntau} n={n_first_timed}..{w.nt}"
+        if tr.get("ng_step_sha1") == hashlib.sha1(src).hexdigest() and tr.get("window") == window:
             traffic = tr.get("bulk_bytes_per_launch_timed_window")
     except (OSError, ValueError):
         traffic = None
     rho = rho_host[k + 1:].numpy().copy()
+    # properties that hold at any size: particle number conserved for all t; Galitskii-Migdal
+    # total energy conserved once the pulse has decayed (t >= 10: A(t) < 1e-5)
+    obs = torch.zeros(5, dtype=torch.float64, device="cuda")
+    n_after = [n for n in range(k + 1, w.nt + 1) if n * w.h >= 10.0]
+    sample_n = sorted(set([k + 1] + list(range(k + 1, w.nt + 1, max(1, (w.nt - k) // 20))) + [w.nt]))
+    vals = {}
+    for n in sorted(set(sample_n + n_after[:: max(1, len(n_after) // 20)] + ([n_after[-1]] if n_after else []))):
+        ctx.observables(g, n, G, S, e0, mf, obs)
+        vals[n] = obs.cpu().numpy().copy()
+    Ns = np.array([v[0] for v in vals.values()])
+    Eafter = np.array([vals[n][4] for n in vals if n * w.h >= 10.0])
+    properties = {"N_drift_all_t": float(np.ptp(Ns)), "N_mean": float(Ns.mean()),
+                  "E_tot_drift_after_pulse": float(np.ptp(Eafter)) if len(Eafter) else None,
+                  "E_tot_at_end": float(vals[w.nt][4]), "E_kin_at_end": float(vals[w.nt][1]),
+                  "E_corr_at_end": float(vals[w.nt][3]), "samples": len(vals)}
     f32c = None
     if a.precision == "both":
         # FP32-compensated time steps from the same setup (slices 0..k are not touched by the
@@ -348,6 +364,7 @@ def run_ours(a):
         "device_status": {"status": st, "flags": flags},
         "observables": {"N_loc_first_timed": float(np.real(-1j * rho[n_first_timed - k - 1])),
                         "N_loc_last": float(np.real(-1j * rho[-1]))},
+        "properties": properties,
     }
     if f32c is not None:
         line["f32c"] = f32c

@@ -236,6 +236,17 @@ ng_status ng_extrapolate_timestep(ng_ctx *ctx, const ng_grid *grid, int tstp, ng
 ng_status ng_distance_timestep(ng_ctx *ctx, const ng_grid *grid, int tstp, ng_herm A,
                                ng_herm B, double *out_dev, void *stream);
 
+/* Observables of time slice tstp (0..nt), averaged over the batch (per spin):
+ * out_dev[0] = N = Tr rho, rho(t) = -i G^<(t,t) (Sec. "Hubbard chain", density_matrix);
+ * out_dev[1] = E_kin = Tr[rho eps0(t)] (k-space kinetic energy);
+ * out_dev[2] = E_mf = 1/2 Tr[rho (eps_mf(t) - eps0(t))] (Hartree part);
+ * out_dev[3] = E_corr = 1/2 Im Tr[Sigma * G]^<(t,t) from C^<_1 + C^<_2 + C^<_3 (Eqs. cles1-3);
+ * out_dev[4] = E_kin + E_mf + E_corr, the Galitskii-Migdal total energy (Eq. Total_ener).
+ * G: ldk = nbatch; Sigma: ldk 1 or nbatch; eps0, eps_mf: ldk nbatch (or 1).  out_dev is a
+ * device array of 5 doubles.  Deterministic (fixed-order batch sum).  Workspace 40 nbatch bytes. */
+ng_status ng_observables(ng_ctx *ctx, const ng_grid *grid, int tstp, ng_herm G, ng_herm Sigma, ng_func eps0,
+                         ng_func eps_mf, double *out_dev, void *stream);
+
 /* ---- measurement ---------------------------------------------------------------------- */
 
 /* Start (enable = 1, clearing any previous record) or stop (enable = 0) per-launch timing of

@@ -65,7 +65,8 @@ def run_2b(eps0, U, nt, ntau, beta, h, W, mu=0.0, nbar=0.5, corrector=3, schedul
             old = st.G[kk].mat.copy()
             dyson.dyson_mat(st.G[kk], st.S, st.epsmf[kk], mu, beta, W)
             err += float(np.abs(st.G[kk].mat - old).sum())
-        if err < mats_tol:
+        # a summed distance cannot fall below round-off (about 1e-15 per element)
+        if err < max(mats_tol, 1e-15 * nk * (ntau + 1) * d * d):
             break
     st.log["mats_iter"] = it_m + 1
     st.log["mats_err"] = err
@@ -90,7 +91,8 @@ def run_2b(eps0, U, nt, ntau, beta, h, W, mu=0.0, nbar=0.5, corrector=3, schedul
             old = st.G[kk].copy()
             dyson.dyson_start(st.G[kk], st.S, st.epsmf[kk], mu, beta, h, W)
             err += sum(extrap.distance_norm2(n, st.G[kk], old) for n in range(k + 1))
-        if err < boot_tol and it_b > 2:
+        nel_boot = nk * d * d * ((k + 1) * (k + 2) + (k + 1) * (ntau + 1))
+        if err < max(boot_tol, 1e-15 * nel_boot) and it_b > 2:
             break
     st.log["boot_iter"] = it_b + 1
     st.log["boot_err"] = err

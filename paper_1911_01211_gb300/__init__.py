@@ -78,6 +78,7 @@ SIGNATURES = {
                                  ctypes.POINTER(ng_run_params), ctypes.POINTER(ctypes.c_int), _P]),
     "ng_solve_fixed": (ctypes.c_int, [_P, _G, ng_herm, ng_herm, ng_func, ctypes.c_int, _P]),
     "ng_precision_reset": (ctypes.c_int, [_P]),
+    "ng_observables": (ctypes.c_int, [_P, _G, ctypes.c_int, ng_herm, ng_herm, ng_func, ng_func, _P, _P]),
     "ng_dyson_start_noalloc": (ctypes.c_int, [_G, ng_herm, ng_herm, ng_func, _P]),
     "ng_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "ng_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
@@ -207,6 +208,11 @@ class Context:
         out = (ctypes.c_double * 18)()
         self._chk(self.lib.ng_weights(self.h, out))
         return list(out)
+
+    def observables(self, grid, tstp, G, S, eps0, eps_mf, out, stream=None):
+        """out: device float64 tensor of 5 -> [N, E_kin, E_mf, E_corr, E_tot] (batch averages)."""
+        self._chk(self.lib.ng_observables(self.h, ctypes.byref(grid.c()), tstp, G.c(), S.c(), eps0.c(), eps_mf.c(),
+                                          ctypes.c_void_p(out.data_ptr()), _stream(stream)))
 
     def precision_reset(self):
         self._chk(self.lib.ng_precision_reset(self.h))

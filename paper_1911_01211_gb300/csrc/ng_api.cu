@@ -9,6 +9,7 @@
 #include "ng_setup.cuh"
 #include "ng_slice.cuh"
 #include "ng_step32.cuh"
+#include "ng_obs.cuh"
 
 // FP32 copy of one contour function (NG_F32C time steps): the buffer, the identity of the
 // FP64 source it mirrors and the last slice converted (-2: nothing, -1: mat only).
@@ -44,6 +45,8 @@ struct ng_ctx {
     double prof_flops = 0.0;
     std::vector<int> ev_kind;        // 0 bulk, 1 boundary, per event pair
     Shadow shG, shS;                 // FP32 copies of G and Sigma for NG_F32C
+    void* ws_obs = nullptr;          // per-problem observables before the batch sum
+    size_t ws_obs_bytes = 0;
 };
 
 namespace {
@@ -263,27 +266,57 @@ ng_status launch_timestep32(ng_ctx* c, const Grid& g, int n, const HermV& G, con
     return check_launch(c, "k_step_boundary");
 }
 
+// Matsubara solve.  refine_steps = 0: exact solve by a fresh LU of the current operator (the
+// factors and row interchanges are kept).  refine_steps > 0 (driver only, after a fresh LU of
+// the same grid): iterative refinement of the current G^M against the current operator with
+// the kept factors, at most refine_steps steps; *refined_ok reports convergence of the
+// refinement (update sum below ref_tol); otherwise the caller falls back to a fresh LU.
 template <int D>
-ng_status launch_mat(ng_ctx* c, const Grid& g, const HermV& G, const HermV& S, const FuncV& eps, cudaStream_t s) {
+ng_status launch_mat(ng_ctx* c, const Grid& g, const HermV& G, const HermV& S, const FuncV& eps, cudaStream_t s,
+                     int refine_steps = 0, double ref_tol = 0.0, bool* refined_ok = nullptr) {
     const int T = g.ntau, N = (T + 1) * D, ld = N + D;
     const size_t b_g = sizeof(cplx) * (size_t)g.nb * (T + 1) * D * D;
     const size_t b_A = sizeof(cplx) * (size_t)g.nb * N * ld;
-    ng_status st = ensure(c, &c->ws_mat, &c->ws_mat_bytes, 2 * b_g + b_A);
+    const size_t b_piv = sizeof(int) * (size_t)g.nb * N + 256;
+    ng_status st = ensure(c, &c->ws_mat, &c->ws_mat_bytes, 3 * b_g + b_A + b_piv);
     if (st) return st;
     cplx* ws_g = (cplx*)c->ws_mat;
     cplx* ws_K = ws_g + b_g / sizeof(cplx);
-    cplx* ws_A = ws_K + b_g / sizeof(cplx);
+    cplx* ws_r = ws_K + b_g / sizeof(cplx);
+    cplx* ws_A = ws_r + b_g / sizeof(cplx);
+    int* ws_piv = (int*)(ws_A + b_A / sizeof(cplx));
     const int64_t items = (int64_t)(T + 1) * g.nb;
     k_mat_g<D><<<nblocks(items, 128), 128, 0, s>>>(g, eps, ws_g);
     if ((st = check_launch(c, "k_mat_g"))) return st;
     k_mat_K<D><<<nblocks(items, 128), 128, 0, s>>>(g, S, ws_g, ws_K);
     if ((st = check_launch(c, "k_mat_K"))) return st;
+    if (refine_steps > 0) {
+        *refined_ok = false;
+        double prev = 1e300;
+        for (int r = 0; r < refine_steps; ++r) {
+            k_mat_resid<D><<<nblocks(items, 128), 128, 0, s>>>(g, ws_g, ws_K, G, ws_r);
+            if ((st = check_launch(c, "k_mat_resid"))) return st;
+            CUDA_TRY(c, cudaMemsetAsync(c->d_scalar, 0, sizeof(double), s));
+            k_lu_resolve<<<g.nb, NG_LU_THREADS, 0, s>>>(g, N, D, ws_A, ws_piv, ws_r, G, c->d_scalar);
+            if ((st = check_launch(c, "k_lu_resolve"))) return st;
+            double dsum = 0.0;
+            CUDA_TRY(c, cudaMemcpyAsync(&dsum, c->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, s));
+            CUDA_TRY(c, cudaStreamSynchronize(s));
+            if (!(dsum == dsum)) return NG_OK;               // non-finite: fall back
+            if (dsum == 0.0 || dsum > 0.5 * prev) {           // at the round-off floor, or stalled
+                *refined_ok = dsum < ref_tol;
+                return NG_OK;
+            }
+            prev = dsum;
+        }
+        return NG_OK;
+    }
     const int64_t ab = (int64_t)(T + 1) * (T + 2) * g.nb;
     k_mat_assemble<D><<<nblocks(ab, 256), 256, 0, s>>>(g, ws_g, ws_K, ws_A);
     if ((st = check_launch(c, "k_mat_assemble"))) return st;
     const size_t smem = sizeof(cplx) * (size_t)(ld + N) + NG_LU_THREADS * (sizeof(double) + sizeof(int));
     CUDA_TRY(c, cudaFuncSetAttribute(k_lu_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_lu_solve<<<g.nb, NG_LU_THREADS, smem, s>>>(N, D, ws_A, c->d_status);
+    k_lu_solve<<<g.nb, NG_LU_THREADS, smem, s>>>(N, D, ws_A, ws_piv, c->d_status);
     if ((st = check_launch(c, "k_lu_solve"))) return st;
     k_mat_store<D><<<nblocks(items, 128), 128, 0, s>>>(g, ws_A, G, c->d_status);
     return check_launch(c, "k_mat_store");
@@ -335,6 +368,10 @@ ng_status do_timestep(ng_ctx* c, const Grid& g, int n, const HermV& G, const Her
 }
 ng_status do_mat(ng_ctx* c, const Grid& g, const HermV& G, const HermV& S, const FuncV& eps, cudaStream_t s) {
     return g.nf == 1 ? launch_mat<1>(c, g, G, S, eps, s) : launch_mat<2>(c, g, G, S, eps, s);
+}
+ng_status do_mat_refine(ng_ctx* c, const Grid& g, const HermV& G, const HermV& S, const FuncV& eps, cudaStream_t s,
+                        int steps, double tol, bool* ok) {
+    return g.nf == 1 ? launch_mat<1>(c, g, G, S, eps, s, steps, tol, ok) : launch_mat<2>(c, g, G, S, eps, s, steps, tol, ok);
 }
 ng_status do_start(ng_ctx* c, const Grid& g, const HermV& G, const HermV& S, const FuncV& eps, cudaStream_t s) {
     return g.nf == 1 ? launch_start<1>(c, g, G, S, eps, s) : launch_start<2>(c, g, G, S, eps, s);
@@ -394,6 +431,7 @@ void ng_destroy(ng_ctx* c) {
     cudaFree(c->ws_prev);
     cudaFree(c->shG.buf);
     cudaFree(c->shS.buf);
+    cudaFree(c->ws_obs);
     delete c;
 }
 
@@ -498,6 +536,28 @@ ng_status ng_dyson_timestep(ng_ctx* c, const ng_grid* grid, int tstp, ng_herm G,
     if ((st = check_herm(c, g, S, "Sigma", true, &Sv, 0))) return st;
     if ((st = check_func(c, g, eps, "eps", &ev))) return st;
     return do_timestep(c, g, tstp, Gv, Sv, ev, (cudaStream_t)stream, precision);
+}
+
+ng_status ng_observables(ng_ctx* c, const ng_grid* grid, int tstp, ng_herm G, ng_herm S, ng_func eps0, ng_func epsmf,
+                         double* out_dev, void* stream) {
+    Grid g;
+    HermV Gv, Sv;
+    FuncV e0, mf;
+    ng_status st;
+    if ((st = check_grid(c, grid, &g))) return st;
+    if (tstp < 0 || tstp > g.nt) return fail(c, NG_EINVAL, "tstp = %d must be in 0..nt", tstp);
+    if ((st = check_herm(c, g, G, "G", true, &Gv, g.nb))) return st;
+    if ((st = check_herm(c, g, S, "Sigma", true, &Sv, 0))) return st;
+    if ((st = check_func(c, g, eps0, "eps0", &e0))) return st;
+    if ((st = check_func(c, g, epsmf, "eps_mf", &mf))) return st;
+    if (!out_dev) return fail(c, NG_EINVAL, "out_dev is NULL");
+    if ((st = ensure(c, &c->ws_obs, &c->ws_obs_bytes, sizeof(double) * NG_NOBS * (size_t)g.nb))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (g.nf == 1) k_observables<1><<<g.nb, NG_OBS_THREADS, 0, s>>>(g, tstp, Gv, Sv, e0, mf, (double*)c->ws_obs);
+    else k_observables<2><<<g.nb, NG_OBS_THREADS, 0, s>>>(g, tstp, Gv, Sv, e0, mf, (double*)c->ws_obs);
+    if ((st = check_launch(c, "k_observables"))) return st;
+    k_observables_reduce<<<1, NG_OBS_THREADS, 0, s>>>(g.nb, (const double*)c->ws_obs, out_dev);
+    return check_launch(c, "k_observables_reduce");
 }
 
 ng_status ng_precision_reset(ng_ctx* c) {
@@ -636,17 +696,24 @@ ng_status ng_run_2b(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm Gloc, ng_
         CUDA_TRY(c, cudaMemsetAsync(S.mat, 0, sizeof(cplx) * dd * el_mat, s));
         if ((st = do_mat(c, g, Gv, Sv, mf, s))) return st;
         double err = 0.0;
+        // stopping floors: a summed distance cannot fall below round-off, about 1e-15 per element
+        const double nel_mat = (double)G.ldk * el_mat * dd;
+        const double mats_stop = std::max(p->mats_tol, 1e-15 * nel_mat);
         for (mats_it = 0; mats_it < p->mats_maxiter; ++mats_it) {
             if ((st = do_kreduce(c, g, -1, Lv, Gv, s))) return st;
             if ((st = do_hartree(c, g, -1, mf, e0, Lv, uv, p->nbar, s))) return st;
             if ((st = do_sigma(c, g, -1, Sv, Lv, uv, s))) return st;
             CUDA_TRY(c, cudaMemcpyAsync(Pv.mat.p, Gv.mat.p, per * el_mat, cudaMemcpyDeviceToDevice, s));
-            if ((st = do_mat(c, g, Gv, Sv, mf, s))) return st;
+            // after two fresh solves the operator changes little between iterations: refine the
+            // current iterate with the kept LU factors, refactor only if that stalls
+            bool refined = false;
+            if (mats_it >= 2 && (st = do_mat_refine(c, g, Gv, Sv, mf, s, 30, 1e-13 * nel_mat, &refined))) return st;
+            if (!refined && (st = do_mat(c, g, Gv, Sv, mf, s))) return st;
             CUDA_TRY(c, cudaMemsetAsync(c->d_scalar, 0, sizeof(double), s));
             if ((st = do_distance(c, g, -1, Gv, Pv, c->d_scalar, s))) return st;
             CUDA_TRY(c, cudaMemcpyAsync(&err, c->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, s));
             CUDA_TRY(c, cudaStreamSynchronize(s));
-            if (err < p->mats_tol) break;
+            if (err < mats_stop) break;
         }
         if (mats_it == p->mats_maxiter) noconv = true;
         ++mats_it;
@@ -674,7 +741,7 @@ ng_status ng_run_2b(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm Gloc, ng_
                 if ((st = do_distance(c, g, n, Gv, Pv, c->d_scalar, s))) return st;
             CUDA_TRY(c, cudaMemcpyAsync(&err, c->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, s));
             CUDA_TRY(c, cudaStreamSynchronize(s));
-            if (err < p->boot_tol && boot_it > 2) break;
+            if (err < std::max(p->boot_tol, 1e-15 * (double)G.ldk * dd * (2.0 * el_tri + el_tv)) && boot_it > 2) break;
         }
         if (boot_it == p->boot_maxiter) noconv = true;
         ++boot_it;

@@ -259,7 +259,7 @@ __global__ void k_mat_assemble(Grid g, const cplx* ws_g, const cplx* ws_K, cplx*
 // LU with partial pivoting of the augmented matrix [A | B] (N x (N + nrhs)) and back
 // substitution; one block per problem; writes the solution into column block N..N+nrhs.
 #define NG_LU_THREADS 512
-__global__ void __launch_bounds__(NG_LU_THREADS) k_lu_solve(int N, int nrhs, cplx* ws_A, int* status) {
+__global__ void __launch_bounds__(NG_LU_THREADS) k_lu_solve(int N, int nrhs, cplx* ws_A, int* piv, int* status) {
     const int ld = N + nrhs;
     cplx* A = ws_A + (int64_t)blockIdx.x * N * ld;
     extern __shared__ unsigned char smem_raw[];
@@ -288,6 +288,7 @@ __global__ void __launch_bounds__(NG_LU_THREADS) k_lu_solve(int N, int nrhs, cpl
         }
         const int p = ri[0];
         if (rv[0] <= 0.0 && t == 0) atomicOr(status, NGF_SINGULAR);
+        if (t == 0) piv[(int64_t)blockIdx.x * N + c] = p;   // row interchange of step c
         __syncthreads();
         // swap rows c and p, load the pivot row into shared memory
         for (int j = t; j < ld; j += nt) {
@@ -328,6 +329,73 @@ __global__ void __launch_bounds__(NG_LU_THREADS) k_lu_solve(int N, int nrhs, cpl
         }
         __syncthreads();
     }
+}
+
+// ----------------------------------------------------------------------------------------
+// Iterative refinement of the Matsubara solve with stored LU factors (from an earlier
+// operator): residual r = g + [K * G]^M - G of the current operator (matrix-free, Eqs. cm1/cm2),
+// x = (LU)^-1 r with the stored row interchanges, G += x.  The fixed point is the root of the
+// current discretised equation; only the convergence path differs from a fresh LU.
+// ----------------------------------------------------------------------------------------
+template <int D>
+__global__ void k_mat_resid(Grid g, const cplx* ws_g, const cplx* ws_K, HermV G, cplx* ws_r) {
+    const NgWeights& W = c_W[g.k - 1];
+    const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (item >= (int64_t)(g.ntau + 1) * g.nb) return;
+    const int kb = (int)(item % g.nb), m = (int)(item / g.nb);
+    const int T1 = g.ntau + 1;
+    Mat<D> kg = cmat_ws_comp<D>(W, g, ws_K + (int64_t)kb * T1 * D * D, G.mat, m, kb);
+    const cplx* gg = ws_g + ((int64_t)kb * T1 + m) * D * D;
+    Mat<D> Gm = gmat<D>(G, m, kb);
+    cplx* r = ws_r + (int64_t)kb * T1 * D * D;   // row-major [(m a)][b] per problem
+    for (int a = 0; a < D; ++a)
+        for (int b = 0; b < D; ++b) r[(m * D + a) * D + b] = csub(cadd(gg[a * D + b], kg.v[a][b]), Gm.v[a][b]);
+}
+
+// one block per problem: x = U^-1 L^-1 P r in place (r has nrhs columns), then G^M += x and
+// *dsum += sum |x|
+__global__ void __launch_bounds__(NG_LU_THREADS) k_lu_resolve(Grid g, int N, int nrhs, const cplx* ws_A, const int* piv,
+                                                              cplx* ws_r, HermV G, double* dsum) {
+    const int ld = N + nrhs;
+    const cplx* A = ws_A + (int64_t)blockIdx.x * N * ld;
+    const int* p = piv + (int64_t)blockIdx.x * N;
+    cplx* r = ws_r + (int64_t)blockIdx.x * N * nrhs;
+    const int t = threadIdx.x, nt = blockDim.x;
+    if (t < nrhs)   // row interchanges in factorisation order
+        for (int c = 0; c < N; ++c) {
+            const int q = p[c];
+            if (q != c) { cplx x = r[c * nrhs + t]; r[c * nrhs + t] = r[q * nrhs + t]; r[q * nrhs + t] = x; }
+        }
+    __syncthreads();
+    for (int c = 0; c < N; ++c) {   // forward: unit lower triangle (multipliers below the diagonal)
+        for (int64_t q = t; q < (int64_t)(N - c - 1) * nrhs; q += nt) {
+            const int rr = c + 1 + (int)(q / nrhs), j = (int)(q % nrhs);
+            r[rr * nrhs + j] = csub(r[rr * nrhs + j], cmul(A[(int64_t)rr * ld + c], r[c * nrhs + j]));
+        }
+        __syncthreads();
+    }
+    for (int c = N - 1; c >= 0; --c) {   // backward: upper triangle
+        if (t < nrhs) r[c * nrhs + t] = cdiv(r[c * nrhs + t], A[(int64_t)c * ld + c]);
+        __syncthreads();
+        for (int64_t q = t; q < (int64_t)c * nrhs; q += nt) {
+            const int rr = (int)(q / nrhs), j = (int)(q % nrhs);
+            r[rr * nrhs + j] = csub(r[rr * nrhs + j], cmul(A[(int64_t)rr * ld + c], r[c * nrhs + j]));
+        }
+        __syncthreads();
+    }
+    // G^M += x: element (m, a, b) <-> r[(m nrhs + a) ... ] with N = (ntau+1) nrhs rows
+    double s = 0.0;
+    const int dd = nrhs * nrhs;
+    for (int64_t q = t; q < (int64_t)N * nrhs; q += nt) {
+        const int row = (int)(q / nrhs), b = (int)(q % nrhs);
+        const int m = row / nrhs, a = row % nrhs;
+        const int64_t off = ((int64_t)m * dd + a * nrhs + b) * G.mat.ldk + (G.mat.ldk == 1 ? 0 : blockIdx.x);
+        const cplx x = r[q];
+        G.mat.p[off] = cadd(G.mat.p[off], x);
+        s += sqrt(cabs2(x));
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((t & 31) == 0 && s != 0.0) atomicAdd(dsum, s);
 }
 
 template <int D>

@@ -243,6 +243,43 @@ def test_2b_kspace_chain_small(ng):
         assert_close(herm_to_oracle(G, g, kb), st.G[kb])
 
 
+def test_observables_against_oracle(ng):
+    """ng_observables (N, E_kin, E_mf, E_corr, E_tot) after a small self-consistent chain run,
+    against the oracle's density matrix and Galitskii-Migdal correlation energy."""
+    from oracle import bubble, observables
+    w = wl.chain_kspace(nk=4, nt=20, ntau=20, beta=4.0, h=0.05)
+    g = _grid(ng, w)
+    ctx = ng.Context(w.korder)
+    G = ng.Herm(g)
+    L, S = ng.Herm(g, ldk=1), ng.Herm(g, ldk=1)
+    e0 = ng.Func(g, values=torch.from_numpy(w.eps0))
+    mf = ng.Func(g)
+    U = ng.Func(g, scalar=True)
+    U.val[:, 0, 0, 0] = torch.from_numpy(w.U.astype(complex))
+    ctx.run_2b(g, G, L, S, e0, mf, U, corrector=w.corrector)
+    out = torch.zeros(5, dtype=torch.float64, device="cuda")
+    W = Weights(w.korder)
+    Gk = [herm_to_oracle(G, g, kb) for kb in range(w.nbatch)]
+    So = herm_to_oracle(S, g, 0)
+    mfo = device_to_funcs(mf, g)
+    for n in (0, 3, w.korder + 1, w.nt):
+        ctx.observables(g, n, G, S, e0, mf, out)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        ref = np.zeros(5)
+        for kb in range(w.nbatch):
+            rho = observables.density_matrix(n, Gk[kb])
+            e0k = w.eps0[n + 1, :, :, kb]
+            ref[0] += np.real(np.trace(rho))
+            ref[1] += np.real(np.trace(rho @ e0k))
+            ref[2] += 0.5 * np.real(np.trace(rho @ (mfo[kb](n) - e0k)))
+            ref[3] += observables.correlation_energy(n, Gk[kb], So, W, w.beta, w.h)
+        ref /= w.nbatch
+        ref[4] = ref[1] + ref[2] + ref[3]
+        assert np.abs(got - ref).max() < 1e-12 * max(1.0, np.abs(ref).max()), (n, got, ref)
+    _status_ok(ctx, ng)
+
+
 def test_2b_hubbard_dimer_small(ng):
     """hubbard_dimer workload on a small grid (nf = 2, quench U: 1 -> 2)."""
     w = wl.hubbard_dimer(nt=30, ntau=24, beta=5.0, h=0.05)
