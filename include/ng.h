@@ -247,6 +247,38 @@ ng_status ng_distance_timestep(ng_ctx *ctx, const ng_grid *grid, int tstp, ng_he
 ng_status ng_observables(ng_ctx *ctx, const ng_grid *grid, int tstp, ng_herm G, ng_herm Sigma, ng_func eps0,
                          ng_func eps_mf, double *out_dev, void *stream);
 
+/* ---- uneven batch of independent problems ---------------------------------------------- */
+
+/* Out(t,t') = V In(t,t') V^dagger for every component and element (one problem each,
+ * nbatch = 1, ldk = 1): the embedding self-energy Sigma = V g_bath V^dagger of a cluster coupled
+ * to a bath (Sec. "Test of accuracy and scaling analysis", downfolding).  V_host: host array
+ * [nf_out][nf_in] complex128.  Grids must agree in nt and ntau. */
+ng_status ng_herm_sandwich(ng_ctx *ctx, const ng_grid *grid_out, ng_herm Out, const ng_grid *grid_in, ng_herm In,
+                           const double *V_host, void *stream);
+
+/* A batch of nprob independent problems with their own grids (nf in {1, 2, 4, 8}, nt, ntau,
+ * beta, h may all differ; korder equal to the context's; nbatch = 1 each) and fixed
+ * self-energies.  G[p], Sigma[p] (ldk = 1) and eps[p] are caller-owned device buffers in the
+ * layout of this header.  The batch owns a small device table (allocated here). */
+typedef struct ng_batch ng_batch;
+ng_status ng_batch_create(ng_ctx *ctx, int nprob, const ng_grid *grids, const ng_herm *G, const ng_herm *Sigma,
+                          const ng_func *eps, ng_batch **out);
+void ng_batch_destroy(ng_batch *batch);
+
+/* Matsubara solve and start-up of every problem (as ng_dyson_mat, ng_dyson_start). */
+ng_status ng_batch_setup(ng_ctx *ctx, ng_batch *batch, void *stream);
+
+/* Global time step n for every problem with k < n <= nt_p: one launch computes M_n^-1 of all
+ * active problems, one launch the bulk items of all of them (orbital-element-wise: one thread
+ * per (item, a, b), mixed schedule of ng_dyson_timestep), one launch their boundaries.
+ * threads: block size of the bulk launch, 64, 128 or 256 (0: the tuned or default value). */
+ng_status ng_batch_step(ng_ctx *ctx, ng_batch *batch, int n, int threads, void *stream);
+
+/* Setup, then every global time step until each problem reaches its nt.  The bulk block size
+ * is tuned once, by timing each candidate on a re-run of one representative step (a step is
+ * idempotent); *tuned_threads (may be NULL) receives the choice. */
+ng_status ng_batch_solve(ng_ctx *ctx, ng_batch *batch, int *tuned_threads, void *stream);
+
 /* ---- measurement ---------------------------------------------------------------------- */
 
 /* Start (enable = 1, clearing any previous record) or stop (enable = 0) per-launch timing of

@@ -78,6 +78,13 @@ SIGNATURES = {
                                  ctypes.POINTER(ng_run_params), ctypes.POINTER(ctypes.c_int), _P]),
     "ng_solve_fixed": (ctypes.c_int, [_P, _G, ng_herm, ng_herm, ng_func, ctypes.c_int, _P]),
     "ng_precision_reset": (ctypes.c_int, [_P]),
+    "ng_herm_sandwich": (ctypes.c_int, [_P, _G, ng_herm, _G, ng_herm, ctypes.POINTER(ctypes.c_double), _P]),
+    "ng_batch_create": (ctypes.c_int, [_P, ctypes.c_int, _G, ctypes.POINTER(ng_herm), ctypes.POINTER(ng_herm),
+                                       ctypes.POINTER(ng_func), ctypes.POINTER(_P)]),
+    "ng_batch_destroy": (None, [_P]),
+    "ng_batch_setup": (ctypes.c_int, [_P, _P, _P]),
+    "ng_batch_step": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, _P]),
+    "ng_batch_solve": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int), _P]),
     "ng_observables": (ctypes.c_int, [_P, _G, ctypes.c_int, ng_herm, ng_herm, ng_func, ng_func, _P, _P]),
     "ng_dyson_start_noalloc": (ctypes.c_int, [_G, ng_herm, ng_herm, ng_func, _P]),
     "ng_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
@@ -163,6 +170,44 @@ class Func:
         return ng_func(self.val.data_ptr(), self.ldk)
 
 
+class Batch:
+    """An uneven batch of independent problems (ng_batch_*): per-problem grids and buffers."""
+
+    def __init__(self, ctx, grids, Gs, Ss, epss):
+        self.ctx = ctx
+        n = len(grids)
+        self._keep = (grids, Gs, Ss, epss)
+        self._g = (ng_grid * n)(*[g.c() for g in grids])
+        self._G = (ng_herm * n)(*[x.c() for x in Gs])
+        self._S = (ng_herm * n)(*[x.c() for x in Ss])
+        self._e = (ng_func * n)(*[x.c() for x in epss])
+        h = ctypes.c_void_p()
+        ctx._chk(ctx.lib.ng_batch_create(ctx.h, n, self._g, self._G, self._S, self._e, ctypes.byref(h)))
+        self.h = h
+
+    def setup(self, stream=None):
+        self.ctx._chk(self.ctx.lib.ng_batch_setup(self.ctx.h, self.h, _stream(stream)))
+
+    def step(self, n, threads=0, stream=None):
+        self.ctx._chk(self.ctx.lib.ng_batch_step(self.ctx.h, self.h, n, threads, _stream(stream)))
+
+    def solve(self, stream=None):
+        t = ctypes.c_int()
+        self.ctx._chk(self.ctx.lib.ng_batch_solve(self.ctx.h, self.h, ctypes.byref(t), _stream(stream)))
+        return t.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.ng_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def dyson_start_noalloc(grid, G, S, eps, stream=None):
     """ng_dyson_start_noalloc: the start-up slices without any device allocation (no context;
     fixed 2 MiB static device scratch).  Returns the ng_status code (NG_ESCRATCH when the
@@ -213,6 +258,17 @@ class Context:
         """out: device float64 tensor of 5 -> [N, E_kin, E_mf, E_corr, E_tot] (batch averages)."""
         self._chk(self.lib.ng_observables(self.h, ctypes.byref(grid.c()), tstp, G.c(), S.c(), eps0.c(), eps_mf.c(),
                                           ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+
+    def herm_sandwich(self, grid_out, Out, grid_in, In, V, stream=None):
+        import numpy as np
+        v = np.ascontiguousarray(np.asarray(V, dtype=np.complex128).reshape(grid_out.nf, grid_in.nf))
+        self._chk(self.lib.ng_herm_sandwich(self.h, ctypes.byref(grid_out.c()), Out.c(), ctypes.byref(grid_in.c()),
+                                            In.c(), v.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                            _stream(stream)))
+        torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+
+    def batch(self, grids, Gs, Ss, epss):
+        return Batch(self, grids, Gs, Ss, epss)
 
     def precision_reset(self):
         self._chk(self.lib.ng_precision_reset(self.h))

@@ -10,6 +10,7 @@
 #include "ng_slice.cuh"
 #include "ng_step32.cuh"
 #include "ng_obs.cuh"
+#include "ng_ubatch.cuh"
 
 // FP32 copy of one contour function (NG_F32C time steps): the buffer, the identity of the
 // FP64 source it mirrors and the last slice converted (-2: nothing, -1: mat only).
@@ -47,6 +48,10 @@ struct ng_ctx {
     Shadow shG, shS;                 // FP32 copies of G and Sigma for NG_F32C
     void* ws_obs = nullptr;          // per-problem observables before the batch sum
     size_t ws_obs_bytes = 0;
+    void* ws_uni = nullptr;          // problem table of the element-wise step (nf = 4, 8)
+    size_t ws_uni_bytes = 0;
+    int uni_key_nb = -1;
+    const void *uni_key_G = nullptr, *uni_key_S = nullptr, *uni_key_eps = nullptr;
 };
 
 namespace {
@@ -101,7 +106,8 @@ ng_status check_grid(ng_ctx* c, const ng_grid* g, Grid* out) {
     if (g->nbatch < 1) return fail(c, NG_EINVAL, "nbatch must be >= 1");
     if (!(g->h > 0.0) || !(g->beta > 0.0)) return fail(c, NG_EINVAL, "h and beta must be positive");
     if (g->nf < 1) return fail(c, NG_EINVAL, "nf must be >= 1");
-    if (g->nf > 2) return fail(c, NG_EUNSUPPORTED, "nf = %d: this build supports nf = 1, 2", g->nf);
+    if (g->nf != 1 && g->nf != 2 && g->nf != 4 && g->nf != 8)
+        return fail(c, NG_EUNSUPPORTED, "nf = %d: this build supports nf = 1, 2, 4, 8", g->nf);
     out->nt = g->nt;
     out->ntau = g->ntau;
     out->nf = g->nf;
@@ -360,21 +366,127 @@ ng_status do_hartree(ng_ctx* c, const Grid& g, int tstp, const FuncV& mf, const 
     k_hartree<<<nblocks((int64_t)mf.ldk * g.nf * g.nf, 128), 128, 0, s>>>(g, tstp, mf, e0, L, U, nbar);
     return check_launch(c, "k_hartree");
 }
+// ---------------------------------------------------------------------------------------
+// element-wise time step for nf = 4, 8 and for the uneven batch: one launch table per
+// chunk of <= NG_UMAXP problems at the same global step n
+// ---------------------------------------------------------------------------------------
+struct UHost {
+    int D, nt, ntau, k;
+};
+ng_status ustep(ng_ctx* c, const UProb* d_probs, const std::vector<UHost>& info, const std::vector<int>& active, int n,
+                int threads, cudaStream_t s) {
+    ng_status st;
+    for (size_t c0 = 0; c0 < active.size(); c0 += NG_UMAXP) {
+        UTable tab;
+        memset(&tab, 0, sizeof(tab));
+        tab.n = n;
+        int blk = 0;
+        const size_t c1 = std::min(active.size(), c0 + (size_t)NG_UMAXP);
+        for (size_t i = c0; i < c1; ++i) {
+            const UHost& u = info[active[i]];
+            const int ipb = threads / (u.D * u.D);
+            const int j = (int)(i - c0);
+            tab.prob[j] = active[i];
+            tab.start[j] = blk;
+            tab.nles[j] = (n >= 2 * u.k + 1) ? (n - u.k - 1 + ipb - 1) / ipb : 0;
+            tab.ntv[j] = (u.ntau + 1 + ipb - 1) / ipb;
+            const int nret = (n - u.k + ipb - 1) / ipb;
+            blk += tab.nles[j] + tab.ntv[j] + nret;
+        }
+        tab.np = (int)(c1 - c0);
+        tab.start[tab.np] = blk;
+        k_uminv<<<tab.np, 32, 0, s>>>(d_probs, tab, c->d_status);
+        if ((st = check_launch(c, "k_uminv"))) return st;
+        long e0 = prof_pair(c, 0);
+        if (e0 >= 0) cudaEventRecord(c->ev_pool[e0], s);
+        k_ubulk<<<blk, threads, sizeof(cplx) * threads, s>>>(d_probs, tab, c->d_status);
+        if ((st = check_launch(c, "k_ubulk"))) return st;
+        if (e0 >= 0) cudaEventRecord(c->ev_pool[e0 + 1], s);
+        long e1 = prof_pair(c, 1);
+        if (e1 >= 0) cudaEventRecord(c->ev_pool[e1], s);
+        k_uboundary<<<tab.np, NG_UBND_THREADS, NG_UBND_SMEM, s>>>(d_probs, tab, c->d_status);
+        if (e1 >= 0) cudaEventRecord(c->ev_pool[e1 + 1], s);
+        if ((st = check_launch(c, "k_uboundary"))) return st;
+        if (c->prof) {
+            for (size_t i = c0; i < c1; ++i) {
+                const UHost& u = info[active[i]];
+                Grid gg;
+                gg.k = u.k;
+                gg.ntau = u.ntau;
+                gg.nb = 1;
+                c->prof_flops += 8.0 * u.D * u.D * u.D * bulk_cmacs(gg, n);
+            }
+        }
+    }
+    return NG_OK;
+}
+
+// uniform-batch time step with nf = 4, 8: every interleaved problem kb as one UProb
+ng_status utimestep_uniform(ng_ctx* c, const Grid& g, int n, const HermV& G, const HermV& S, const FuncV& eps,
+                            cudaStream_t s) {
+    const size_t need = sizeof(UProb) * (size_t)g.nb + sizeof(cplx) * 64 * (size_t)g.nb;
+    ng_status st = ensure(c, &c->ws_uni, &c->ws_uni_bytes, need);
+    if (st) return st;
+    UProb* d_probs = (UProb*)c->ws_uni;
+    cplx* d_minv = (cplx*)((char*)c->ws_uni + sizeof(UProb) * (size_t)g.nb);
+    if (c->uni_key_nb != g.nb || c->uni_key_G != G.ret.p || c->uni_key_S != S.ret.p || c->uni_key_eps != eps.p) {
+        std::vector<UProb> h(g.nb);
+        for (int kb = 0; kb < g.nb; ++kb) {
+            h[kb].g = g;
+            h[kb].g.nb = 1;
+            h[kb].G = G;
+            h[kb].S = S;
+            h[kb].eps = eps;
+            h[kb].kb = kb;
+            h[kb].minv = d_minv + 64 * (size_t)kb;
+        }
+        CUDA_TRY(c, cudaMemcpyAsync(d_probs, h.data(), sizeof(UProb) * h.size(), cudaMemcpyHostToDevice, s));
+        CUDA_TRY(c, cudaStreamSynchronize(s));
+        c->uni_key_nb = g.nb;
+        c->uni_key_G = G.ret.p;
+        c->uni_key_S = S.ret.p;
+        c->uni_key_eps = eps.p;
+    }
+    std::vector<UHost> info(g.nb, UHost{g.nf, g.nt, g.ntau, g.k});
+    std::vector<int> active(g.nb);
+    for (int kb = 0; kb < g.nb; ++kb) active[kb] = kb;
+    return ustep(c, d_probs, info, active, n, 128, s);
+}
+
 ng_status do_timestep(ng_ctx* c, const Grid& g, int n, const HermV& G, const HermV& S, const FuncV& eps, cudaStream_t s,
                       int precision = NG_FP64) {
+    if (g.nf > 2) {
+        if (precision != NG_FP64) return fail(c, NG_EUNSUPPORTED, "NG_F32C needs nf <= 2");
+        return utimestep_uniform(c, g, n, G, S, eps, s);
+    }
     if (precision == NG_F32C)
         return g.nf == 1 ? launch_timestep32<1>(c, g, n, G, S, eps, s) : launch_timestep32<2>(c, g, n, G, S, eps, s);
     return g.nf == 1 ? launch_timestep<1>(c, g, n, G, S, eps, s) : launch_timestep<2>(c, g, n, G, S, eps, s);
 }
 ng_status do_mat(ng_ctx* c, const Grid& g, const HermV& G, const HermV& S, const FuncV& eps, cudaStream_t s) {
-    return g.nf == 1 ? launch_mat<1>(c, g, G, S, eps, s) : launch_mat<2>(c, g, G, S, eps, s);
+    switch (g.nf) {
+        case 1: return launch_mat<1>(c, g, G, S, eps, s);
+        case 2: return launch_mat<2>(c, g, G, S, eps, s);
+        case 4: return launch_mat<4>(c, g, G, S, eps, s);
+        default: return launch_mat<8>(c, g, G, S, eps, s);
+    }
 }
 ng_status do_mat_refine(ng_ctx* c, const Grid& g, const HermV& G, const HermV& S, const FuncV& eps, cudaStream_t s,
                         int steps, double tol, bool* ok) {
-    return g.nf == 1 ? launch_mat<1>(c, g, G, S, eps, s, steps, tol, ok) : launch_mat<2>(c, g, G, S, eps, s, steps, tol, ok);
+    switch (g.nf) {
+        case 1: return launch_mat<1>(c, g, G, S, eps, s, steps, tol, ok);
+        case 2: return launch_mat<2>(c, g, G, S, eps, s, steps, tol, ok);
+        case 4: return launch_mat<4>(c, g, G, S, eps, s, steps, tol, ok);
+        default: return launch_mat<8>(c, g, G, S, eps, s, steps, tol, ok);
+    }
 }
 ng_status do_start(ng_ctx* c, const Grid& g, const HermV& G, const HermV& S, const FuncV& eps, cudaStream_t s) {
-    return g.nf == 1 ? launch_start<1>(c, g, G, S, eps, s) : launch_start<2>(c, g, G, S, eps, s);
+    switch (g.nf) {
+        case 1: return launch_start<1>(c, g, G, S, eps, s);
+        case 2: return launch_start<2>(c, g, G, S, eps, s);
+        case 4: return launch_start<4>(c, g, G, S, eps, s);
+        default: return launch_start<8>(c, g, G, S, eps, s);
+    }
 }
 ng_status do_extrap(ng_ctx* c, const Grid& g, int n, const HermV& G, cudaStream_t s) {
     const int64_t items = (int64_t)(2 * (n + 2) + g.ntau + 1) * g.nf * g.nf * G.ret.ldk;
@@ -432,6 +544,7 @@ void ng_destroy(ng_ctx* c) {
     cudaFree(c->shG.buf);
     cudaFree(c->shS.buf);
     cudaFree(c->ws_obs);
+    cudaFree(c->ws_uni);
     delete c;
 }
 
@@ -496,7 +609,12 @@ ng_status ng_green_from_H_const(ng_ctx* c, const ng_grid* grid, ng_herm G, const
     if ((st = ensure(c, (void**)&c->d_eps, &c->d_eps_bytes, bytes))) return st;
     cudaStream_t s = (cudaStream_t)stream;
     CUDA_TRY(c, cudaMemcpyAsync(c->d_eps, eps_host, bytes, cudaMemcpyHostToDevice, s));
-    return g.nf == 1 ? launch_free<1>(c, g, Gv, c->d_eps, scale, s) : launch_free<2>(c, g, Gv, c->d_eps, scale, s);
+    switch (g.nf) {
+        case 1: return launch_free<1>(c, g, Gv, c->d_eps, scale, s);
+        case 2: return launch_free<2>(c, g, Gv, c->d_eps, scale, s);
+        case 4: return launch_free<4>(c, g, Gv, c->d_eps, scale, s);
+        default: return launch_free<8>(c, g, Gv, c->d_eps, scale, s);
+    }
 }
 
 ng_status ng_dyson_mat(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm S, ng_func eps, void* stream) {
@@ -553,6 +671,7 @@ ng_status ng_observables(ng_ctx* c, const ng_grid* grid, int tstp, ng_herm G, ng
     if (!out_dev) return fail(c, NG_EINVAL, "out_dev is NULL");
     if ((st = ensure(c, &c->ws_obs, &c->ws_obs_bytes, sizeof(double) * NG_NOBS * (size_t)g.nb))) return st;
     cudaStream_t s = (cudaStream_t)stream;
+    if (g.nf > 2) return fail(c, NG_EUNSUPPORTED, "ng_observables supports nf <= 2");
     if (g.nf == 1) k_observables<1><<<g.nb, NG_OBS_THREADS, 0, s>>>(g, tstp, Gv, Sv, e0, mf, (double*)c->ws_obs);
     else k_observables<2><<<g.nb, NG_OBS_THREADS, 0, s>>>(g, tstp, Gv, Sv, e0, mf, (double*)c->ws_obs);
     if ((st = check_launch(c, "k_observables"))) return st;
@@ -848,3 +967,198 @@ extern "C" ng_status ng_dyson_start_noalloc(const ng_grid* grid, ng_herm G, ng_h
     if (cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess) { cudaGetLastError(); return NG_ECUDA; }
     return q.nf == 1 ? noalloc_start<1>(g, Gv, Sv, ev, ws, status, s) : noalloc_start<2>(g, Gv, Sv, ev, ws, status, s);
 }
+
+// =========================================================================================
+// Uneven batch of independent problems (ng_batch_*) and the embedding sandwich
+// =========================================================================================
+struct ng_batch {
+    int np = 0;
+    int device = 0;
+    std::vector<Grid> grids;
+    std::vector<HermV> G, S;
+    std::vector<FuncV> eps;
+    std::vector<UHost> info;
+    UProb* d_probs = nullptr;
+    cplx* d_minv = nullptr;
+    int threads = 0;      // block size of the bulk kernel chosen by the autotune (0: not tuned)
+    double tune_ms[3] = {0, 0, 0};
+};
+
+namespace {
+__global__ void k_sandwich(Grid go, HermV O, Grid gi, HermV I, const cplx* V) {
+    const int Do = go.nf, Di = gi.nf;
+    const int64_t T1 = go.ntau + 1, ntri = tri(go.nt + 1), ntv = (int64_t)(go.nt + 1) * T1;
+    const int64_t nel = T1 + 2 * ntri + ntv;
+    const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (item >= nel * Do * Do) return;
+    const int ab = (int)(item % (Do * Do));
+    int64_t e = item / (Do * Do);
+    const int a = ab / Do, b = ab % Do;
+    const Comp* co;
+    const Comp* ci;
+    if (e < T1) { co = &O.mat; ci = &I.mat; }
+    else if ((e -= T1) < ntri) { co = &O.ret; ci = &I.ret; }
+    else if ((e -= ntri) < ntri) { co = &O.les; ci = &I.les; }
+    else { e -= ntri; co = &O.tv; ci = &I.tv; }
+    cplx s = cz();
+    for (int c = 0; c < Di; ++c)
+        for (int d = 0; d < Di; ++d)
+            s = cfma(cmul(V[a * Di + c], ci->p[e * Di * Di + c * Di + d]), cconj(V[b * Di + d]), s);
+    co->p[e * Do * Do + ab] = s;
+}
+}  // namespace
+
+extern "C" {
+
+ng_status ng_herm_sandwich(ng_ctx* c, const ng_grid* grid_out, ng_herm Out, const ng_grid* grid_in, ng_herm In,
+                           const double* V_host, void* stream) {
+    Grid go, gi;
+    HermV Ov, Iv;
+    ng_status st;
+    if ((st = check_grid(c, grid_out, &go))) return st;
+    if ((st = check_grid(c, grid_in, &gi))) return st;
+    if (go.nb != 1 || gi.nb != 1) return fail(c, NG_EINVAL, "ng_herm_sandwich takes one problem (nbatch = 1)");
+    if (go.nt != gi.nt || go.ntau != gi.ntau) return fail(c, NG_EINVAL, "grids differ in nt or ntau");
+    if ((st = check_herm(c, go, Out, "Out", true, &Ov, 1))) return st;
+    if ((st = check_herm(c, gi, In, "In", true, &Iv, 1))) return st;
+    if (!V_host) return fail(c, NG_EINVAL, "V is NULL");
+    const size_t bytes = sizeof(cplx) * go.nf * gi.nf;
+    if ((st = ensure(c, (void**)&c->d_eps, &c->d_eps_bytes, bytes))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_eps, V_host, bytes, cudaMemcpyHostToDevice, s));
+    const int64_t nel = (go.ntau + 1) + 2 * tri(go.nt + 1) + (int64_t)(go.nt + 1) * (go.ntau + 1);
+    k_sandwich<<<nblocks(nel * go.nf * go.nf, 256), 256, 0, s>>>(go, Ov, gi, Iv, c->d_eps);
+    return check_launch(c, "k_sandwich");
+}
+
+ng_status ng_batch_create(ng_ctx* c, int nprob, const ng_grid* grids, const ng_herm* G, const ng_herm* S,
+                          const ng_func* eps, ng_batch** out) {
+    if (!c || !out) return NG_EINVAL;
+    *out = nullptr;
+    if (nprob < 1 || !grids || !G || !S || !eps) return fail(c, NG_EINVAL, "empty or NULL problem arrays");
+    ng_batch* b = new ng_batch();
+    b->np = nprob;
+    b->device = c->device;
+    std::vector<UProb> h(nprob);
+    for (int p = 0; p < nprob; ++p) {
+        Grid g;
+        HermV Gv, Sv;
+        FuncV ev;
+        ng_status st;
+        if ((st = check_grid(c, &grids[p], &g)) || (g.nb != 1 && (st = fail(c, NG_EINVAL, "problem %d: nbatch must be 1", p))) ||
+            (st = check_herm(c, g, G[p], "G", true, &Gv, 1)) || (st = check_herm(c, g, S[p], "Sigma", true, &Sv, 1)) ||
+            (st = check_func(c, g, eps[p], "eps", &ev))) {
+            delete b;
+            return st;
+        }
+        b->grids.push_back(g);
+        b->G.push_back(Gv);
+        b->S.push_back(Sv);
+        b->eps.push_back(ev);
+        b->info.push_back(UHost{g.nf, g.nt, g.ntau, g.k});
+        h[p].g = g;
+        h[p].G = Gv;
+        h[p].S = Sv;
+        h[p].eps = ev;
+        h[p].kb = 0;
+    }
+    if (cudaMalloc(&b->d_probs, sizeof(UProb) * nprob) != cudaSuccess ||
+        cudaMalloc(&b->d_minv, sizeof(cplx) * 64 * nprob) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(b->d_probs);
+        delete b;
+        return fail(c, NG_ENOMEM, "batch tables");
+    }
+    for (int p = 0; p < nprob; ++p) h[p].minv = b->d_minv + 64 * (size_t)p;
+    if (cudaMemcpy(b->d_probs, h.data(), sizeof(UProb) * nprob, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(b->d_probs);
+        cudaFree(b->d_minv);
+        delete b;
+        return fail(c, NG_ECUDA, "upload of the batch table");
+    }
+    *out = b;
+    return NG_OK;
+}
+
+void ng_batch_destroy(ng_batch* b) {
+    if (!b) return;
+    cudaSetDevice(b->device);
+    cudaDeviceSynchronize();
+    cudaFree(b->d_probs);
+    cudaFree(b->d_minv);
+    delete b;
+}
+
+ng_status ng_batch_setup(ng_ctx* c, ng_batch* b, void* stream) {
+    if (!c || !b) return NG_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    ng_status st;
+    for (int p = 0; p < b->np; ++p) {
+        if ((st = do_mat(c, b->grids[p], b->G[p], b->S[p], b->eps[p], s))) return st;
+        if ((st = do_start(c, b->grids[p], b->G[p], b->S[p], b->eps[p], s))) return st;
+    }
+    return NG_OK;
+}
+
+ng_status ng_batch_step(ng_ctx* c, ng_batch* b, int n, int threads, void* stream) {
+    if (!c || !b) return NG_EINVAL;
+    if (threads == 0) threads = b->threads ? b->threads : 128;
+    if (threads != 64 && threads != 128 && threads != 256) return fail(c, NG_EINVAL, "threads must be 64, 128 or 256");
+    std::vector<int> active;
+    for (int p = 0; p < b->np; ++p)
+        if (n > b->info[p].k && n <= b->info[p].nt) active.push_back(p);
+    if (active.empty()) return NG_OK;
+    static bool smem_set = false;
+    if (!smem_set) {
+        CUDA_TRY(c, cudaFuncSetAttribute(k_uboundary, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)NG_UBND_SMEM));
+        smem_set = true;
+    }
+    return ustep(c, b->d_probs, b->info, active, n, threads, (cudaStream_t)stream);
+}
+
+ng_status ng_batch_solve(ng_ctx* c, ng_batch* b, int* tuned_threads, void* stream) {
+    if (!c || !b) return NG_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    ng_status st;
+    if ((st = ng_batch_setup(c, b, stream))) return st;
+    int kmin = 1 << 30, ntmax = 0, ntmin = 1 << 30;
+    for (const UHost& u : b->info) {
+        kmin = std::min(kmin, u.k);
+        ntmax = std::max(ntmax, u.nt);
+        ntmin = std::min(ntmin, u.nt);
+    }
+    // autotune the bulk block size once, on a representative step (re-running a step is
+    // idempotent: slice n is recomputed from slices < n)
+    const int n_tune = std::max(2 * kmin + 2, ntmin / 2);
+    for (int n = kmin + 1; n <= ntmax; ++n) {
+        if (n == n_tune && b->threads == 0) {
+            const int cand[3] = {64, 128, 256};
+            cudaEvent_t e0, e1;
+            CUDA_TRY(c, cudaEventCreate(&e0));
+            CUDA_TRY(c, cudaEventCreate(&e1));
+            float best = 1e30f;
+            for (int i = 0; i < 3; ++i) {
+                float t_best = 1e30f;
+                for (int rep = 0; rep < 2; ++rep) {
+                    CUDA_TRY(c, cudaEventRecord(e0, s));
+                    if ((st = ng_batch_step(c, b, n, cand[i], stream))) return st;
+                    CUDA_TRY(c, cudaEventRecord(e1, s));
+                    CUDA_TRY(c, cudaEventSynchronize(e1));
+                    float ms = 0.f;
+                    CUDA_TRY(c, cudaEventElapsedTime(&ms, e0, e1));
+                    t_best = std::min(t_best, ms);
+                }
+                b->tune_ms[i] = t_best;
+                if (t_best < best) { best = t_best; b->threads = cand[i]; }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+        }
+        if ((st = ng_batch_step(c, b, n, 0, stream))) return st;
+    }
+    if (tuned_threads) *tuned_threads = b->threads;
+    return NG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,421 @@
+// Uneven batch (ng_batch_*): independent problems of different orbital dimension nf in
+// {1, 2, 4, 8}, length nt and inverse temperature, each with its own fixed self-energy, stepped
+// together.  One bulk launch per global time step covers the bulk items of every active
+// problem; the orbital-element-wise formulation (one thread per (item, a, b)) keeps the
+// register footprint independent of nf.  Same formulas and schedule as ng_step.cuh (paper
+// Sec. "Time stepping", mixed schedule).
+#pragma once
+
+#include "ng_step.cuh"
+
+#define NG_UMAXP 128    // problems per batch
+#define NG_UMAXD 8
+
+struct UProb {
+    Grid g;          // g.nb = 1 (one problem), g.nf = D
+    HermV G, S;      // ldk as stored; kb selects the problem inside interleaved storage
+    FuncV eps;
+    int kb;
+    cplx* minv;      // D*D workspace: M_n^-1 of the current step
+};
+
+// per-step launch table: blocks [start[i], start[i+1]) belong to problem prob[i]; inside,
+// the first nles[i] blocks are lesser items, then ntv[i] left-mixing, then retarded items
+struct UTable {
+    int np;
+    int n;                      // global time step
+    int start[NG_UMAXP + 1];
+    int prob[NG_UMAXP];
+    int nles[NG_UMAXP], ntv[NG_UMAXP];
+};
+
+// element (a,b) of a stored d x d block
+__device__ __forceinline__ cplx uel(const Comp& c, int64_t e, int D, int a, int b, int kb) {
+    return c.p[(e * (D * D) + a * D + b) * c.ldk + (c.ldk == 1 ? 0 : kb)];
+}
+__device__ __forceinline__ void ust(const Comp& c, int64_t e, int D, int a, int b, int kb, cplx v) {
+    c.p[(e * (D * D) + a * D + b) * c.ldk + (c.ldk == 1 ? 0 : kb)] = v;
+}
+__device__ __forceinline__ cplx ufunc(const FuncV& f, int n, int D, int a, int b, int kb) {
+    return f.p[((int64_t)(n + 1) * (D * D) + a * D + b) * f.ldk + (f.ldk == 1 ? 0 : kb)];
+}
+// G^R(n,j) element with the modified retarded continuation for j > n
+__device__ __forceinline__ cplx uretx(const HermV& X, int n, int j, int D, int a, int b, int kb) {
+    if (j <= n) return uel(X.ret, tri(n) + j, D, a, b, kb);
+    return cneg(cconj(uel(X.ret, tri(j) + n, D, b, a, kb)));
+}
+// G^<(j,n) element for any j, n
+__device__ __forceinline__ cplx ules(const HermV& X, int j, int n, int D, int a, int b, int kb) {
+    if (j <= n) return uel(X.les, tri(n) + j, D, a, b, kb);
+    return cneg(cconj(uel(X.les, tri(j) + n, D, b, a, kb)));
+}
+
+// M_n^-1 of every active problem (thread 0 of one block per problem), D x D Gauss-Jordan
+__global__ void k_uminv(const UProb* probs, UTable tab, int* status) {
+    if (blockIdx.x >= tab.np || threadIdx.x != 0) return;
+    const UProb& P = probs[tab.prob[blockIdx.x]];
+    const NgWeights& W = c_W[P.g.k - 1];
+    const int D = P.g.nf, n = tab.n, kb = P.kb;
+    cplx M[NG_UMAXD * NG_UMAXD], R[NG_UMAXD * NG_UMAXD];
+    for (int a = 0; a < D; ++a)
+        for (int b = 0; b < D; ++b) {
+            cplx e = ufunc(P.eps, n, D, a, b, kb);
+            if (a == b) e.x -= P.g.mu;
+            cplx v = cmuli(e);
+            v = cadd(v, cscal(P.g.h * gw(W, n, n), cmuli(uel(P.S.ret, tri(n) + n, D, a, b, kb))));
+            if (a == b) v.x += W.a[0] / P.g.h;
+            M[a * D + b] = v;
+            R[a * D + b] = cr(a == b ? 1.0 : 0.0);
+        }
+    if (dense_solve(M, D, R, D)) atomicOr(status, NGF_SINGULAR);
+    for (int i = 0; i < D * D; ++i) P.minv[i] = R[i];
+}
+
+// ---------------------------------------------------------------------------------------
+// element-wise bulk items; each thread holds one complex accumulator per sum
+// ---------------------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ cplx u_qtv(const NgWeights& W, const Grid& g, const HermV& G, const HermV& S, int n, int m,
+                                      int a, int b, int kb) {
+    const int k = W.k, T = g.ntau;
+    const int64_t rowS = (int64_t)n * (T + 1);
+    cplx c2 = cz(), c3 = cz();
+    if (m <= k) {
+        for (int j = 0; j <= k; ++j)
+            for (int l = 0; l <= k; ++l) {
+                const double r = W.R[m][j][l];
+#pragma unroll
+                for (int c = 0; c < D; ++c)
+                    c2 = cfma(cscal(r, uel(S.tv, rowS + l, D, a, c, kb)), uel(G.mat, T - j, D, c, b, kb), c2);
+            }
+    } else {
+        greg_for(W, m, m, [&](int l, double w) {
+#pragma unroll
+            for (int c = 0; c < D; ++c)
+                c2 = cfma(cscal(w, uel(S.tv, rowS + m - l, D, a, c, kb)), uel(G.mat, T - l, D, c, b, kb), c2);
+        });
+    }
+    if (m >= T - k) {
+        for (int j = 0; j <= k; ++j)
+            for (int l = 0; l <= k; ++l) {
+                const double r = W.R[T - m][j][l];
+#pragma unroll
+                for (int c = 0; c < D; ++c)
+                    c3 = cfma(cscal(r, uel(S.tv, rowS + T - l, D, a, c, kb)), uel(G.mat, j, D, c, b, kb), c3);
+            }
+    } else {
+        greg_for(W, T - m, T - m, [&](int l, double w) {
+#pragma unroll
+            for (int c = 0; c < D; ++c)
+                c3 = cfma(cscal(w, uel(S.tv, rowS + m + l, D, a, c, kb)), uel(G.mat, l, D, c, b, kb), c3);
+        });
+    }
+    // -i htau (xi c2 + c3)
+    return cscal(g.htau, cmulmi(cadd(cscal((double)g.sig, c2), c3)));
+}
+
+// rhs of one element (a, b) of a bulk item; task 0 les (m >= 1), 1 tv, 2 ret
+template <int D>
+__device__ cplx u_rhs(const NgWeights& W, const Grid& g, const HermV& G, const HermV& S, int n, int task, int m, int a,
+                      int b, int kb) {
+    const int k = W.k, T = g.ntau, T1 = g.ntau + 1;
+    if (task == 2) {  // retarded (B): -bdf/h - h i sum_l w Sigma^R(n,m+l) G^R(m+l,m)
+        const int L = n - m;
+        cplx acc = cz();
+        greg_for(W, L, L - 1, [&](int l, double w) {
+#pragma unroll
+            for (int c = 0; c < D; ++c)
+                acc = cfma(cscal(w, uel(S.ret, tri(n) + m + l, D, a, c, kb)), uel(G.ret, tri(m + l) + m, D, c, b, kb), acc);
+        });
+        cplx bdf = cz();
+        for (int l = 1; l <= k; ++l) bdf = cadd(bdf, cscal(W.a[l], uel(G.ret, tri(n - l) + m, D, a, b, kb)));
+        return csub(cscal(-1.0 / g.h, bdf), cscal(g.h, cmuli(acc)));
+    }
+    if (task == 1) {  // left-mixing: q - bdf/h - h i sum_j w Sigma^R(n,j) G^tv(j,m)
+        cplx acc = cz();
+        greg_for(W, n, n - 1, [&](int j, double w) {
+#pragma unroll
+            for (int c = 0; c < D; ++c)
+                acc = cfma(cscal(w, uel(S.ret, tri(n) + j, D, a, c, kb)), uel(G.tv, (int64_t)j * T1 + m, D, c, b, kb), acc);
+        });
+        cplx bdf = cz();
+        for (int l = 1; l <= k; ++l) bdf = cadd(bdf, cscal(W.a[l], uel(G.tv, (int64_t)(n - l) * T1 + m, D, a, b, kb)));
+        cplx r = u_qtv<D>(W, g, G, S, n, m, a, b, kb);
+        r = csub(r, cscal(1.0 / g.h, bdf));
+        return csub(r, cscal(g.h, cmuli(acc)));
+    }
+    // lesser (B): q - bdf/h + h i hist, q = i h C1 - xi htau C3
+    cplx c1 = cz();
+    if (m <= k) {
+        for (int j = 0; j <= k; ++j)
+#pragma unroll
+            for (int c = 0; c < D; ++c)
+                c1 = cfma(cscal(W.greg[m][j], uretx(G, m, j, D, a, c, kb)), uel(S.les, tri(n) + j, D, c, b, kb), c1);
+    } else {
+        greg_for(W, m, m, [&](int j, double w) {
+#pragma unroll
+            for (int c = 0; c < D; ++c)
+                c1 = cfma(cscal(w, uel(G.ret, tri(m) + j, D, a, c, kb)), uel(S.les, tri(n) + j, D, c, b, kb), c1);
+        });
+    }
+    cplx c3 = cz();   // sum_j w G^tv(m,j) [Sigma^tv(n,T-j)]^dagger
+    greg_for(W, T, T, [&](int j, double w) {
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+            c3 = cfma(cscal(w, uel(G.tv, (int64_t)m * T1 + j, D, a, c, kb)),
+                      cconj(uel(S.tv, (int64_t)n * T1 + T - j, D, b, c, kb)), c3);
+    });
+    cplx hist = cz();  // sum_l w G^<(m,l) [Sigma^R(n,l)]^dagger
+    greg_for(W, n, n - 1, [&](int l, double w) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            cplx gl = (l >= m) ? uel(G.les, tri(l) + m, D, a, c, kb) : cneg(cconj(uel(G.les, tri(m) + l, D, c, a, kb)));
+            hist = cfma(cscal(w, gl), cconj(uel(S.ret, tri(n) + l, D, b, c, kb)), hist);
+        }
+    });
+    cplx bdf = cz();
+    for (int l = 1; l <= k; ++l) bdf = cadd(bdf, cscal(W.a[l], uel(G.les, tri(n - l) + m, D, a, b, kb)));
+    cplx q = csub(cscal(g.h, cmuli(c1)), cscal((double)g.sig * g.htau, c3));
+    cplx r = csub(q, cscal(1.0 / g.h, bdf));
+    return cadd(r, cscal(g.h, cmuli(hist)));
+}
+
+template <int D>
+__device__ __forceinline__ void u_bulk_block(const UProb& P, int n, int lblk, int nles, int ntv, int* status) {
+    const NgWeights& W = c_W[P.g.k - 1];
+    constexpr int DD = D * D;
+    const int ipb = blockDim.x / DD;  // items per block
+    int task, base;
+    if (lblk < nles) { task = 0; base = lblk; }
+    else if (lblk < nles + ntv) { task = 1; base = lblk - nles; }
+    else { task = 2; base = lblk - nles - ntv; }
+    const int t = threadIdx.x;
+    const int li = t / DD, ab = t % DD, a = ab / D, b = ab % D;
+    const int col = base * ipb + li;
+    const int k = W.k;
+    int ncol, m;
+    if (task == 0) { ncol = n - k - 1; m = col + 1; }
+    else if (task == 1) { ncol = P.g.ntau + 1; m = col; }
+    else { ncol = n - k; m = col; }
+    const bool valid = (li < ipb) && (col < ncol);
+    extern __shared__ cplx rhs[];   // blockDim.x entries
+    cplx r = cz();
+    if (valid) r = u_rhs<D>(W, P.g, P.G, P.S, n, task, m, a, b, P.kb);
+    if (t < ipb * DD) rhs[t] = r;
+    __syncthreads();
+    if (!valid) return;
+    const cplx* rr = rhs + li * DD;
+    cplx y = cz();
+    if (task == 0) {  // y = rhs (M_n^dagger)^-1 = rhs (M_n^-1)^dagger: y_ab = sum_c rhs_ac conj(Minv_bc)
+#pragma unroll
+        for (int c = 0; c < D; ++c) y = cfma(rr[a * D + c], cconj(P.minv[b * D + c]), y);
+    } else {          // y = M_n^-1 rhs
+#pragma unroll
+        for (int c = 0; c < D; ++c) y = cfma(P.minv[a * D + c], rr[c * D + b], y);
+    }
+    if (!cfinite(y)) atomicOr(status, NGF_NONFINITE);
+    const Comp& dst = task == 0 ? P.G.les : (task == 1 ? P.G.tv : P.G.ret);
+    const int64_t e = task == 0 ? tri(n) + m : (task == 1 ? (int64_t)n * (P.g.ntau + 1) + m : tri(n) + m);
+    ust(dst, e, D, a, b, P.kb, y);
+}
+
+__global__ void __launch_bounds__(256) k_ubulk(const UProb* probs, UTable tab, int* status) {
+    // find the problem of this block (tables are short)
+    int i = 0;
+    while (i + 1 < tab.np && (int)blockIdx.x >= tab.start[i + 1]) ++i;
+    const UProb& P = probs[tab.prob[i]];
+    const int lblk = blockIdx.x - tab.start[i];
+    switch (P.g.nf) {
+        case 1: u_bulk_block<1>(P, tab.n, lblk, tab.nles[i], tab.ntv[i], status); break;
+        case 2: u_bulk_block<2>(P, tab.n, lblk, tab.nles[i], tab.ntv[i], status); break;
+        case 4: u_bulk_block<4>(P, tab.n, lblk, tab.nles[i], tab.ntv[i], status); break;
+        default: u_bulk_block<8>(P, tab.n, lblk, tab.nles[i], tab.ntv[i], status); break;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// boundary of step n for every active problem: one block per problem, runtime D <= 8
+// ---------------------------------------------------------------------------------------
+#define NG_UBND_THREADS 128
+#define NG_UBND_SMEM                                                                                  \
+    (sizeof(cplx) * ((NG_KMAX * NG_UMAXD) * (NG_KMAX * NG_UMAXD) + (NG_KMAX * NG_UMAXD) * NG_UMAXD + \
+                     NG_UBND_THREADS + 2 * (2 * NG_KMAX + 1) * NG_UMAXD * NG_UMAXD))
+
+// -i (C^<_2 + C^<_3)[Sigma,1,G](m,n) element (a,b), partial over j = j0, j0+js, ...
+__device__ cplx u_qlesA_part(const NgWeights& W, const Grid& g, const HermV& G, const HermV& S, int m, int n, int D,
+                             int a, int b, int kb, int j0, int js) {
+    const int k = W.k, T = g.ntau, T1 = g.ntau + 1;
+    cplx c2 = cz(), c3 = cz();
+    const int jmax = n <= k ? k : n;
+    for (int j = j0; j <= jmax; j += js) {
+        const double w = n <= k ? W.greg[n][j] : gw(W, n, j);
+        for (int c = 0; c < D; ++c)   // Sigma^<(m,j) G^A(j,n), G^A(j,n)_cb = conj(G~^R(n,j)_bc)
+            c2 = cfma(cscal(w, ules(S, m, j, D, a, c, kb)), cconj(uretx(G, n, j, D, b, c, kb)), c2);
+    }
+    for (int j = j0; j <= T; j += js) {
+        const double w = gw(W, T, j);
+        for (int c = 0; c < D; ++c)   // Sigma^tv(m,j) [G^tv(n,T-j)]^dagger
+            c3 = cfma(cscal(w, uel(S.tv, (int64_t)m * T1 + j, D, a, c, kb)),
+                      cconj(uel(G.tv, (int64_t)n * T1 + T - j, D, b, c, kb)), c3);
+    }
+    return cadd(cscal(g.h, cmulmi(c2)), cscal((double)g.sig * g.htau, c3));
+}
+
+// M_m = a_0/h + i(eps_m - mu) + h w_{m,m} i Sigma^R(m,m) into out[D*D]
+__device__ void u_stepmat(const NgWeights& W, const UProb& P, int m, cplx* out) {
+    const int D = P.g.nf;
+    for (int a = 0; a < D; ++a)
+        for (int b = 0; b < D; ++b) {
+            cplx e = ufunc(P.eps, m, D, a, b, P.kb);
+            if (a == b) e.x -= P.g.mu;
+            cplx v = cadd(cmuli(e), cscal(P.g.h * gw(W, m, m), cmuli(uel(P.S.ret, tri(m) + m, D, a, b, P.kb))));
+            if (a == b) v.x += W.a[0] / P.g.h;
+            out[a * D + b] = v;
+        }
+}
+
+__global__ void __launch_bounds__(NG_UBND_THREADS) k_uboundary(const UProb* probs, UTable tab, int* status) {
+    const UProb& P = probs[tab.prob[blockIdx.x]];
+    const NgWeights& W = c_W[P.g.k - 1];
+    const Grid& g = P.g;
+    const int D = g.nf, DD = D * D, k = W.k, n = tab.n, kb = P.kb, t = threadIdx.x;
+    // dynamic shared memory (NG_UBND_SMEM bytes): A[(kD)^2], B[kD x D], red[threads],
+    // qs/hs[(2k+1) x D^2] (sources and partial histories of the (A) rows)
+    extern __shared__ unsigned char ub_smem[];
+    cplx* A = reinterpret_cast<cplx*>(ub_smem);
+    cplx* B = A + (NG_KMAX * NG_UMAXD) * (NG_KMAX * NG_UMAXD);
+    cplx* red = B + (NG_KMAX * NG_UMAXD) * NG_UMAXD;
+    cplx(*qs)[NG_UMAXD * NG_UMAXD] = reinterpret_cast<cplx(*)[NG_UMAXD * NG_UMAXD]>(red + NG_UBND_THREADS);
+    cplx(*hs)[NG_UMAXD * NG_UMAXD] = qs + (2 * NG_KMAX + 1);
+    const int N = k * D;
+    // ---- retarded start-up along row n (conjugate VIDE, implementation (A)) ----------
+    // transposed system: rows (j, a), columns (l, b): A = Mh[l][j]^T, B = -(y0 Mh[0][j])^T
+    for (int q = t; q < k * (k + 1) * DD; q += blockDim.x) {
+        const int j = 1 + q / ((k + 1) * DD), rem = q % ((k + 1) * DD), l = rem / DD, ab = rem % DD;
+        const int a = ab / D, b = ab % D;
+        // Mh[l][j]_{ba} = D_{j,l}/h delta_ba + delta_lj i(eps_{n-j} - mu)_ba + h s_{j,l} i Sigma~^R(n-l, n-j)_ba
+        cplx v = cscal(g.h * W.greg[j][l], cmuli(uretx(P.S, n - l, n - j, D, b, a, kb)));
+        if (a == b) v.x += W.D[j][l] / g.h;
+        if (l == j) {
+            cplx e = ufunc(P.eps, n - j, D, b, a, kb);
+            if (a == b) e.x -= g.mu;
+            v = cadd(v, cmuli(e));
+        }
+        if (l > 0) A[((j - 1) * D + a) * N + (l - 1) * D + b] = v;
+    }
+    // right-hand side from Mh[0][j]_{ca}
+    for (int q = t; q < k * DD; q += blockDim.x) {
+        const int j = 1 + q / DD, ab = q % DD, a = ab / D, c = ab % D;
+        cplx v = cscal(g.h * W.greg[j][0], cmuli(uretx(P.S, n, n - j, D, c, a, kb)));
+        if (a == c) v.x += W.D[j][0] / g.h;
+        // -(y0 Mh[0][j])^T_{a c} = -(-i Mh[0][j]_{c a}) = i Mh[0][j]_{ca}
+        B[((j - 1) * D + a) * D + c] = cmuli(v);
+    }
+    __syncthreads();
+    if (t == 0 && dense_solve(A, N, B, D)) atomicOr(status, NGF_SINGULAR);
+    __syncthreads();
+    for (int q = t; q < (k + 1) * DD; q += blockDim.x) {
+        const int l = q / DD, ab = q % DD, c = ab / D, a = ab % D;   // y_l[c][a] = B[((l-1)D + a)][c]
+        cplx y = (l == 0) ? cr(0.0) : B[((l - 1) * D + a) * D + c];
+        if (l == 0) y = (c == a) ? make_double2(0.0, -1.0) : cz();
+        if (!cfinite(y)) atomicOr(status, NGF_NONFINITE);
+        ust(P.G.ret, tri(n) + n - l, D, c, a, kb, y);
+    }
+    for (int q = t; q < DD; q += blockDim.x) {   // G^<(0,n) = -[G^tv(n,0)]^dagger
+        const int a = q / D, b = q % D;
+        ust(P.G.les, tri(n) + 0, D, a, b, kb, cneg(cconj(uel(P.G.tv, (int64_t)n * (g.ntau + 1), D, b, a, kb))));
+    }
+    __syncthreads();
+    // ---- lesser column: rows by (A) ----------------------------------------------------
+    const bool full = (n <= 2 * k);
+    const int m0 = full ? 1 : n - k;
+    const int nq = n - m0 + 1;
+    const int ngrp = blockDim.x / DD;         // thread groups over j
+    const int grp = t / DD, ab = t % DD, a = ab / D, b = ab % D;
+    for (int r = 0; r < nq; ++r) {
+        const int m = m0 + r;
+        cplx qv = cz(), hv = cz();
+        if (grp < ngrp) {
+            qv = u_qlesA_part(W, g, P.G, P.S, m, n, D, a, b, kb, grp, ngrp);
+            if (!full && m > k)
+                for (int l = grp; l < m0; l += ngrp)
+                    for (int c = 0; c < D; ++c)
+                        hv = cfma(cscal(gw(W, m, l), uel(P.S.ret, tri(m) + l, D, a, c, kb)),
+                                  uel(P.G.les, tri(n) + l, D, c, b, kb), hv);
+        }
+        // reduce over groups (fixed order)
+        for (int pass = 0; pass < 2; ++pass) {
+            red[t] = pass == 0 ? qv : hv;
+            __syncthreads();
+            if (t < DD) {
+                cplx s = cz();
+                for (int gi = 0; gi < ngrp; ++gi) s = cadd(s, red[gi * DD + t]);
+                if (pass == 0) qs[r][t] = s; else hs[r][t] = s;
+            }
+            __syncthreads();
+        }
+    }
+    if (t != 0) return;
+    int sing = 0;
+    int mstep = m0;
+    cplx M[NG_UMAXD * NG_UMAXD], R[NG_UMAXD * NG_UMAXD], acc[NG_UMAXD * NG_UMAXD];
+    if (full) {   // VIDE start-up for m = 1..k
+        for (int m = 1; m <= k; ++m) {
+            for (int ab2 = 0; ab2 < DD; ++ab2) acc[ab2] = qs[m - 1][ab2];
+            for (int l = 0; l <= k; ++l)
+                for (int aa = 0; aa < D; ++aa)
+                    for (int bb = 0; bb < D; ++bb) {
+                        cplx v = cscal(g.h * W.greg[m][l], cmuli(uretx(P.S, m, l, D, aa, bb, kb)));
+                        if (aa == bb) v.x += W.D[m][l] / g.h;
+                        if (l == m) {
+                            cplx e = ufunc(P.eps, m, D, aa, bb, kb);
+                            if (aa == bb) e.x -= g.mu;
+                            v = cadd(v, cmuli(e));
+                        }
+                        if (l == 0) {   // acc -= M[m][0] y0
+                            for (int cc = 0; cc < D; ++cc)
+                                acc[aa * D + cc] = csub(acc[aa * D + cc], cmul(v, uel(P.G.les, tri(n), D, bb, cc, kb)));
+                        } else {
+                            A[((m - 1) * D + aa) * N + (l - 1) * D + bb] = v;
+                        }
+                    }
+            for (int aa = 0; aa < D; ++aa)
+                for (int cc = 0; cc < D; ++cc) B[((m - 1) * D + aa) * D + cc] = acc[aa * D + cc];
+        }
+        if (dense_solve(A, N, B, D)) atomicOr(status, NGF_SINGULAR);
+        for (int m = 1; m <= k; ++m)
+            for (int aa = 0; aa < D; ++aa)
+                for (int cc = 0; cc < D; ++cc) ust(P.G.les, tri(n) + m, D, aa, cc, kb, B[((m - 1) * D + aa) * D + cc]);
+        mstep = k + 1;
+    }
+    for (int m = mstep; m <= n; ++m) {   // serial VIDE steps
+        const int r = m - m0;
+        for (int ab2 = 0; ab2 < DD; ++ab2) {
+            acc[ab2] = qs[r][ab2];
+            R[ab2] = hs[r][ab2];
+        }
+        const int lfrom = full ? 0 : m0;
+        for (int l = lfrom; l < m; ++l)
+            for (int aa = 0; aa < D; ++aa)
+                for (int bb = 0; bb < D; ++bb) {
+                    cplx s = R[aa * D + bb];
+                    for (int cc = 0; cc < D; ++cc)
+                        s = cfma(cscal(gw(W, m, l), uel(P.S.ret, tri(m) + l, D, aa, cc, kb)), uel(P.G.les, tri(n) + l, D, cc, bb, kb), s);
+                    R[aa * D + bb] = s;
+                }
+        for (int aa = 0; aa < D; ++aa)
+            for (int bb = 0; bb < D; ++bb) {
+                cplx bdf = cz();
+                for (int l = 1; l <= k; ++l) bdf = cadd(bdf, cscal(W.a[l], uel(P.G.les, tri(n) + m - l, D, aa, bb, kb)));
+                acc[aa * D + bb] = csub(csub(acc[aa * D + bb], cscal(1.0 / g.h, bdf)), cscal(g.h, cmuli(R[aa * D + bb])));
+            }
+        u_stepmat(W, P, m, M);
+        if (dense_solve(M, D, acc, D)) sing = 1;
+        for (int aa = 0; aa < D; ++aa)
+            for (int bb = 0; bb < D; ++bb) {
+                if (!cfinite(acc[aa * D + bb])) atomicOr(status, NGF_NONFINITE);
+                ust(P.G.les, tri(n) + m, D, aa, bb, kb, acc[aa * D + bb]);
+            }
+    }
+    if (sing) atomicOr(status, NGF_SINGULAR);
+}

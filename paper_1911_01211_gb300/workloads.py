@@ -86,6 +86,26 @@ def square_kspace(L=16, nt=1000, ntau=400, beta=10.0, h=0.02, korder=5, U=1.5, c
                     U=np.full(nt + 2, U), extra={"A": A})
 
 
+def uneven_clusters(nprob=64, seed=191101211, nt_range=(500, 3000), ntau=300, h=0.02, beta_range=(5.0, 30.0),
+                    dims=(1, 2, 4, 8), nbath=4, vscale=0.3, korder=5):
+    """Independent embedded clusters: per problem nf ~ U(dims), nt ~ U{nt_range}, beta ~ U(beta_range),
+    cluster Hamiltonian h (nf x nf hermitian, N(0,1) entries), a bath of nbath levels with its own
+    hermitian Hamiltonian h_b and a real coupling V (nf x nbath, N(0, vscale^2)); the embedding
+    self-energy is V g0(h_b) V^dagger.  Returns a list of dicts with these inputs."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(nprob):
+        d = int(rng.choice(dims))
+        nt = int(rng.integers(nt_range[0], nt_range[1] + 1))
+        beta = float(rng.uniform(*beta_range))
+        hs = random_hermitian(rng, d)
+        hb = random_hermitian(rng, nbath)
+        V = rng.normal(0.0, vscale, (d, nbath))
+        out.append({"nf": d, "nt": nt, "ntau": ntau, "beta": beta, "h": h, "korder": korder, "hs": hs, "hb": hb,
+                    "V": V})
+    return out
+
+
 def random_hermitian(rng, d, scale=1.0):
     """d x d hermitian: diagonal N(0, scale^2), off-diagonal re, im ~ N(0, scale^2/2)."""
     a = rng.normal(0.0, scale, (d, d))
