@@ -48,6 +48,8 @@ struct ng_ctx {
     Shadow shG, shS;                 // FP32 copies of G and Sigma for NG_F32C
     void* ws_obs = nullptr;          // per-problem observables before the batch sum
     size_t ws_obs_bytes = 0;
+    void* ws_minv = nullptr;         // M_n^-1 per problem of the current step
+    size_t ws_minv_bytes = 0;
     void* ws_uni = nullptr;          // problem table of the element-wise step (nf = 4, 8)
     size_t ws_uni_bytes = 0;
     int uni_key_nb = -1;
@@ -185,6 +187,14 @@ double bulk_cmacs(const Grid& g, int n) {
 // launch bodies templated on the orbital dimension
 // ---------------------------------------------------------------------------------------
 template <int D>
+ng_status launch_minv(ng_ctx* c, const Grid& g, int n, const HermV& S, const FuncV& eps, cudaStream_t s) {
+    ng_status st = ensure(c, &c->ws_minv, &c->ws_minv_bytes, sizeof(cplx) * D * D * (size_t)g.nb);
+    if (st) return st;
+    k_minv_step<D><<<nblocks(g.nb, 128), 128, 0, s>>>(g, n, S, eps, (cplx*)c->ws_minv, c->d_status);
+    return check_launch(c, "k_minv_step");
+}
+
+template <int D>
 ng_status launch_timestep(ng_ctx* c, const Grid& g, int n, const HermV& G, const HermV& S, const FuncV& eps,
                           cudaStream_t s) {
     const int k = g.k, thr = 128;
@@ -194,7 +204,10 @@ ng_status launch_timestep(ng_ctx* c, const Grid& g, int n, const HermV& G, const
     const int b_les = (int)nblocks(it_les, thr), b_tv = (int)nblocks(it_tv, thr), b_ret = (int)nblocks(it_ret, thr);
     long e0 = prof_pair(c, 0);
     if (e0 >= 0) cudaEventRecord(c->ev_pool[e0], s);
-    k_step_bulk<D><<<b_les + b_tv + b_ret, thr, 0, s>>>(g, n, G, S, eps, b_les, b_tv, b_ret, c->d_status);
+    ng_status sm = launch_minv<D>(c, g, n, S, eps, s);
+    if (sm) return sm;
+    k_step_bulk<D><<<b_les + b_tv + b_ret, thr, 0, s>>>(g, n, G, S, eps, (const cplx*)c->ws_minv, b_les, b_tv, b_ret,
+                                                        c->d_status);
     ng_status st = check_launch(c, "k_step_bulk");
     if (st) return st;
     if (e0 >= 0) {
@@ -258,7 +271,9 @@ ng_status launch_timestep32(ng_ctx* c, const Grid& g, int n, const HermV& G, con
     const int b_les = (int)nblocks(it_les, thr), b_tv = (int)nblocks(it_tv, thr), b_ret = (int)nblocks(it_ret, thr);
     long e0 = prof_pair(c, 0);
     if (e0 >= 0) cudaEventRecord(c->ev_pool[e0], s);
-    k_step_bulk32<D><<<b_les + b_tv + b_ret, thr, 0, s>>>(g, n, G, S, c->shG.v, c->shS.v, eps, b_les, b_tv, b_ret,
+    if ((st = launch_minv<D>(c, g, n, S, eps, s))) return st;
+    k_step_bulk32<D><<<b_les + b_tv + b_ret, thr, 0, s>>>(g, n, G, S, c->shG.v, c->shS.v, eps,
+                                                          (const cplx*)c->ws_minv, b_les, b_tv, b_ret,
                                                           c->d_status);
     if ((st = check_launch(c, "k_step_bulk32"))) return st;
     if (e0 >= 0) {
@@ -545,6 +560,7 @@ void ng_destroy(ng_ctx* c) {
     cudaFree(c->shS.buf);
     cudaFree(c->ws_obs);
     cudaFree(c->ws_uni);
+    cudaFree(c->ws_minv);
     delete c;
 }
 

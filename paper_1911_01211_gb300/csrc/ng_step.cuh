@@ -29,6 +29,7 @@ __device__ __forceinline__ void greg_for(const NgWeights& W, int L, int lmax, F&
     const int e1 = min(k, lmax);
     for (int l = 0; l <= e1; ++l) f(l, W.omega[l]);
     const int e2 = min(L - k - 1, lmax);
+#pragma unroll 4
     for (int l = k + 1; l <= e2; ++l) f(l, 1.0);
     for (int l = L - k; l <= lmax; ++l) f(l, W.omega[L - l]);
 }
@@ -192,8 +193,33 @@ __device__ __forceinline__ void les_item(const NgWeights& W, const Grid& g, cons
 // lesser (B) items, then the left-mixing row, then the retarded (B) items.  Items are
 // (column, problem) pairs with the problem index fastest, so a warp reads contiguous
 // problem vectors of each history element.
+// M_n^-1 of every problem of the batch, once per step (one thread per problem); minv_ws
+// holds D x D complex per problem
 template <int D>
-__global__ void __launch_bounds__(128) k_step_bulk(Grid g, int n, HermV G, HermV S, FuncV eps,
+__global__ void k_minv_step(Grid g, int n, HermV S, FuncV eps, cplx* minv_ws, int* status) {
+    const int kb = blockIdx.x * blockDim.x + threadIdx.x;
+    if (kb >= g.nb) return;
+    const NgWeights& W = c_W[g.k - 1];
+    int sing = 0;
+    Mat<D> Mi = minv<D>(step_matrix<D>(W, g, S, eps, n, kb), &sing);
+    if (sing) atomicOr(status, NGF_SINGULAR);
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = 0; b < D; ++b) minv_ws[((int64_t)kb * D + a) * D + b] = Mi.v[a][b];
+}
+template <int D>
+__device__ __forceinline__ Mat<D> ld_minv(const cplx* minv_ws, int kb) {
+    Mat<D> r;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = 0; b < D; ++b) r.v[a][b] = minv_ws[((int64_t)kb * D + a) * D + b];
+    return r;
+}
+
+template <int D>
+__global__ void __launch_bounds__(128) k_step_bulk(Grid g, int n, HermV G, HermV S, FuncV eps, const cplx* minv_ws,
                                                    int nb_les, int nb_tv, int nb_ret, int* status) {
     const NgWeights& W = c_W[g.k - 1];
     int blk = blockIdx.x;
@@ -209,9 +235,7 @@ __global__ void __launch_bounds__(128) k_step_bulk(Grid g, int n, HermV G, HermV
     else if (task == 1) ncol = g.ntau + 1;  // m = 0..ntau
     else ncol = n - W.k;                    // m = 0..n-k-1
     if (col >= ncol) return;
-    int sing = 0;
-    Mat<D> Minv = minv<D>(step_matrix<D>(W, g, S, eps, n, kb), &sing);
-    if (sing) atomicOr(status, NGF_SINGULAR);
+    const Mat<D> Minv = ld_minv<D>(minv_ws, kb);
     if (task == 0) les_item<D>(W, g, G, S, Minv, n, (int)col + 1, kb, status);
     else if (task == 1) tv_item<D>(W, g, G, S, Minv, n, (int)col, kb, status);
     else ret_item<D>(W, g, G, S, Minv, n, (int)col, kb, status);

@@ -231,7 +231,8 @@ __device__ __forceinline__ void les_item32(const NgWeights& W, const Grid& g, co
 
 template <int D>
 __global__ void __launch_bounds__(128) k_step_bulk32(Grid g, int n, HermV G, HermV S, HermV32 G32, HermV32 S32,
-                                                     FuncV eps, int nb_les, int nb_tv, int nb_ret, int* status) {
+                                                     FuncV eps, const cplx* minv_ws, int nb_les, int nb_tv,
+                                                     int nb_ret, int* status) {
     const NgWeights& W = c_W[g.k - 1];
     int blk = blockIdx.x;
     int task;
@@ -246,9 +247,7 @@ __global__ void __launch_bounds__(128) k_step_bulk32(Grid g, int n, HermV G, Her
     else if (task == 1) ncol = g.ntau + 1;
     else ncol = n - W.k;
     if (col >= ncol) return;
-    int sing = 0;
-    Mat<D> Minv = minv<D>(step_matrix<D>(W, g, S, eps, n, kb), &sing);
-    if (sing) atomicOr(status, NGF_SINGULAR);
+    const Mat<D> Minv = ld_minv<D>(minv_ws, kb);
     if (task == 0) les_item32<D>(W, g, G, S, G32, S32, Minv, n, (int)col + 1, kb, status);
     else if (task == 1) tv_item32<D>(W, g, G, S, G32, S32, Minv, n, (int)col, kb, status);
     else ret_item32<D>(W, g, G, S, G32, S32, Minv, n, (int)col, kb, status);
