@@ -320,33 +320,33 @@ def run_ours(a):
                   "E_tot_drift_after_pulse": float(np.ptp(Eafter)) if len(Eafter) else None,
                   "E_tot_at_end": float(vals[w.nt][4]), "E_kin_at_end": float(vals[w.nt][1]),
                   "E_corr_at_end": float(vals[w.nt][3]), "samples": len(vals)}
-    f32c = None
+    modes = {}
     if a.precision == "both":
-        # FP32-compensated time steps from the same setup (slices 0..k are not touched by the
-        # stepping), same timed window; error against the FP64 run on the final slice n = nt
-        # (all k-points, ret row / les column / tv row) and on rho_loc(t) for every t.
+        # FP32-compensated and double-float time steps, each re-propagated from the same setup
+        # (slices 0..k are not touched by the stepping) over the same timed window; error
+        # against the FP64 run on the final slice n = nt (all k-points, ret row / les column /
+        # tv row) and on rho_loc(t) for every t.
         nt = w.nt
-        ref = {"ret": G.ret[ng.tri(nt):ng.tri(nt) + nt + 1].clone(), "les": G.les[ng.tri(nt):ng.tri(nt) + nt + 1].clone(),
-               "tv": G.tv[nt * (w.ntau + 1):(nt + 1) * (w.ntau + 1)].clone()}
-        ms32, prof32, clk32, _ = propagate(ng.NG_F32C)
-        st32, flags32 = ctx.status_sync()
-        err = {}
-        for c, r in ref.items():
-            x = {"ret": G.ret[ng.tri(nt):ng.tri(nt) + nt + 1], "les": G.les[ng.tri(nt):ng.tri(nt) + nt + 1],
-                 "tv": G.tv[nt * (w.ntau + 1):(nt + 1) * (w.ntau + 1)]}[c]
-            err[c] = float((x - r).abs().max() / r.abs().max())
-        rho32 = rho_host[k + 1:].numpy()
-        err["rho_loc_abs"] = float(np.abs(rho32 - rho).max())
-        v32 = world * w.nbatch * K / (ms32 / 1e3)
-        ach32 = prof32["bulk_flops"] / (prof32["bulk_ms"] / 1e3) / 1e12
-        f32c = {"value": v32, "unit": "k-point timesteps/s", "ms_per_step": ms32 / K, "dtype": "f32c",
-                "speedup_vs_f64": v32 / (world * w.nbatch * K / (ms / 1e3)),
-                "max_rel_err_vs_f64_final_slice": err,
-                "bulk_kernel": {"kernel": "k_step_bulk32<1>", "algorithmic_fp64_equiv_tflops": ach32,
-                                "avg_launch_ms": prof32["bulk_ms"] / max(1, prof32["bulk_launches"]),
-                                "share_of_timed": prof32["bulk_ms"] / ms32,
-                                "history_gbs": prof32["bulk_flops"] / 8.0 * 8.0 / (prof32["bulk_ms"] / 1e3) / 1e9},
-                "clocks": clk32, "device_status": {"status": st32, "flags": flags32}}
+        sl = lambda: {"ret": G.ret[ng.tri(nt):ng.tri(nt) + nt + 1], "les": G.les[ng.tri(nt):ng.tri(nt) + nt + 1],
+                      "tv": G.tv[nt * (w.ntau + 1):(nt + 1) * (w.ntau + 1)]}
+        ref = {c: x.clone() for c, x in sl().items()}
+        bytes_per_elem = {"f32c": 8, "df64": 16}
+        for name, prec, kern in (("f32c", ng.NG_F32C, "k_step_bulk32<1>"), ("df64", ng.NG_DF64, "k_step_bulkdf<1>")):
+            msm, profm, clkm, _ = propagate(prec)
+            stm, flagsm = ctx.status_sync()
+            err = {c: float((x - ref[c]).abs().max() / ref[c].abs().max()) for c, x in sl().items()}
+            err["rho_loc_abs"] = float(np.abs(rho_host[k + 1:].numpy() - rho).max())
+            vm = world * w.nbatch * K / (msm / 1e3)
+            cmacs = profm["bulk_flops"] / (8.0 * w.nf ** 3)
+            modes[name] = {
+                "value": vm, "unit": "k-point timesteps/s", "ms_per_step": msm / K, "dtype": name,
+                "speedup_vs_f64": vm / value, "max_rel_err_vs_f64_final_slice": err,
+                "bulk_kernel": {"kernel": kern,
+                                "algorithmic_fp64_equiv_tflops": profm["bulk_flops"] / (profm["bulk_ms"] / 1e3) / 1e12,
+                                "history_gbs": cmacs * bytes_per_elem[name] / (profm["bulk_ms"] / 1e3) / 1e9,
+                                "avg_launch_ms": profm["bulk_ms"] / max(1, profm["bulk_launches"]),
+                                "share_of_timed": profm["bulk_ms"] / msm},
+                "clocks": clkm, "device_status": {"status": stm, "flags": flagsm}}
     if rank != 0:
         return
     line = {
@@ -370,8 +370,7 @@ def run_ours(a):
                         "N_loc_last": float(np.real(-1j * rho[-1]))},
         "properties": properties,
     }
-    if f32c is not None:
-        line["f32c"] = f32c
+    line.update(modes)
     if world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, list(range(n_first_timed, w.nt + 1)))
     print(json.dumps(line), flush=True)

@@ -92,8 +92,10 @@ typedef struct {
 /* NG_FP64: every sum in FP64.  NG_F32C: the O(n) and O(ntau) history and source sums of the
  * time step read FP32 copies of the history and accumulate exact FP32 products with Kahan
  * compensation (rounded once to FP64); BDF terms, the per-step matrix inverses, the (A)
- * boundary steps, the start-up and the Matsubara solve stay FP64. */
-typedef enum { NG_FP64 = 0, NG_F32C = 1 } ng_precision;
+ * boundary steps, the start-up and the Matsubara solve stay FP64.  NG_DF64: the same sums in
+ * double-float arithmetic (each value an FP32 pair, 48 significand bits; products with their
+ * cross terms, TwoSum accumulation), FP64-class accuracy on the FP32 pipes. */
+typedef enum { NG_FP64 = 0, NG_F32C = 1, NG_DF64 = 2 } ng_precision;
 
 /* Parameters of the self-consistent second-Born driver (ng_run_2b). */
 typedef struct {
@@ -165,7 +167,8 @@ ng_status ng_dyson_start(ng_ctx *ctx, const ng_grid *grid, ng_herm G, ng_herm Si
  * step per tau_m; lesser column by conjugate single steps for 1 <= m <= tstp-k-1 (B) and
  * serial VIDE steps (A) for m >= tstp-k (the whole column by (A) when tstp <= 2k).
  * Reads slices < tstp of G, slices <= tstp of Sigma and eps; writes slice tstp of G.
- * precision: NG_FP64 or NG_F32C.  With NG_F32C the context keeps FP32 copies of G (ldk =
+ * precision: NG_FP64, NG_F32C or NG_DF64 (the last two for nf <= 2; NG_DF64 keeps 16-byte
+ * double-float copies, otherwise as NG_F32C).  With NG_F32C the context keeps FP32 copies of G (ldk =
  * nbatch) and Sigma: slices < tstp are converted once when tstp first reaches them, Sigma's
  * slice tstp on every call.  Call ng_precision_reset after changing slices < tstp of G or
  * Sigma in place (the copies are also rebuilt when the buffers or the grid change).

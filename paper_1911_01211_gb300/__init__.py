@@ -22,7 +22,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libng.so")
 
 NG_OK, NG_EINVAL, NG_ENOMEM, NG_ECUDA, NG_ENOCONV, NG_ETIMEOUT, NG_ENONFINITE, NG_EUNSUPPORTED, NG_ESCRATCH = range(9)
-NG_FP64, NG_F32C = 0, 1
+NG_FP64, NG_F32C, NG_DF64 = 0, 1, 2
 _STATUS_NAMES = ["NG_OK", "NG_EINVAL", "NG_ENOMEM", "NG_ECUDA", "NG_ENOCONV", "NG_ETIMEOUT",
                  "NG_ENONFINITE", "NG_EUNSUPPORTED", "NG_ESCRATCH"]
 

@@ -11,6 +11,17 @@
 #include "ng_step32.cuh"
 #include "ng_obs.cuh"
 #include "ng_ubatch.cuh"
+#include "ng_stepdf.cuh"
+
+// double-float copy of one contour function (NG_DF64 time steps), as Shadow
+struct ShadowDF {
+    void* buf = nullptr;
+    size_t bytes = 0;
+    const void* key_ret = nullptr;
+    int key_nt = -1, key_ntau = -1, key_nf = -1, key_ldk = -1;
+    int upto = -2;
+    HermVdf v;
+};
 
 // FP32 copy of one contour function (NG_F32C time steps): the buffer, the identity of the
 // FP64 source it mirrors and the last slice converted (-2: nothing, -1: mat only).
@@ -46,6 +57,7 @@ struct ng_ctx {
     double prof_flops = 0.0;
     std::vector<int> ev_kind;        // 0 bulk, 1 boundary, per event pair
     Shadow shG, shS;                 // FP32 copies of G and Sigma for NG_F32C
+    ShadowDF dfG, dfS;               // double-float copies of G and Sigma for NG_DF64
     void* ws_obs = nullptr;          // per-problem observables before the batch sum
     size_t ws_obs_bytes = 0;
     void* ws_minv = nullptr;         // M_n^-1 per problem of the current step
@@ -256,6 +268,69 @@ ng_status update_shadow(ng_ctx* c, Shadow& sh, const Grid& g, const HermV& X, in
     }
     if (current && (st = conv(n, n))) return st;
     return NG_OK;
+}
+
+ng_status update_shadow_df(ng_ctx* c, ShadowDF& sh, const Grid& g, const HermV& X, int n, bool current, cudaStream_t s) {
+    const int dd = g.nf * g.nf, ldk = X.ret.ldk, T1 = g.ntau + 1;
+    if (sh.key_ret != X.ret.p || sh.key_nt != g.nt || sh.key_ntau != g.ntau || sh.key_nf != g.nf || sh.key_ldk != ldk) {
+        const size_t el = (size_t)T1 + 2 * (size_t)tri(g.nt + 1) + (size_t)(g.nt + 1) * T1;
+        ng_status st = ensure(c, &sh.buf, &sh.bytes, sizeof(float4) * el * dd * ldk);
+        if (st) return st;
+        float4* p = (float4*)sh.buf;
+        sh.v.mat = Comp64x{p, ldk};
+        sh.v.ret = Comp64x{p + (size_t)T1 * dd * ldk, ldk};
+        sh.v.les = Comp64x{sh.v.ret.p + (size_t)tri(g.nt + 1) * dd * ldk, ldk};
+        sh.v.tv = Comp64x{sh.v.les.p + (size_t)tri(g.nt + 1) * dd * ldk, ldk};
+        sh.key_ret = X.ret.p;
+        sh.key_nt = g.nt;
+        sh.key_ntau = g.ntau;
+        sh.key_nf = g.nf;
+        sh.key_ldk = ldk;
+        sh.upto = -2;
+    }
+    auto conv = [&](int n0, int n1) -> ng_status {
+        if (n1 < n0 || n1 < -1) return NG_OK;
+        const int a = n0 < 0 ? 0 : n0;
+        const int64_t items = (2 * (tri(n1 + 1) - tri(a)) + (int64_t)(n1 - a + 1) * T1 + (n0 < 0 ? T1 : 0)) * dd * ldk;
+        const unsigned blocks = (unsigned)std::min<int64_t>((items + 255) / 256, 152 * 16);
+        k_shadow_df<<<blocks, 256, 0, s>>>(g, n0, n1, X, sh.v, ldk);
+        return check_launch(c, "k_shadow_df");
+    };
+    ng_status st;
+    if (sh.upto < n - 1) {
+        if ((st = conv(sh.upto + 1, n - 1))) return st;
+        sh.upto = n - 1;
+    }
+    if (current && (st = conv(n, n))) return st;
+    return NG_OK;
+}
+
+template <int D>
+ng_status launch_timestepdf(ng_ctx* c, const Grid& g, int n, const HermV& G, const HermV& S, const FuncV& eps,
+                            cudaStream_t s) {
+    ng_status st;
+    if ((st = update_shadow_df(c, c->dfG, g, G, n, false, s))) return st;
+    if ((st = update_shadow_df(c, c->dfS, g, S, n, true, s))) return st;
+    const int k = g.k, thr = 128;
+    const int64_t it_les = (n >= 2 * k + 1) ? (int64_t)g.nb * (n - k - 1) : 0;
+    const int64_t it_tv = (int64_t)g.nb * (g.ntau + 1);
+    const int64_t it_ret = (int64_t)g.nb * (n - k);
+    const int b_les = (int)nblocks(it_les, thr), b_tv = (int)nblocks(it_tv, thr), b_ret = (int)nblocks(it_ret, thr);
+    if ((st = launch_minv<D>(c, g, n, S, eps, s))) return st;
+    long e0 = prof_pair(c, 0);
+    if (e0 >= 0) cudaEventRecord(c->ev_pool[e0], s);
+    k_step_bulkdf<D><<<b_les + b_tv + b_ret, thr, 0, s>>>(g, n, G, c->dfG.v, c->dfS.v, (const cplx*)c->ws_minv, b_les,
+                                                          b_tv, b_ret, c->d_status);
+    if ((st = check_launch(c, "k_step_bulkdf"))) return st;
+    if (e0 >= 0) {
+        cudaEventRecord(c->ev_pool[e0 + 1], s);
+        c->prof_flops += 8.0 * D * D * D * bulk_cmacs(g, n);
+    }
+    long e1 = prof_pair(c, 1);
+    if (e1 >= 0) cudaEventRecord(c->ev_pool[e1], s);
+    k_step_boundary<D><<<g.nb, NG_BND_THREADS, 0, s>>>(g, n, G, S, eps, c->d_status);
+    if (e1 >= 0) cudaEventRecord(c->ev_pool[e1 + 1], s);
+    return check_launch(c, "k_step_boundary");
 }
 
 template <int D>
@@ -471,9 +546,11 @@ ng_status utimestep_uniform(ng_ctx* c, const Grid& g, int n, const HermV& G, con
 ng_status do_timestep(ng_ctx* c, const Grid& g, int n, const HermV& G, const HermV& S, const FuncV& eps, cudaStream_t s,
                       int precision = NG_FP64) {
     if (g.nf > 2) {
-        if (precision != NG_FP64) return fail(c, NG_EUNSUPPORTED, "NG_F32C needs nf <= 2");
+        if (precision != NG_FP64) return fail(c, NG_EUNSUPPORTED, "NG_F32C and NG_DF64 need nf <= 2");
         return utimestep_uniform(c, g, n, G, S, eps, s);
     }
+    if (precision == NG_DF64)
+        return g.nf == 1 ? launch_timestepdf<1>(c, g, n, G, S, eps, s) : launch_timestepdf<2>(c, g, n, G, S, eps, s);
     if (precision == NG_F32C)
         return g.nf == 1 ? launch_timestep32<1>(c, g, n, G, S, eps, s) : launch_timestep32<2>(c, g, n, G, S, eps, s);
     return g.nf == 1 ? launch_timestep<1>(c, g, n, G, S, eps, s) : launch_timestep<2>(c, g, n, G, S, eps, s);
@@ -558,6 +635,8 @@ void ng_destroy(ng_ctx* c) {
     cudaFree(c->ws_prev);
     cudaFree(c->shG.buf);
     cudaFree(c->shS.buf);
+    cudaFree(c->dfG.buf);
+    cudaFree(c->dfS.buf);
     cudaFree(c->ws_obs);
     cudaFree(c->ws_uni);
     cudaFree(c->ws_minv);
@@ -665,7 +744,8 @@ ng_status ng_dyson_timestep(ng_ctx* c, const ng_grid* grid, int tstp, ng_herm G,
     ng_status st;
     if ((st = check_grid(c, grid, &g))) return st;
     if (tstp <= g.k || tstp > g.nt) return fail(c, NG_EINVAL, "tstp = %d must be in k+1..nt = %d..%d", tstp, g.k + 1, g.nt);
-    if (precision != NG_FP64 && precision != NG_F32C) return fail(c, NG_EINVAL, "unknown precision %d", precision);
+    if (precision != NG_FP64 && precision != NG_F32C && precision != NG_DF64)
+        return fail(c, NG_EINVAL, "unknown precision %d", precision);
     if ((st = check_herm(c, g, G, "G", true, &Gv, g.nb))) return st;
     if ((st = check_herm(c, g, S, "Sigma", true, &Sv, 0))) return st;
     if ((st = check_func(c, g, eps, "eps", &ev))) return st;
@@ -701,6 +781,10 @@ ng_status ng_precision_reset(ng_ctx* c) {
     c->shG.key_ret = nullptr;
     c->shS.upto = -2;
     c->shS.key_ret = nullptr;
+    c->dfG.upto = -2;
+    c->dfG.key_ret = nullptr;
+    c->dfS.upto = -2;
+    c->dfS.key_ret = nullptr;
     return NG_OK;
 }
 
@@ -806,7 +890,8 @@ ng_status ng_run_2b(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm Gloc, ng_
     if (U.ldk != 1) return fail(c, NG_EINVAL, "U.ldk must be 1");
     if (epsmf.ldk != G.ldk) return fail(c, NG_EINVAL, "eps_mf.ldk must equal G.ldk");
     if (p->corrector < 1) return fail(c, NG_EINVAL, "corrector must be >= 1");
-    if (p->precision != NG_FP64 && p->precision != NG_F32C) return fail(c, NG_EINVAL, "unknown precision %d", p->precision);
+    if (p->precision != NG_FP64 && p->precision != NG_F32C && p->precision != NG_DF64)
+        return fail(c, NG_EINVAL, "unknown precision %d", p->precision);
     if (p->n_to > g.nt || (p->n_to >= p->n_from && p->n_from <= g.k))
         return fail(c, NG_EINVAL, "stepping range %d..%d invalid (k = %d, nt = %d)", p->n_from, p->n_to, g.k, g.nt);
     cudaStream_t s = (cudaStream_t)stream;
