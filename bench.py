@@ -50,8 +50,11 @@ def parse():
     ap.add_argument("--nt", type=int, default=2000)
     ap.add_argument("--ntau", type=int, default=800)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["chain", "uneven"], default="chain",
-                    help="chain: the headline chain_kspace run; uneven: the 64-cluster uneven batch")
+    ap.add_argument("--workload", choices=["chain", "uneven", "adjoint"], default="chain",
+                    help="chain: the headline chain_kspace run; uneven: the 64-cluster uneven batch; "
+                         "adjoint: gradient of E_kin(t_N) on the 16x16 square lattice")
+    ap.add_argument("--fd-slices", type=int, default=20, help="adjoint: time slices checked by central differences")
+    ap.add_argument("--adj-nt", type=int, default=1000, help="adjoint: nt (development override)")
     ap.add_argument("--nprob", type=int, default=64, help="problems of the uneven batch")
     ap.add_argument("--precision", choices=["f64", "both"], default="both",
                     help="f64: the FP64 headline only; both: also time the FP32-compensated mode")
@@ -434,11 +437,89 @@ def run_uneven(a):
     batch.close()
 
 
+def run_adjoint(a):
+    """Gradient dE_kin(t_N)/dA(t_n), n = 1..N, on the square_kspace model (16 x 16 k-points,
+    nt = 1000, ntau = 400, h = 0.02, beta = 10, U = 1.5, 3 corrector passes, Peierls pulse
+    A0 = 0.5, omega = 2, t0 = 5, sigma = 1.5): FP64 forward (Matsubara loop, bootstrapping, all
+    time steps) and the discrete adjoint, each timed with CUDA events; the gradient is checked
+    against central finite differences of the GPU forward (delta = 1e-6) on seeded slices."""
+    import numpy as np
+    import torch
+    import paper_1911_01211_gb300 as ng
+    from paper_1911_01211_gb300 import workloads as wl
+    from paper_1911_01211_gb300.adjoint import densities
+    L, nt, ntau, beta, h, U = 16, a.adj_nt, 400, 10.0, 0.02, 1.5
+    g = ng.Grid(nt=nt, ntau=ntau, nf=1, nbatch=L * L, korder=5, h=h, beta=beta)
+    ctx = ng.Context(5)
+    kx, ky = np.meshgrid(2 * np.pi * np.arange(L) / L, 2 * np.pi * np.arange(L) / L, indexing="ij")
+    kx = torch.as_tensor(kx.ravel(), device="cuda")
+    ky = torch.as_tensor(ky.ravel(), device="cuda")
+    t = np.concatenate([[0.0], h * np.arange(nt + 1)])
+    A0 = wl.pulse_A(t)
+    A0[0] = 0.0
+    Ut = torch.full((nt + 2,), U, dtype=torch.float64, device="cuda")
+
+    def loss(A):
+        e0 = -2.0 * torch.cos(kx[None, :] - A[:, None]) - 2.0 * torch.cos(ky[None, :])
+        rho = densities(e0, ctx, g, Ut)
+        return (rho[nt].real * e0[nt + 1]).mean()
+
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    At = torch.tensor(A0, dtype=torch.float64, device="cuda", requires_grad=True)
+    loss(At)            # warm-up (context workspaces, library load)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    ev[0].record()
+    Lv = loss(At)
+    ev[1].record()
+    Lv.backward()
+    ev[2].record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    t_fwd, t_bwd = ev[0].elapsed_time(ev[1]) / 1e3, ev[1].elapsed_time(ev[2]) / 1e3
+    grad = At.grad.cpu().numpy()
+    rng = np.random.default_rng(191101211)
+    idx = sorted(rng.choice(np.arange(2, nt + 2), a.fd_slices, replace=False).tolist()) if a.fd_slices > 0 else []
+    fd = []
+    delta = 1e-6
+    with torch.no_grad():
+        for i in idx:
+            vals = []
+            for sgn in (1.0, -1.0):
+                Ap = torch.tensor(A0, dtype=torch.float64, device="cuda")
+                Ap[i] += sgn * delta
+                vals.append(loss(Ap).item())
+            fd.append((vals[0] - vals[1]) / (2 * delta))
+    fd = np.array(fd)
+    gi = grad[idx] if idx else np.zeros(0)
+    err = float(np.abs(gi - fd).max() / np.abs(fd).max()) if idx else None
+    per = [float(abs(x - y) / max(abs(y), 1e-300)) for x, y in zip(gi, fd)]
+    units = L * L * (nt - 5)
+    line = {"metric": "adjoint gradient k-point timesteps/s", "value": units / t_bwd,
+            "unit": "k-point timesteps/s (backward sweep)", "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": 1e3 * t_bwd / (nt - 5), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"square_kspace 16x16 nt={nt} ntau={ntau} h={h} beta={beta} U={U} k=5 corrector=3, "
+                                   "loss E_kin(t_N), parameters A(t_1..t_N)",
+                       "segment_steps": int(np.ceil(np.sqrt(nt - 5)))},
+            "forward_s": t_fwd, "backward_s": t_bwd, "backward_over_forward": t_bwd / t_fwd,
+            "loss": Lv.item(),
+            "fd_check": {"slices": [int(i) - 1 for i in idx], "delta": delta, "max_rel_err_normwise": err,
+                         "max_rel_err_per_slice": max(per) if per else None,
+                         "median_rel_err_per_slice": float(np.median(per)) if per else None},
+            "grad_norm_inf": float(np.abs(grad).max()), "clocks": clk,
+            "device_status": dict(zip(("status", "flags"), ctx.status_sync()))}
+    print(json.dumps(line), flush=True)
+
+
 if __name__ == "__main__":
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "uneven":
         run_uneven(args)
+    elif args.workload == "adjoint":
+        run_adjoint(args)
     else:
         run_ours(args)

@@ -318,6 +318,33 @@ ng_status ng_run_2b(ng_ctx *ctx, const ng_grid *grid, ng_herm G, ng_herm Gloc, n
 ng_status ng_solve_fixed(ng_ctx *ctx, const ng_grid *grid, ng_herm G, ng_herm Sigma,
                          ng_func eps, int n_to, void *stream);
 
+/* ---- adjoint -------------------------------------------------------------------------- */
+
+/* Discrete adjoint (reverse mode) of ng_run_2b for nf = 1: the exact gradient of a real loss
+ * L of the densities G_kb^<(t_n, t_n) with respect to the bare dispersion eps0_kb(t_n),
+ * n = 0..nt, through the algorithm as executed in FP64 (predictor, p->corrector passes of
+ * {Gloc, Hartree, second-Born, Dyson time step} per step, mixed schedule, and the
+ * bootstrapped start slices 0..k, Sec. "Time stepping", "Start", "Hubbard chain").  The
+ * paper has no adjoint; the method's own equations are transposed step by step.
+ * Precondition: G, Gloc, Sigma, eps_mf hold the state that ng_run_2b (do_setup = 1,
+ * stepping k+1..nt, FP64, the same p->corrector) left; eps0 and U are its inputs.
+ * seed (device, [nt+1][nbatch] complex128): c_kb(n) = dL/dRe G^<_kb(n,n) + i dL/dIm G^<_kb(n,n).
+ * cG (ldk = nbatch) and cS (ldk = 1): caller-owned herm buffers shaped like G and Sigma
+ * (mat unused), overwritten with the cotangents of the final history.
+ * The corrector iterates are recomputed from the kept history in segments of `segment` steps
+ * (0: ceil(sqrt(nt - k))), each re-run forward with its iterates held in the context, then
+ * walked backwards.  The start slices are a fixed point of the bootstrapping; their adjoint
+ * is iterated to |change| <= p->boot_tol |mu| (default 1e-14), at most p->boot_maxiter times.
+ * grad_eps0 (device, [nt+2][nbatch] double): dL/deps0_kb(t_n) at index n+1 (row 0 unused).
+ * G, Gloc, Sigma and eps_mf are rewritten with bitwise-equal values by the recomputation.
+ * info (host, may be NULL) receives {start-slice iterations, segments, segment length}.
+ * Errors: NG_EUNSUPPORTED for nf != 1; NG_EINVAL for bad layouts; NG_ENOCONV if the start-slice
+ * adjoint did not converge; NG_ENOMEM if the context workspace cannot be allocated. */
+ng_status ng_adjoint_2b(ng_ctx *ctx, const ng_grid *grid, ng_herm G, ng_herm Gloc, ng_herm Sigma,
+                        ng_func eps0, ng_func eps_mf, ng_func U, const ng_run_params *p,
+                        const void *seed, ng_herm cG, ng_herm cS, int segment, double *grad_eps0,
+                        int *info, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

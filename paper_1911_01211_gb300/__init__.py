@@ -89,6 +89,9 @@ SIGNATURES = {
     "ng_dyson_start_noalloc": (ctypes.c_int, [_G, ng_herm, ng_herm, ng_func, _P]),
     "ng_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "ng_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
+    "ng_adjoint_2b": (ctypes.c_int, [_P, _G, ng_herm, ng_herm, ng_herm, ng_func, ng_func, ng_func,
+                                     ctypes.POINTER(ng_run_params), _P, ng_herm, ng_herm, ctypes.c_int, _P,
+                                     ctypes.POINTER(ctypes.c_int), _P]),
 }
 
 _lib = None
@@ -339,3 +342,16 @@ class Context:
         if not (allow_noconv and st == NG_ENOCONV):
             self._chk(st)
         return list(iters)
+
+    def adjoint_2b(self, grid, G, Gloc, S, eps0, eps_mf, U, seed, cG, cS, grad_eps0, corrector=3, nbar=0.5,
+                   boot_tol=1e-14, boot_maxiter=200, segment=0, stream=None):
+        """ng_adjoint_2b: seed = device complex128 [nt+1, nbatch] cotangent of G^<_kb(n,n);
+        grad_eps0 = device float64 [nt+2, nbatch] (index n+1).  Returns
+        [start-slice iterations, segments, segment length]."""
+        p = ng_run_params(corrector, 0.0, 0, boot_tol, boot_maxiter, nbar, grid.korder + 1, grid.nt, 0, NG_FP64)
+        info = (ctypes.c_int * 3)()
+        self._chk(self.lib.ng_adjoint_2b(self.h, ctypes.byref(grid.c()), G.c(), Gloc.c(), S.c(), eps0.c(),
+                                         eps_mf.c(), U.c(), ctypes.byref(p), ctypes.c_void_p(seed.data_ptr()),
+                                         cG.c(), cS.c(), segment, ctypes.c_void_p(grad_eps0.data_ptr()), info,
+                                         _stream(stream)))
+        return list(info)

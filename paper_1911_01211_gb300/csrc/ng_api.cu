@@ -12,6 +12,8 @@
 #include "ng_obs.cuh"
 #include "ng_ubatch.cuh"
 #include "ng_stepdf.cuh"
+#include "ng_adjoint_types.h"
+#include <cmath>
 
 // double-float copy of one contour function (NG_DF64 time steps), as Shadow
 struct ShadowDF {
@@ -66,6 +68,8 @@ struct ng_ctx {
     size_t ws_uni_bytes = 0;
     int uni_key_nb = -1;
     const void *uni_key_G = nullptr, *uni_key_S = nullptr, *uni_key_eps = nullptr;
+    void* ws_adj = nullptr;          // adjoint: iterate store, work vectors, start-slice buffers
+    size_t ws_adj_bytes = 0;
 };
 
 namespace {
@@ -609,7 +613,11 @@ ng_status ng_create(int korder, int device, ng_ctx** out) {
     if (device >= 0 && device < 64 && !g_weights_loaded[device]) {
         NgWeights all[NG_KMAX];
         for (int k = 1; k <= NG_KMAX; ++k) ng_make_weights(k, &all[k - 1]);
-        if (cudaMemcpyToSymbol(c_W, all, sizeof(all)) != cudaSuccess) { cudaGetLastError(); delete c; return NG_ECUDA; }
+        if (cudaMemcpyToSymbol(c_W, all, sizeof(all)) != cudaSuccess || adj_load_weights(all) != cudaSuccess) {
+            cudaGetLastError();
+            delete c;
+            return NG_ECUDA;
+        }
         g_weights_loaded[device] = true;
     }
     if (cudaMalloc(&c->d_status, sizeof(int)) != cudaSuccess || cudaMalloc(&c->d_scalar, sizeof(double)) != cudaSuccess) {
@@ -640,6 +648,7 @@ void ng_destroy(ng_ctx* c) {
     cudaFree(c->ws_obs);
     cudaFree(c->ws_uni);
     cudaFree(c->ws_minv);
+    cudaFree(c->ws_adj);
     delete c;
 }
 
@@ -1263,3 +1272,287 @@ ng_status ng_batch_solve(ng_ctx* c, ng_batch* b, int* tuned_threads, void* strea
 }
 
 }  // extern "C"
+
+// =========================================================================================
+// Discrete adjoint of the second-Born time stepping (ng_adjoint_2b), nf = 1.
+// The final forward history is kept in full (every slice depends on all earlier ones); the
+// corrector iterates of slice n are recomputed from it segment by segment: the steps of a
+// segment are re-run forward with their iterates captured, then walked backwards.
+// =========================================================================================
+namespace {
+
+struct AdjLayout {
+    int64_t L;           // longest slice: 2 (nt+1) + ntau + 1
+    int64_t itstride;    // one captured pass: per-k slice, G_loc slice, Sigma slice, eps_mf(n)
+    int seg, corr;
+    cplx *store, *cw, *cSw, *cmfw, *cA, *caccR, *caccT, *crhs, *cMn, *retA, *part, *cLoc, *cmf;
+    double* ce0;
+    // start slices
+    int64_t E;
+    cplx *mu, *ctot, *ctot0, *Pk, *cSx, *cLb, *cmfx;
+    double* dist;
+};
+
+size_t adj_layout(const Grid& g, int seg, int corr, AdjLayout* A, char* base) {
+    const int64_t nb = g.nb, T = g.ntau, K1 = g.k + 1;
+    A->L = 2 * (int64_t)(g.nt + 1) + T + 1;
+    A->itstride = A->L * nb + 2 * A->L + nb;
+    A->seg = seg;
+    A->corr = corr;
+    A->E = boot_E(g.k, g.ntau);
+    size_t off = 0;
+    auto take = [&](int64_t count) {   // count complex numbers, 256-byte aligned
+        char* p = base ? base + off : nullptr;
+        off += (((size_t)count * sizeof(cplx)) + 255) / 256 * 256;
+        return (cplx*)p;
+    };
+    A->store = take((int64_t)seg * corr * A->itstride);
+    A->cw = take(A->L * nb);
+    A->cSw = take(A->L);
+    A->cmfw = take(nb);
+    A->cA = take((int64_t)NG_MAXQ * nb);
+    A->caccR = take((int64_t)(g.nt + 1) * nb);
+    A->caccT = take((T + 1) * nb);
+    A->crhs = take((int64_t)(g.nt + 1) * nb);
+    A->cMn = take(nb);
+    A->retA = take(K1 * K1 * nb);
+    A->part = take((int64_t)NG_ADJ_NPART * A->L);
+    A->cLoc = take(A->L);
+    A->cmf = take((int64_t)(g.nt + 2) * nb);
+    A->ce0 = (double*)take(((int64_t)(g.nt + 2) * nb + 1) / 2);
+    A->mu = take(A->E * nb);
+    A->ctot = take(A->E * nb);
+    A->ctot0 = take(A->E * nb);
+    A->Pk = take(A->E * nb);
+    A->cSx = take(A->E);
+    A->cLb = take(A->E);
+    A->cmfx = take((int64_t)(g.nt + 2) * nb);
+    A->dist = (double*)take(1);
+    return off;
+}
+
+// slice views: of a herm at step n (ld = nb or 1) ...
+SliceV herm_slice(const HermV& X, int n, int ntau) {
+    const int64_t ld = X.ret.ldk;
+    return SliceV{X.ret.p + tri(n) * ld, X.les.p + tri(n) * ld, X.tv.p + (int64_t)n * (ntau + 1) * ld};
+}
+// ... of one captured pass in the iterate store
+struct Captured {
+    SliceV Gk, Gl, S;
+    cplx* mf;
+};
+Captured captured(const AdjLayout& A, const Grid& g, int q, int it, int n) {
+    cplx* b = A.store + ((int64_t)q * A.corr + it) * A.itstride;
+    const int64_t nb = g.nb, n1 = n + 1;
+    Captured c;
+    c.Gk = SliceV{b, b + n1 * nb, b + 2 * n1 * nb};
+    cplx* l = b + A.L * nb;
+    c.Gl = SliceV{l, l + n1, l + 2 * n1};
+    cplx* s = l + A.L;
+    c.S = SliceV{s, s + n1, s + 2 * n1};
+    c.mf = s + A.L;
+    return c;
+}
+// ... of slice n of slices 0..k in the compact layout of ng_adjoint_types.h
+SliceV boot_slice(cplx* base, int64_t ld, int k, int ntau, int n) {
+    const int64_t T3 = tri(k + 1);
+    return SliceV{base + tri(n) * ld, base + (T3 + tri(n)) * ld, base + (2 * T3 + (int64_t)n * (ntau + 1)) * ld};
+}
+
+#define ADJ_TRY(ctx, call, what)                                                               \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) return fail(ctx, NG_ECUDA, "%s: %s", what, cudaGetErrorString(e_)); \
+    } while (0)
+
+// forward step n of the driver with the iterates of every corrector pass captured (FP64)
+ng_status adj_forward_step(ng_ctx* c, const Grid& g, int n, int corr, const HermV& Gv, const HermV& Lv, const HermV& Sv,
+                           const FuncV& mf, const FuncV& e0, const FuncV& uv, double nbar, const AdjLayout& A, int q,
+                           cudaStream_t s) {
+    ng_status st;
+    if ((st = do_extrap(c, g, n - 1, Gv, s))) return st;
+    for (int it = 0; it < corr; ++it) {
+        const Captured cp = captured(A, g, q, it, n);
+        if ((st = do_kreduce(c, g, n, Lv, Gv, s))) return st;
+        ADJ_TRY(c, adj_slice_copy(n, g.ntau, 1, herm_slice(Lv, n, g.ntau), cp.Gl, s), "capture of G_loc");
+        if ((st = do_hartree(c, g, n, mf, e0, Lv, uv, nbar, s))) return st;
+        CUDA_TRY(c, cudaMemcpyAsync(cp.mf, mf.p + (int64_t)(n + 1) * g.nb, sizeof(cplx) * g.nb,
+                                    cudaMemcpyDeviceToDevice, s));
+        if ((st = do_sigma(c, g, n, Sv, Lv, uv, s))) return st;
+        ADJ_TRY(c, adj_slice_copy(n, g.ntau, 1, herm_slice(Sv, n, g.ntau), cp.S, s), "capture of Sigma");
+        if ((st = do_timestep(c, g, n, Gv, Sv, mf, s, NG_FP64))) return st;
+        ADJ_TRY(c, adj_slice_copy(n, g.ntau, g.nb, herm_slice(Gv, n, g.ntau), cp.Gk, s), "capture of G");
+    }
+    return NG_OK;
+}
+
+// backward step n: the corrector passes in reverse, then the predictor
+ng_status adj_backward_step(ng_ctx* c, const Grid& g, int n, const HermV& Gv, const HermV& Sv, const FuncV& mf,
+                            const FuncV& uv, const HermV& cG, const HermV& cS, const AdjLayout& A, int q,
+                            cudaStream_t s) {
+    const int k = g.k, nb = g.nb, T = g.ntau;
+    const SliceV cw{A.cw, A.cw + (int64_t)(n + 1) * nb, A.cw + 2 * (int64_t)(n + 1) * nb};
+    const SliceV cSw{A.cSw, A.cSw + (n + 1), A.cSw + 2 * (n + 1)};
+    const SliceV cLoc{A.cLoc, A.cLoc + (n + 1), A.cLoc + 2 * (n + 1)};
+    // cotangents of the final slice n, of Sigma slice n and of eps_mf(n) start the last pass
+    ADJ_TRY(c, adj_slice_copy(n, T, nb, herm_slice(cG, n, T), cw, s), "gather of c(G)");
+    ADJ_TRY(c, adj_slice_copy(n, T, 1, herm_slice(cS, n, T), cSw, s), "gather of c(Sigma)");
+    CUDA_TRY(c, cudaMemcpyAsync(A.cmfw, A.cmf + (int64_t)(n + 1) * nb, sizeof(cplx) * nb, cudaMemcpyDeviceToDevice, s));
+    AdjStep a;
+    a.g = g;
+    a.n = n;
+    a.full = (n <= 2 * k);
+    a.m0 = a.full ? 1 : n - k;
+    a.nq = n - a.m0 + 1;
+    a.Gr = Gv.ret.p; a.Gl = Gv.les.p; a.Gt = Gv.tv.p; a.Gm = Gv.mat.p;
+    a.Sr = Sv.ret.p; a.Sl = Sv.les.p; a.St = Sv.tv.p;
+    a.mf = mf.p;
+    a.cGr = cG.ret.p; a.cGl = cG.les.p; a.cGt = cG.tv.p;
+    a.cSr = cS.ret.p; a.cSl = cS.les.p; a.cSt = cS.tv.p;
+    a.cmf = A.cmf;
+    a.cw = cw;
+    a.cSw = cSw;
+    a.cmfw = A.cmfw;
+    a.cA = A.cA; a.caccR = A.caccR; a.caccT = A.caccT; a.crhs = A.crhs; a.cMn = A.cMn; a.retA = A.retA;
+    a.part = A.part;
+    a.plen = A.L;
+    for (int it = A.corr - 1; it >= 0; --it) {
+        const Captured cp = captured(A, g, q, it, n);
+        a.Gc = cp.Gk;
+        a.Sc = cp.S;
+        a.mfc = cp.mf;
+        ADJ_TRY(c, adj_pass(a, cp.Gl, uv.p, cLoc, A.ce0 + (int64_t)(n + 1) * nb, s), "adjoint corrector pass");
+    }
+    ADJ_TRY(c, adj_predictor(g, n, cw, cG.ret.p, cG.les.p, cG.tv.p, s), "adjoint predictor");
+    return NG_OK;
+}
+
+// start slices 0..k: fixed point x = F(x, eps0) of the bootstrapping; implicit adjoint
+// mu = c_tot + F_x^T mu by iteration, then d/deps0 = F_eps^T mu
+ng_status adj_boot(ng_ctx* c, const Grid& g, const HermV& Gv, const HermV& Lv, const HermV& Sv, const FuncV& mf,
+                   const FuncV& uv, const HermV& cG, const HermV& cS, const AdjLayout& A, double tol, int maxiter,
+                   int* iters, cudaStream_t s) {
+    const int k = g.k, nb = g.nb, T = g.ntau;
+    const int64_t E = A.E;
+    ng_status st;
+    for (int n = 0; n <= k; ++n)   // G_loc slices 0..k of the final start slices
+        if ((st = do_kreduce(c, g, n, Lv, Gv, s))) return st;
+    // cotangent of the start slices: direct, plus through Sigma(0..k) and eps_mf(0..k)
+    ADJ_TRY(c, adj_boot_gather(g, cG.ret.p, cG.les.p, cG.tv.p, nb, A.ctot0, s), "start-slice gather");
+    auto through_sigma = [&](const cplx* cSig /* compact, ld 1 */, const cplx* cmfr, bool from_herm) -> ng_status {
+        for (int n = 0; n <= k; ++n) {
+            SliceV cs = from_herm ? herm_slice(cS, n, T) : boot_slice((cplx*)cSig, 1, k, T, n);
+            ADJ_TRY(c, adj_sigma2b(g, n, herm_slice(Lv, n, T), cs, cmfr + (int64_t)(n + 1) * nb, uv.p,
+                                   boot_slice(A.cLb, 1, k, T, n), s), "second-Born transpose (start slices)");
+        }
+        return NG_OK;
+    };
+    if ((st = through_sigma(nullptr, A.cmf, true))) return st;
+    ADJ_TRY(c, adj_ce0_rows(k + 1, nb, A.cmf, A.ce0, s), "eps0 cotangent (start slices)");
+    CUDA_TRY(c, cudaMemsetAsync(A.dist, 0, 2 * sizeof(double), s));
+    ADJ_TRY(c, adj_boot_update(E, nb, A.ctot0, A.cLb, A.ctot, A.dist, s), "start-slice update");
+    CUDA_TRY(c, cudaMemcpyAsync(A.mu, A.ctot, sizeof(cplx) * E * nb, cudaMemcpyDeviceToDevice, s));
+    AdjBoot b;
+    b.g = g;
+    b.Gr = Gv.ret.p; b.Gl = Gv.les.p; b.Gt = Gv.tv.p; b.Gm = Gv.mat.p;
+    b.Sr = Sv.ret.p; b.Sl = Sv.les.p; b.St = Sv.tv.p;
+    b.mf = mf.p;
+    b.mu = A.mu;
+    b.Pk = A.Pk;
+    b.cmfx = A.cmfx;
+    auto start_vjp = [&]() -> ng_status {
+        CUDA_TRY(c, cudaMemsetAsync(A.Pk, 0, sizeof(cplx) * E * nb, s));
+        CUDA_TRY(c, cudaMemsetAsync(A.cmfx, 0, sizeof(cplx) * (size_t)(k + 2) * nb, s));
+        ADJ_TRY(c, adj_boot_start(b, s), "start-up transpose");
+        return NG_OK;
+    };
+    int it = 0;
+    bool done = false;
+    for (it = 1; it <= maxiter; ++it) {
+        if ((st = start_vjp())) return st;
+        ADJ_TRY(c, adj_boot_reduce(E, nb, A.Pk, A.cSx, s), "start-slice reduction");
+        if ((st = through_sigma(A.cSx, A.cmfx, false))) return st;
+        CUDA_TRY(c, cudaMemsetAsync(A.dist, 0, 2 * sizeof(double), s));
+        ADJ_TRY(c, adj_boot_update(E, nb, A.ctot, A.cLb, A.mu, A.dist, s), "start-slice update");
+        double d[2];
+        CUDA_TRY(c, cudaMemcpyAsync(d, A.dist, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(c, cudaStreamSynchronize(s));
+        if (!(d[0] == d[0]) || !(d[1] == d[1])) return fail(c, NG_ENONFINITE, "adjoint of the start slices is not finite");
+        if (d[0] <= tol * d[1]) { done = true; break; }
+    }
+    // F_eps^T at the final mu
+    if ((st = start_vjp())) return st;
+    ADJ_TRY(c, adj_ce0_rows(k + 1, nb, A.cmfx, A.ce0, s), "eps0 cotangent (start slices)");
+    if (iters) *iters = it;
+    if (!done) return fail(c, NG_ENOCONV, "adjoint of the start slices did not converge in %d iterations", maxiter);
+    return NG_OK;
+}
+
+}  // namespace
+
+extern "C" ng_status ng_adjoint_2b(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm Gloc, ng_herm S, ng_func eps0,
+                                   ng_func epsmf, ng_func U, const ng_run_params* p, const void* seed, ng_herm cG,
+                                   ng_herm cS, int segment, double* grad_eps0, int* info, void* stream) {
+    Grid g;
+    HermV Gv, Lv, Sv, cGv, cSv;
+    FuncV e0, mf, uv;
+    ng_status st;
+    if ((st = check_grid(c, grid, &g))) return st;
+    if (g.nf != 1) return fail(c, NG_EUNSUPPORTED, "ng_adjoint_2b supports nf = 1 (nf = %d)", g.nf);
+    if (!p || !seed || !grad_eps0) return fail(c, NG_EINVAL, "params, seed and grad_eps0 must not be NULL");
+    if (p->corrector < 1) return fail(c, NG_EINVAL, "corrector must be >= 1");
+    if (G.ldk != g.nb || cG.ldk != g.nb) return fail(c, NG_EINVAL, "G and cG must have ldk = nbatch");
+    if ((st = check_herm(c, g, G, "G", true, &Gv, g.nb))) return st;
+    if ((st = check_herm(c, g, cG, "cG", true, &cGv, g.nb))) return st;
+    if (Gloc.ldk != 1 || S.ldk != 1 || cS.ldk != 1) return fail(c, NG_EINVAL, "Gloc, Sigma and cS must have ldk = 1");
+    if ((st = check_herm(c, g, Gloc, "Gloc", true, &Lv, 1))) return st;
+    if ((st = check_herm(c, g, S, "Sigma", true, &Sv, 1))) return st;
+    if ((st = check_herm(c, g, cS, "cS", true, &cSv, 1))) return st;
+    if ((st = check_func(c, g, eps0, "eps0", &e0))) return st;
+    if ((st = check_func(c, g, epsmf, "eps_mf", &mf))) return st;
+    if ((st = check_func(c, g, U, "U", &uv))) return st;
+    if (U.ldk != 1 || epsmf.ldk != g.nb || eps0.ldk != g.nb)
+        return fail(c, NG_EINVAL, "U.ldk must be 1 and eps0.ldk, eps_mf.ldk must be nbatch");
+    if (!aligned16(seed) || ((uintptr_t)grad_eps0 & 7u)) return fail(c, NG_EINVAL, "seed or grad_eps0 misaligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int k = g.k, nb = g.nb, T = g.ntau, N = g.nt;
+    const int nsteps = N - k;
+    int seg = segment > 0 ? segment : (int)std::ceil(std::sqrt((double)nsteps));
+    seg = std::max(1, std::min(seg, nsteps));
+    AdjLayout A;
+    const size_t need = adj_layout(g, seg, p->corrector, &A, nullptr);
+    if ((st = ensure(c, &c->ws_adj, &c->ws_adj_bytes, need))) return st;
+    adj_layout(g, seg, p->corrector, &A, (char*)c->ws_adj);
+    // cotangent stores start at zero, then the seed on the G^<(n,n) diagonal
+    const size_t per = sizeof(cplx) * (size_t)nb;
+    CUDA_TRY(c, cudaMemsetAsync(cG.ret, 0, per * tri(N + 1), s));
+    CUDA_TRY(c, cudaMemsetAsync(cG.les, 0, per * tri(N + 1), s));
+    CUDA_TRY(c, cudaMemsetAsync(cG.tv, 0, per * (size_t)(N + 1) * (T + 1), s));
+    CUDA_TRY(c, cudaMemsetAsync(cS.ret, 0, sizeof(cplx) * tri(N + 1), s));
+    CUDA_TRY(c, cudaMemsetAsync(cS.les, 0, sizeof(cplx) * tri(N + 1), s));
+    CUDA_TRY(c, cudaMemsetAsync(cS.tv, 0, sizeof(cplx) * (size_t)(N + 1) * (T + 1), s));
+    CUDA_TRY(c, cudaMemsetAsync(A.cmf, 0, per * (N + 2), s));
+    CUDA_TRY(c, cudaMemsetAsync(A.ce0, 0, sizeof(double) * (size_t)(N + 2) * nb, s));
+    ADJ_TRY(c, adj_seed(g, (const cplx*)seed, (cplx*)cG.les, s), "seed");
+    // segments from the last: [s0, s1], recomputed forward with capture, then walked backwards
+    int nseg = 0;
+    for (int s1 = N; s1 > k; s1 -= seg, ++nseg) {
+        const int s0 = std::max(k + 1, s1 - seg + 1);
+        for (int n = s0; n <= s1; ++n)
+            if ((st = adj_forward_step(c, g, n, p->corrector, Gv, Lv, Sv, mf, e0, uv, p->nbar, A, n - s0, s)))
+                return st;
+        for (int n = s1; n >= s0; --n)
+            if ((st = adj_backward_step(c, g, n, Gv, Sv, mf, uv, cGv, cSv, A, n - s0, s))) return st;
+    }
+    int boot_it = 0;
+    if ((st = adj_boot(c, g, Gv, Lv, Sv, mf, uv, cGv, cSv, A, p->boot_tol > 0 ? p->boot_tol : 1e-14,
+                       p->boot_maxiter > 0 ? p->boot_maxiter : 200, &boot_it, s)))
+        return st;
+    CUDA_TRY(c, cudaMemcpyAsync(grad_eps0, A.ce0, sizeof(double) * (size_t)(N + 2) * nb, cudaMemcpyDeviceToDevice, s));
+    if (info) {
+        info[0] = boot_it;
+        info[1] = nseg;
+        info[2] = seg;
+    }
+    return NG_OK;
+}
