@@ -54,6 +54,7 @@ def parse():
                     help="chain: the headline chain_kspace run; uneven: the 64-cluster uneven batch; "
                          "adjoint: gradient of E_kin(t_N) on the 16x16 square lattice")
     ap.add_argument("--fd-slices", type=int, default=20, help="adjoint: time slices checked by central differences")
+    ap.add_argument("--fd4-slices", type=int, default=5, help="adjoint: slices also checked by the fourth-order stencil")
     ap.add_argument("--adj-nt", type=int, default=1000, help="adjoint: nt (development override)")
     ap.add_argument("--nprob", type=int, default=64, help="problems of the uneven batch")
     ap.add_argument("--precision", choices=["f64", "both"], default="both",
@@ -495,6 +496,22 @@ def run_adjoint(a):
     gi = grad[idx] if idx else np.zeros(0)
     err = float(np.abs(gi - fd).max() / np.abs(fd).max()) if idx else None
     per = [float(abs(x - y) / max(abs(y), 1e-300)) for x, y in zip(gi, fd)]
+    # the same derivative resolved below the central difference's rounding floor
+    # (eps |L| / delta ~ 1e-10 here): fourth-order stencil, delta = 1e-3, first slices
+    idx4 = idx[:a.fd4_slices]
+    fd4 = []
+    with torch.no_grad():
+        for i in idx4:
+            vals = []
+            for sgn in (-2.0, -1.0, 1.0, 2.0):
+                Ap = torch.tensor(A0, dtype=torch.float64, device="cuda")
+                Ap[i] += sgn * 1e-3
+                vals.append(loss(Ap).item())
+            fd4.append((vals[0] - 8 * vals[1] + 8 * vals[2] - vals[3]) / (12e-3))
+    fd4 = np.array(fd4)
+    g4 = grad[idx4] if idx4 else np.zeros(0)
+    err4 = float(np.abs(g4 - fd4).max() / np.abs(fd4).max()) if idx4 else None
+    per4 = [float(abs(x - y) / max(abs(y), 1e-300)) for x, y in zip(g4, fd4)]
     units = L * L * (nt - 5)
     line = {"metric": "adjoint gradient k-point timesteps/s", "value": units / t_bwd,
             "unit": "k-point timesteps/s (backward sweep)", "n_gpus": 1, "steps": 1, "warmup": 1,
@@ -508,6 +525,8 @@ def run_adjoint(a):
             "fd_check": {"slices": [int(i) - 1 for i in idx], "delta": delta, "max_rel_err_normwise": err,
                          "max_rel_err_per_slice": max(per) if per else None,
                          "median_rel_err_per_slice": float(np.median(per)) if per else None},
+            "fd4_check": {"slices": [int(i) - 1 for i in idx4], "delta": 1e-3, "stencil": "fourth-order central",
+                          "max_rel_err_normwise": err4, "max_rel_err_per_slice": max(per4) if per4 else None},
             "grad_norm_inf": float(np.abs(grad).max()), "clocks": clk,
             "device_status": dict(zip(("status", "flags"), ctx.status_sync()))}
     print(json.dumps(line), flush=True)
