@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--fd4-slices", type=int, default=5, help="adjoint: slices also checked by the fourth-order stencil")
     ap.add_argument("--adj-nt", type=int, default=1000, help="adjoint: nt (development override)")
     ap.add_argument("--nprob", type=int, default=64, help="problems of the uneven batch")
+    ap.add_argument("--compare-plain", action="store_true",
+                    help="uneven: also solve the same problems one after another with the plain path")
     ap.add_argument("--precision", choices=["f64", "both"], default="both",
                     help="f64: the FP64 headline only; both: also time the FP32-compensated mode")
     return ap.parse_args()
@@ -434,6 +436,23 @@ def run_uneven(a):
                          "frac": achieved / peak, "traffic": None, "kernel": "k_ubulk",
                          "share_of_timed": prof["bulk_ms"] / ms},
             "tuned_threads": threads, "clocks": clk, "device_status": {"status": st, "flags": flags}}
+    if a.compare_plain:
+        # the plain GPU form on the same problems: one problem after another through
+        # ng_solve_fixed (Matsubara, start-up, every time step of that problem alone)
+        for G in Gs:
+            for x in G.tensors().values():
+                x.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for g, G, S, e in zip(grids, Gs, Ss, es):
+            ctx.solve_fixed(g, G, S, e)
+        e1.record()
+        torch.cuda.synchronize()
+        ms_plain = e0.elapsed_time(e1)
+        line["plain_form"] = {"value": units / (ms_plain / 1e3), "unit": "problem timesteps/s", "ms": ms_plain,
+                              "what": "same problems solved one after another with ng_solve_fixed",
+                              "batch_speedup": ms_plain / ms}
     print(json.dumps(line), flush=True)
     batch.close()
 

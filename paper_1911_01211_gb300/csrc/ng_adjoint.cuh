@@ -308,26 +308,35 @@ __global__ void __launch_bounds__(128) k_adj_bulk(AdjStep a) {
 // ======================================================================================
 // 5. History cotangents and the partial sums of the self-energy row / column cotangents.
 // ======================================================================================
+// The history kernels below run one block per history row (or column); each warp takes one
+// index of the other time argument at a time and its lanes take the problems kb = lane,
+// lane + 32, ..., so the weights and self-energy values of that index are warp-uniform and the
+// per-problem arrays are read in contiguous 512-byte runs.
+
 // tv history row j < n: tv step (all tau), BDF, and the C^<_3 source of the lesser (B) row j.
 __global__ void __launch_bounds__(256) k_adj_tvrow(AdjStep a) {
     const NgWeights& W = c_W[a.g.k - 1];
     const int k = W.k, n = a.n, nb = a.g.nb, T = a.g.ntau, j = blockIdx.x;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const double h = a.g.h, ht = a.g.htau, xi = (double)a.g.sig;
     __shared__ cplx red[32];
     const cplx coefA = cadd(cmuli(cscal(h * gw(W, n, j), cconj(a.Sc.ret[j]))),
                             cr(j >= n - k ? -W.a[n - j] / h : 0.0));
     const bool useB = !a.full && j >= 1 && j <= n - k - 1;
-    const int64_t cnt = (int64_t)(T + 1) * nb;
+    const cplx* crj = a.crhs + (int64_t)j * nb;
     cplx acc = cz();
-    for (int64_t e = threadIdx.x; e < cnt; e += blockDim.x) {
-        const int m = (int)(e / nb), kb = (int)(e % nb);
-        const cplx cT = a.caccT[e];
-        const int64_t hidx = ((int64_t)j * (T + 1) + m) * nb + kb;
-        cplx v = cmul(coefA, cT);
-        if (useB)   // w_{T,m} Sigma^tv(n, T-m) (-xi htau) crhs_j
-            v = cfma(cscal(-xi * ht * gw(W, T, m), a.Sc.tv[T - m]), a.crhs[(int64_t)j * nb + kb], v);
-        a.cGt[hidx] = cadd(a.cGt[hidx], v);
-        acc = cfma(cconj(a.Gt[hidx]), cT, acc);
+    for (int m = wp; m <= T; m += nw) {
+        // w_{T,m} Sigma^tv(n, T-m) (-xi htau), multiplying crhs_j
+        const cplx sB = useB ? cscal(-xi * ht * gw(W, T, m), a.Sc.tv[T - m]) : cz();
+        const int64_t base = ((int64_t)j * (T + 1) + m) * nb;
+        const cplx* cTm = a.caccT + (int64_t)m * nb;
+        for (int kb = lane; kb < nb; kb += 32) {
+            const cplx cT = cTm[kb];
+            cplx v = cfma(coefA, cT, a.cGt[base + kb]);
+            if (useB) v = cfma(sB, crj[kb], v);
+            a.cGt[base + kb] = v;
+            acc = cfma(cconj(a.Gt[base + kb]), cT, acc);
+        }
     }
     acc = block_csum(acc, red);
     if (threadIdx.x == 0) a.part[P_TVROW * a.plen + j] = cmuli(cscal(h * gw(W, n, j), acc));
@@ -337,14 +346,14 @@ __global__ void __launch_bounds__(256) k_adj_tvrow(AdjStep a) {
 __global__ void __launch_bounds__(256) k_adj_tvcol(AdjStep a) {
     const NgWeights& W = c_W[a.g.k - 1];
     const int k = W.k, n = a.n, nb = a.g.nb, T = a.g.ntau, m = blockIdx.x;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const double ht = a.g.htau, xi = (double)a.g.sig;
     __shared__ cplx red[32];
-    const int nrow = n - k - 1;   // rows 1..n-k-1
-    const int64_t cnt = (int64_t)nrow * nb;
     cplx acc = cz();
-    for (int64_t e = threadIdx.x; e < cnt; e += blockDim.x) {
-        const int j = 1 + (int)(e / nb), kb = (int)(e % nb);
-        acc = cfma(a.Gt[((int64_t)j * (T + 1) + m) * nb + kb], cconj(a.crhs[(int64_t)j * nb + kb]), acc);
+    for (int j = 1 + wp; j <= n - k - 1; j += nw) {
+        const int64_t base = ((int64_t)j * (T + 1) + m) * nb;
+        const cplx* crj = a.crhs + (int64_t)j * nb;
+        for (int kb = lane; kb < nb; kb += 32) acc = cfma(a.Gt[base + kb], cconj(crj[kb]), acc);
     }
     acc = block_csum(acc, red);
     if (threadIdx.x == 0) a.part[P_TVCOL * a.plen + (T - m)] = cscal(-xi * ht * gw(W, T, m), acc);
@@ -356,33 +365,39 @@ __global__ void __launch_bounds__(256) k_adj_tvcol(AdjStep a) {
 __global__ void __launch_bounds__(256) k_adj_rrow(AdjStep a) {
     const NgWeights& W = c_W[a.g.k - 1];
     const int k = W.k, n = a.n, nb = a.g.nb, j = blockIdx.x;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const double h = a.g.h;
     __shared__ cplx red[32];
     const cplx sRc = cconj(a.Sc.ret[j]);
     const double bdf = (j >= n - k) ? -W.a[n - j] / h : 0.0;
     const bool rowB = !a.full && j >= 1 && j <= n - k - 1;
-    const int64_t cnt = (int64_t)(j + 1) * nb;
+    const cplx* crj = a.crhs + (int64_t)j * nb;
     cplx acc = cz();
-    for (int64_t e = threadIdx.x; e < cnt; e += blockDim.x) {
-        const int m = (int)(e / nb), kb = (int)(e % nb);
-        const int64_t hidx = (tri(j) + m) * nb + kb;
-        cplx v = cz();
-        if (m <= n - k - 1) {
-            const cplx cR = a.caccR[(int64_t)m * nb + kb];
-            const double w = gw(W, n - m, j - m);
-            v = cadd(cmuli(cscal(h * w, cmul(sRc, cR))), cscal(bdf, cR));
-            acc = cfma(cscal(w, cconj(a.Gr[hidx])), cR, acc);
+    for (int m = wp; m <= j; m += nw) {
+        const int64_t base = (tri(j) + m) * nb;
+        const bool colB = (m <= n - k - 1);
+        const double w = colB ? gw(W, n - m, j - m) : 0.0;
+        const cplx cR0 = cadd(cmuli(cscal(h * w, sRc)), cr(bdf));   // multiplies caccR_m
+        // c1 of row j: w_{j,m} conj(Sigma^<(m,n)) (-i h) crhs_j
+        const cplx c1 = rowB ? cmulmi(cscal(h * ((j > k) ? gw(W, j, m) : W.greg[j][m]), cconj(a.Sc.les[m]))) : cz();
+        // row m < j <= k continued: -i h greg[m][j] Sigma^<(j,n) conj(crhs_m)
+        const bool cont = !a.full && j <= k && m >= 1 && m < j && m <= n - k - 1;
+        const cplx c2 = cont ? cmulmi(cscal(h * W.greg[m][j], a.Sc.les[j])) : cz();
+        const cplx* cRm = a.caccR + (int64_t)m * nb;
+        const cplx* crm = a.crhs + (int64_t)m * nb;
+        cplx t = cz();   // sum over the problems of conj(G^R(j,m)) caccR_m, weighted once below
+        for (int kb = lane; kb < nb; kb += 32) {
+            cplx v = a.cGr[base + kb];
+            if (colB) {
+                const cplx cR = cRm[kb];
+                v = cfma(cR0, cR, v);
+                t = cfma(cconj(a.Gr[base + kb]), cR, t);
+            }
+            if (rowB) v = cfma(c1, crj[kb], v);
+            if (cont) v = cfma(c2, cconj(crm[kb]), v);
+            a.cGr[base + kb] = v;
         }
-        if (rowB) {   // c1 of row j: w_{j,m} conj(Sigma^<(m,n)) cc1_j, cc1 = -i h crhs
-            const double w = (j > k) ? gw(W, j, m) : W.greg[j][m];
-            const cplx cc1 = cmulmi(cscal(h, a.crhs[(int64_t)j * nb + kb]));
-            v = cfma(cscal(w, cconj(a.Sc.les[m])), cc1, v);
-        }
-        if (!a.full && j <= k && m >= 1 && m < j && m <= n - k - 1) {   // row m, continued index j
-            const cplx cc1 = cmulmi(cscal(h, a.crhs[(int64_t)m * nb + kb]));
-            v = csub(v, cmul(cscal(W.greg[m][j], a.Sc.les[j]), cconj(cc1)));
-        }
-        a.cGr[hidx] = cadd(a.cGr[hidx], v);
+        acc = cadd(acc, cscal(w, t));
     }
     acc = block_csum(acc, red);
     if (threadIdx.x == 0) a.part[P_RROW * a.plen + j] = cmuli(cscal(h, acc));
@@ -392,27 +407,28 @@ __global__ void __launch_bounds__(256) k_adj_rrow(AdjStep a) {
 __global__ void __launch_bounds__(256) k_adj_rcol(AdjStep a) {
     const NgWeights& W = c_W[a.g.k - 1];
     const int k = W.k, n = a.n, nb = a.g.nb, b = blockIdx.x;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const double h = a.g.h;
     __shared__ cplx red[32];
-    const int a0 = max(1, b), a1 = n - k - 1;
-    const int nlow = (b <= k) ? max(0, b - 1) : 0;     // rows 1..b-1 through the continuation
-    const int64_t cnt = (int64_t)(max(0, a1 - a0 + 1) + nlow) * nb;
     cplx acc = cz();
-    for (int64_t e = threadIdx.x; e < cnt; e += blockDim.x) {
-        const int r = (int)(e / nb), kb = (int)(e % nb);
-        if (r < nlow) {
-            const int ar = 1 + r;   // ar < b <= k: R~(ar,b) = -conj(G^R(b,ar))
-            const cplx cc1 = cmulmi(cscal(h, a.crhs[(int64_t)ar * nb + kb]));
-            acc = csub(acc, cmul(cscal(W.greg[ar][b], a.Gr[(tri(b) + ar) * nb + kb]), cc1));
-        } else {
-            const int ar = a0 + (r - nlow);
-            const double w = (ar > k) ? gw(W, ar, b) : W.greg[ar][b];
-            const cplx cc1 = cmulmi(cscal(h, a.crhs[(int64_t)ar * nb + kb]));
-            acc = cfma(cscal(w, cconj(a.Gr[(tri(ar) + b) * nb + kb])), cc1, acc);
-        }
+    // rows ar >= max(1, b): R~(ar,b) = G^R(ar,b); rows 1 <= ar < b <= k: R~(ar,b) = -conj(G^R(b,ar))
+    for (int ar = 1 + wp; ar <= n - k - 1; ar += nw) {
+        const bool dir = ar >= b;
+        if (!dir && b > k) continue;
+        const double w = (dir && ar > k) ? gw(W, ar, b) : W.greg[ar][b];
+        const int64_t base = (dir ? tri(ar) + b : tri(b) + ar) * nb;
+        const cplx* cra = a.crhs + (int64_t)ar * nb;
+        // cc1 = -i h crhs:  dir: w conj(G^R(ar,b)) cc1;  continued: -w G^R(b,ar) cc1
+        // (-i h applied once after the block sum, w once per row)
+        cplx t = cz();
+        if (dir)
+            for (int kb = lane; kb < nb; kb += 32) t = cfma(cconj(a.Gr[base + kb]), cra[kb], t);
+        else
+            for (int kb = lane; kb < nb; kb += 32) t = cfma(a.Gr[base + kb], cra[kb], t);
+        acc = cadd(acc, cscal(dir ? w : -w, t));
     }
     acc = block_csum(acc, red);
-    if (threadIdx.x == 0) a.part[P_RCOL * a.plen + b] = acc;
+    if (threadIdx.x == 0) a.part[P_RCOL * a.plen + b] = cmulmi(cscal(h, acc));
 }
 
 // les history column b < n: history term and BDF of the lesser (B) rows; partial of
@@ -420,26 +436,33 @@ __global__ void __launch_bounds__(256) k_adj_rcol(AdjStep a) {
 __global__ void __launch_bounds__(256) k_adj_lcol(AdjStep a) {
     const NgWeights& W = c_W[a.g.k - 1];
     const int k = W.k, n = a.n, nb = a.g.nb, b = blockIdx.x;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const double h = a.g.h;
     __shared__ cplx red[32];
-    const cplx sRb = a.Sc.ret[b];
     const double wb = gw(W, n, b);
     const double bdf = (b >= n - k) ? -W.a[n - b] / h : 0.0;
     const bool colB = b >= 1 && b <= n - k - 1;
-    const int64_t cnt = (int64_t)(b + 1) * nb;
+    // -i h w_{n,b} Sigma^R(n,b) + bdf, multiplying crhs_ar
+    const cplx c0 = cadd(cmulmi(cscal(h * wb, a.Sc.ret[b])), cr(bdf));
+    const cplx* crb = a.crhs + (int64_t)b * nb;
     cplx acc = cz();
-    for (int64_t e = threadIdx.x; e < cnt; e += blockDim.x) {
-        const int ar = (int)(e / nb), kb = (int)(e % nb);
-        const int64_t hidx = (tri(b) + ar) * nb + kb;
-        cplx v = cz();
-        if (ar >= 1 && ar <= n - k - 1) {
-            const cplx cr_ = a.crhs[(int64_t)ar * nb + kb];
-            v = cadd(cmulmi(cscal(h * wb, cmul(sRb, cr_))), cscal(bdf, cr_));
-            acc = cfma(a.Gl[hidx], cconj(cr_), acc);
+    for (int ar = wp; ar <= b; ar += nw) {
+        const int64_t base = (tri(b) + ar) * nb;
+        const bool rowB = ar >= 1 && ar <= n - k - 1;
+        const bool cnj = ar < b && colB;
+        // row m = b, index l = ar < b:  -i h w_{n,ar} conj(Sigma^R(n,ar)) conj(crhs_b)
+        const cplx c1 = cnj ? cmulmi(cscal(h * gw(W, n, ar), cconj(a.Sc.ret[ar]))) : cz();
+        const cplx* cra = a.crhs + (int64_t)ar * nb;
+        for (int kb = lane; kb < nb; kb += 32) {
+            cplx v = a.cGl[base + kb];
+            if (rowB) {
+                const cplx cr_ = cra[kb];
+                v = cfma(c0, cr_, v);
+                acc = cfma(a.Gl[base + kb], cconj(cr_), acc);
+            }
+            if (cnj) v = cfma(c1, cconj(crb[kb]), v);
+            a.cGl[base + kb] = v;
         }
-        if (ar < b && colB)   // row m = b, index l = ar < b:  -i h w_{n,a} conj(Sigma^R(n,a)) conj(crhs_b)
-            v = csub(v, cmuli(cscal(h * gw(W, n, ar), cmul(cconj(a.Sc.ret[ar]), cconj(a.crhs[(int64_t)b * nb + kb])))));
-        a.cGl[hidx] = cadd(a.cGl[hidx], v);
     }
     acc = block_csum(acc, red);
     if (threadIdx.x == 0) a.part[P_LCOL * a.plen + b] = cmuli(cscal(h * wb, acc));
@@ -449,15 +472,15 @@ __global__ void __launch_bounds__(256) k_adj_lcol(AdjStep a) {
 __global__ void __launch_bounds__(256) k_adj_lrow(AdjStep a) {
     const NgWeights& W = c_W[a.g.k - 1];
     const int k = W.k, n = a.n, nb = a.g.nb, ar = blockIdx.x;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const double h = a.g.h;
     __shared__ cplx red[32];
-    const int m0 = max(ar + 1, 1), m1 = n - k - 1;
-    const int64_t cnt = (int64_t)max(0, m1 - m0 + 1) * nb;
     cplx acc = cz();
-    for (int64_t e = threadIdx.x; e < cnt; e += blockDim.x) {
-        const int m = m0 + (int)(e / nb), kb = (int)(e % nb);
+    for (int m = max(ar + 1, 1) + wp; m <= n - k - 1; m += nw) {
+        const int64_t base = (tri(m) + ar) * nb;
+        const cplx* crm = a.crhs + (int64_t)m * nb;
         // G^<(m, a) = -conj(G^<(a, m))
-        acc = csub(acc, cmul(cconj(a.Gl[(tri(m) + ar) * nb + kb]), cconj(a.crhs[(int64_t)m * nb + kb])));
+        for (int kb = lane; kb < nb; kb += 32) acc = csub(acc, cconj(cmul(a.Gl[base + kb], crm[kb])));
     }
     acc = block_csum(acc, red);
     if (threadIdx.x == 0) a.part[P_LROW * a.plen + ar] = cmuli(cscal(h * gw(W, n, ar), acc));
@@ -468,34 +491,31 @@ __global__ void __launch_bounds__(256) k_adj_lrow(AdjStep a) {
 __global__ void __launch_bounds__(256) k_adj_qtv(AdjStep a) {
     const NgWeights& W = c_W[a.g.k - 1];
     const int k = W.k, nb = a.g.nb, T = a.g.ntau, p = blockIdx.x;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const double ht = a.g.htau, xi = (double)a.g.sig;
     __shared__ cplx red[32];
-    const int64_t cnt = (int64_t)(T + 1) * nb;
     cplx acc = cz();
-    for (int64_t e = threadIdx.x; e < cnt; e += blockDim.x) {
-        const int m = (int)(e / nb), kb = (int)(e % nb);
-        const cplx cC = cmuli(cscal(ht, a.caccT[e]));
-        cplx w = cz();   // sum of weight * conj(G^M) multiplying cC
+    for (int m = wp; m <= T; m += nw) {
         // C2 (with xi): m <= k: R[m][j][p] xi G^M(T-j), p <= k;  m > k: w_{m,m-p} xi G^M(T-m+p), p <= m
-        if (m <= k) {
-            if (p <= k)
-                for (int j = 0; j <= k; ++j)
-                    w = cadd(w, cscal(W.R[m][j][p] * xi, cconj(a.Gm[(int64_t)(T - j) * nb + kb])));
-        } else if (p <= m) {
-            w = cadd(w, cscal(gw(W, m, m - p) * xi, cconj(a.Gm[(int64_t)(T - m + p) * nb + kb])));
-        }
         // C3: m >= T-k: R[T-m][j][T-p] G^M(j), p >= T-k;  m < T-k: w_{T-m,p-m} G^M(p-m), p >= m
-        if (m >= T - k) {
-            if (p >= T - k)
-                for (int j = 0; j <= k; ++j)
-                    w = cadd(w, cscal(W.R[T - m][j][T - p], cconj(a.Gm[(int64_t)j * nb + kb])));
-        } else if (p >= m) {
-            w = cadd(w, cscal(gw(W, T - m, p - m), cconj(a.Gm[(int64_t)(p - m) * nb + kb])));
+        const bool c2R = (m <= k) && (p <= k), c2G = (m > k) && (p <= m);
+        const bool c3R = (m >= T - k) && (p >= T - k), c3G = (m < T - k) && (p >= m);
+        if (!(c2R || c2G || c3R || c3G)) continue;
+        const double w2 = c2G ? gw(W, m, m - p) * xi : 0.0, w3 = c3G ? gw(W, T - m, p - m) : 0.0;
+        const cplx* cTm = a.caccT + (int64_t)m * nb;
+        for (int kb = lane; kb < nb; kb += 32) {
+            cplx w = cz();
+            if (c2R)
+                for (int j = 0; j <= k; ++j) w = cadd(w, cscal(W.R[m][j][p] * xi, cconj(a.Gm[(int64_t)(T - j) * nb + kb])));
+            if (c2G) w = cadd(w, cscal(w2, cconj(a.Gm[(int64_t)(T - m + p) * nb + kb])));
+            if (c3R)
+                for (int j = 0; j <= k; ++j) w = cadd(w, cscal(W.R[T - m][j][T - p], cconj(a.Gm[(int64_t)j * nb + kb])));
+            if (c3G) w = cadd(w, cscal(w3, cconj(a.Gm[(int64_t)(p - m) * nb + kb])));
+            acc = cfma(w, cTm[kb], acc);
         }
-        acc = cfma(w, cC, acc);
     }
     acc = block_csum(acc, red);
-    if (threadIdx.x == 0) a.part[P_QTV * a.plen + p] = acc;
+    if (threadIdx.x == 0) a.part[P_QTV * a.plen + p] = cmuli(cscal(ht, acc));
 }
 
 // Current self-energy slice: add the partial sums, the M_n term and the retarded (A) block.

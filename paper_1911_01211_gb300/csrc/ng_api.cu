@@ -373,14 +373,14 @@ ng_status launch_timestep32(ng_ctx* c, const Grid& g, int n, const HermV& G, con
 // refinement (update sum below ref_tol); otherwise the caller falls back to a fresh LU.
 template <int D>
 ng_status launch_mat(ng_ctx* c, const Grid& g, const HermV& G, const HermV& S, const FuncV& eps, cudaStream_t s,
-                     int refine_steps = 0, double ref_tol = 0.0, bool* refined_ok = nullptr) {
+                     int refine_steps = 0, double ref_tol = 0.0, bool* refined_ok = nullptr, void* ws_ext = nullptr) {
     const int T = g.ntau, N = (T + 1) * D, ld = N + D;
     const size_t b_g = sizeof(cplx) * (size_t)g.nb * (T + 1) * D * D;
     const size_t b_A = sizeof(cplx) * (size_t)g.nb * N * ld;
     const size_t b_piv = sizeof(int) * (size_t)g.nb * N + 256;
-    ng_status st = ensure(c, &c->ws_mat, &c->ws_mat_bytes, 3 * b_g + b_A + b_piv);
-    if (st) return st;
-    cplx* ws_g = (cplx*)c->ws_mat;
+    ng_status st = NG_OK;
+    if (!ws_ext && (st = ensure(c, &c->ws_mat, &c->ws_mat_bytes, 3 * b_g + b_A + b_piv))) return st;
+    cplx* ws_g = (cplx*)(ws_ext ? ws_ext : c->ws_mat);
     cplx* ws_K = ws_g + b_g / sizeof(cplx);
     cplx* ws_r = ws_K + b_g / sizeof(cplx);
     cplx* ws_A = ws_r + b_g / sizeof(cplx);
@@ -423,12 +423,13 @@ ng_status launch_mat(ng_ctx* c, const Grid& g, const HermV& G, const HermV& S, c
 }
 
 template <int D>
-ng_status launch_start(ng_ctx* c, const Grid& g, const HermV& G, const HermV& S, const FuncV& eps, cudaStream_t s) {
+ng_status launch_start(ng_ctx* c, const Grid& g, const HermV& G, const HermV& S, const FuncV& eps, cudaStream_t s,
+                       void* ws_ext = nullptr) {
     const int k = g.k, N = k * D;
     const size_t need = sizeof(cplx) * (size_t)g.nb * (N * N + k * D * D);
-    ng_status st = ensure(c, &c->ws_st, &c->ws_st_bytes, need);
-    if (st) return st;
-    cplx* ws = (cplx*)c->ws_st;
+    ng_status st = NG_OK;
+    if (!ws_ext && (st = ensure(c, &c->ws_st, &c->ws_st_bytes, need))) return st;
+    cplx* ws = (cplx*)(ws_ext ? ws_ext : c->ws_st);
     k_start_ret<D><<<nblocks(g.nb, 64), 64, 0, s>>>(g, G, S, eps, ws, c->d_status);
     if ((st = check_launch(c, "k_start_ret"))) return st;
     k_start_tv<D><<<nblocks((int64_t)(g.ntau + 1) * g.nb, 128), 128, 0, s>>>(g, G, S, ws, c->d_status);
@@ -518,11 +519,14 @@ ng_status ustep(ng_ctx* c, const UProb* d_probs, const std::vector<UHost>& info,
 // uniform-batch time step with nf = 4, 8: every interleaved problem kb as one UProb
 ng_status utimestep_uniform(ng_ctx* c, const Grid& g, int n, const HermV& G, const HermV& S, const FuncV& eps,
                             cudaStream_t s) {
-    const size_t need = sizeof(UProb) * (size_t)g.nb + sizeof(cplx) * 64 * (size_t)g.nb;
+    // the M_n^-1 blocks start on a 256-byte boundary after the table (sizeof(UProb) is a
+    // multiple of 8 only, and the blocks are read as 16-byte complex numbers)
+    const size_t off_minv = (sizeof(UProb) * (size_t)g.nb + 255) / 256 * 256;
+    const size_t need = off_minv + sizeof(cplx) * 64 * (size_t)g.nb;
     ng_status st = ensure(c, &c->ws_uni, &c->ws_uni_bytes, need);
     if (st) return st;
     UProb* d_probs = (UProb*)c->ws_uni;
-    cplx* d_minv = (cplx*)((char*)c->ws_uni + sizeof(UProb) * (size_t)g.nb);
+    cplx* d_minv = (cplx*)((char*)c->ws_uni + off_minv);
     if (c->uni_key_nb != g.nb || c->uni_key_G != G.ret.p || c->uni_key_S != S.ret.p || c->uni_key_eps != eps.p) {
         std::vector<UProb> h(g.nb);
         for (int kb = 0; kb < g.nb; ++kb) {
@@ -559,13 +563,23 @@ ng_status do_timestep(ng_ctx* c, const Grid& g, int n, const HermV& G, const Her
         return g.nf == 1 ? launch_timestep32<1>(c, g, n, G, S, eps, s) : launch_timestep32<2>(c, g, n, G, S, eps, s);
     return g.nf == 1 ? launch_timestep<1>(c, g, n, G, S, eps, s) : launch_timestep<2>(c, g, n, G, S, eps, s);
 }
-ng_status do_mat(ng_ctx* c, const Grid& g, const HermV& G, const HermV& S, const FuncV& eps, cudaStream_t s) {
+ng_status do_mat(ng_ctx* c, const Grid& g, const HermV& G, const HermV& S, const FuncV& eps, cudaStream_t s,
+                 void* ws = nullptr) {
     switch (g.nf) {
-        case 1: return launch_mat<1>(c, g, G, S, eps, s);
-        case 2: return launch_mat<2>(c, g, G, S, eps, s);
-        case 4: return launch_mat<4>(c, g, G, S, eps, s);
-        default: return launch_mat<8>(c, g, G, S, eps, s);
+        case 1: return launch_mat<1>(c, g, G, S, eps, s, 0, 0.0, nullptr, ws);
+        case 2: return launch_mat<2>(c, g, G, S, eps, s, 0, 0.0, nullptr, ws);
+        case 4: return launch_mat<4>(c, g, G, S, eps, s, 0, 0.0, nullptr, ws);
+        default: return launch_mat<8>(c, g, G, S, eps, s, 0, 0.0, nullptr, ws);
     }
+}
+// workspace bytes of one Matsubara solve and of one start-up (nb problems of grid g)
+size_t mat_ws_bytes(const Grid& g) {
+    const size_t D = g.nf, T = g.ntau, N = (T + 1) * D, ld = N + D;
+    return 3 * sizeof(cplx) * g.nb * (T + 1) * D * D + sizeof(cplx) * g.nb * N * ld + sizeof(int) * g.nb * N + 256;
+}
+size_t start_ws_bytes(const Grid& g) {
+    const size_t D = g.nf, N = (size_t)g.k * D;
+    return sizeof(cplx) * g.nb * (N * N + g.k * D * D);
 }
 ng_status do_mat_refine(ng_ctx* c, const Grid& g, const HermV& G, const HermV& S, const FuncV& eps, cudaStream_t s,
                         int steps, double tol, bool* ok) {
@@ -576,12 +590,13 @@ ng_status do_mat_refine(ng_ctx* c, const Grid& g, const HermV& G, const HermV& S
         default: return launch_mat<8>(c, g, G, S, eps, s, steps, tol, ok);
     }
 }
-ng_status do_start(ng_ctx* c, const Grid& g, const HermV& G, const HermV& S, const FuncV& eps, cudaStream_t s) {
+ng_status do_start(ng_ctx* c, const Grid& g, const HermV& G, const HermV& S, const FuncV& eps, cudaStream_t s,
+                   void* ws = nullptr) {
     switch (g.nf) {
-        case 1: return launch_start<1>(c, g, G, S, eps, s);
-        case 2: return launch_start<2>(c, g, G, S, eps, s);
-        case 4: return launch_start<4>(c, g, G, S, eps, s);
-        default: return launch_start<8>(c, g, G, S, eps, s);
+        case 1: return launch_start<1>(c, g, G, S, eps, s, ws);
+        case 2: return launch_start<2>(c, g, G, S, eps, s, ws);
+        case 4: return launch_start<4>(c, g, G, S, eps, s, ws);
+        default: return launch_start<8>(c, g, G, S, eps, s, ws);
     }
 }
 ng_status do_extrap(ng_ctx* c, const Grid& g, int n, const HermV& G, cudaStream_t s) {
@@ -1092,7 +1107,13 @@ struct ng_batch {
     cplx* d_minv = nullptr;
     int threads = 0;      // block size of the bulk kernel chosen by the autotune (0: not tuned)
     double tune_ms[3] = {0, 0, 0};
+    // concurrent per-problem setup: streams, join events and one workspace per stream
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> events;
+    void* ws_setup = nullptr;
+    size_t ws_setup_bytes = 0;
 };
+#define NG_SETUP_STREAMS 16
 
 namespace {
 __global__ void k_sandwich(Grid go, HermV O, Grid gi, HermV I, const cplx* V) {
@@ -1197,6 +1218,9 @@ void ng_batch_destroy(ng_batch* b) {
     cudaDeviceSynchronize();
     cudaFree(b->d_probs);
     cudaFree(b->d_minv);
+    cudaFree(b->ws_setup);
+    for (cudaStream_t x : b->streams) cudaStreamDestroy(x);
+    for (cudaEvent_t e : b->events) cudaEventDestroy(e);
     delete b;
 }
 
@@ -1204,9 +1228,42 @@ ng_status ng_batch_setup(ng_ctx* c, ng_batch* b, void* stream) {
     if (!c || !b) return NG_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     ng_status st;
+    // The per-problem setups are independent and each Matsubara LU runs in one block, so they
+    // run concurrently on up to NG_SETUP_STREAMS streams with a workspace each, the costliest
+    // (nf^3 (ntau+1)^3) first, and are joined back into the caller's stream.
+    const int ns = std::min(b->np, NG_SETUP_STREAMS);
+    std::vector<int> order(b->np);
+    for (int p = 0; p < b->np; ++p) order[p] = p;
+    auto cost = [&](int p) {
+        const double d = b->grids[p].nf, t = b->grids[p].ntau + 1;
+        return d * d * d * t * t * t;
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost(x) > cost(y); });
+    size_t wmat = 0, wst = 0;
     for (int p = 0; p < b->np; ++p) {
-        if ((st = do_mat(c, b->grids[p], b->G[p], b->S[p], b->eps[p], s))) return st;
-        if ((st = do_start(c, b->grids[p], b->G[p], b->S[p], b->eps[p], s))) return st;
+        wmat = std::max(wmat, (mat_ws_bytes(b->grids[p]) + 255) / 256 * 256);
+        wst = std::max(wst, (start_ws_bytes(b->grids[p]) + 255) / 256 * 256);
+    }
+    if ((st = ensure(c, &b->ws_setup, &b->ws_setup_bytes, (size_t)ns * (wmat + wst)))) return st;
+    for (int i = (int)b->streams.size(); i < ns; ++i) {
+        cudaStream_t x;
+        cudaEvent_t e;
+        CUDA_TRY(c, cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+        CUDA_TRY(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        b->streams.push_back(x);
+        b->events.push_back(e);
+    }
+    CUDA_TRY(c, cudaEventRecord(b->events[0], s));
+    for (int i = 0; i < ns; ++i) CUDA_TRY(c, cudaStreamWaitEvent(b->streams[i], b->events[0], 0));
+    for (int q = 0; q < b->np; ++q) {
+        const int p = order[q], i = q % ns;
+        char* ws = (char*)b->ws_setup + (size_t)i * (wmat + wst);
+        if ((st = do_mat(c, b->grids[p], b->G[p], b->S[p], b->eps[p], b->streams[i], ws))) return st;
+        if ((st = do_start(c, b->grids[p], b->G[p], b->S[p], b->eps[p], b->streams[i], ws + wmat))) return st;
+    }
+    for (int i = 0; i < ns; ++i) {
+        CUDA_TRY(c, cudaEventRecord(b->events[i], b->streams[i]));
+        CUDA_TRY(c, cudaStreamWaitEvent(s, b->events[i], 0));
     }
     return NG_OK;
 }

@@ -75,12 +75,13 @@ def test_uneven_batch_against_oracle(ng):
     batch.close()
 
 
-def test_uniform_nf4_timestep_against_oracle(ng):
-    """The uniform-batch ng_dyson_timestep with nf = 4 (element-wise kernels), two problems
-    stored interleaved, one step from the oracle's history."""
+@pytest.mark.parametrize("nb", [1, 2, 3])
+def test_uniform_nf4_timestep_against_oracle(ng, nb):
+    """The uniform-batch ng_dyson_timestep with nf = 4 (element-wise kernels), nb problems
+    stored interleaved (odd nb included), one step from the oracle's history."""
     from tests.test_gpu_parity import _oracle_problem_set
     from oracle import dyson
-    k, N, T, beta, h, nb, d = 5, 20, 14, 2.5, 0.06, 2, 4
+    k, N, T, beta, h, d = 5, 20, 14, 2.5, 0.06, 4
     W, Gs, Ss, epss = _oracle_problem_set(d, nb, N, T, beta, h, k, seed=31)
     g = ng.Grid(nt=N, ntau=T, nf=d, nbatch=nb, korder=k, h=h, beta=beta)
     ctx = ng.Context(k)
@@ -99,3 +100,27 @@ def test_uniform_nf4_timestep_against_oracle(ng):
                          (got.tv[n], ref.tv[n])):
                 assert np.abs(x - y).max() / np.abs(y).max() < TOL, (n, kb)
     assert ctx.status_sync() == (ng.NG_OK, 0)
+
+
+def test_plain_solve_of_one_cluster_matches_the_batch(ng):
+    """ng_solve_fixed on single nf = 4 and nf = 8 clusters (nbatch = 1, the plain path the batch
+    is compared with) gives the batch's result."""
+    probs = wl.uneven_clusters(nprob=2, seed=11, nt_range=(16, 24), ntau=14, h=0.05, beta_range=(2.0, 4.0))
+    for p, d in zip(probs, (4, 8)):
+        rng = np.random.default_rng(d)
+        p["nf"] = d
+        p["hs"] = wl.random_hermitian(rng, d)
+        p["V"] = rng.normal(0.0, 0.3, (d, 4))
+    ctx = ng.Context(5)
+    dev = [_device_cluster(ng, ctx, p) for p in probs]
+    batch = ctx.batch([x[0] for x in dev], [x[1] for x in dev], [x[2] for x in dev], [x[3] for x in dev])
+    batch.solve()
+    torch.cuda.synchronize()
+    for p, (g, G, S, eps) in zip(probs, dev):
+        G2 = ng.Herm(g)
+        ctx.solve_fixed(g, G2, S, eps)
+        torch.cuda.synchronize()
+        e = relerr(herm_to_oracle(G2, g, 0), herm_to_oracle(G, g, 0))
+        assert max(e.values()) < 1e-12, (p["nf"], e)
+    assert ctx.status_sync() == (ng.NG_OK, 0)
+    batch.close()
