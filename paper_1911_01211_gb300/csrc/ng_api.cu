@@ -68,6 +68,8 @@ struct ng_ctx {
     size_t ws_uni_bytes = 0;
     int uni_key_nb = -1;
     const void *uni_key_G = nullptr, *uni_key_S = nullptr, *uni_key_eps = nullptr;
+    void* ws_usrc = nullptr;         // element-wise step: chunk partials of the (A) sources
+    size_t ws_usrc_bytes = 0;
     void* ws_adj = nullptr;          // adjoint: iterate store, work vectors, start-slice buffers
     size_t ws_adj_bytes = 0;
 };
@@ -471,6 +473,10 @@ struct UHost {
 ng_status ustep(ng_ctx* c, const UProb* d_probs, const std::vector<UHost>& info, const std::vector<int>& active, int n,
                 int threads, cudaStream_t s) {
     ng_status st;
+    // the boundary kernels use more than the default 48 KB of dynamic shared memory (set on
+    // every call: the attribute is per device, and ustep serves the batch and the nf = 4, 8 step)
+    CUDA_TRY(c, cudaFuncSetAttribute(k_uboundary_ret, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)NG_UBND_SMEM));
+    CUDA_TRY(c, cudaFuncSetAttribute(k_uboundary_les, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)NG_UBND_SMEM));
     for (size_t c0 = 0; c0 < active.size(); c0 += NG_UMAXP) {
         UTable tab;
         memset(&tab, 0, sizeof(tab));
@@ -490,6 +496,17 @@ ng_status ustep(ng_ctx* c, const UProb* d_probs, const std::vector<UHost>& info,
         }
         tab.np = (int)(c1 - c0);
         tab.start[tab.np] = blk;
+        // chunks of the (A) rows' source sums: max(n, k) + 1 + ntau + 1 summation indices
+        int nsum = 0;
+        for (size_t i = c0; i < c1; ++i) nsum = std::max(nsum, std::max(n, info[active[i]].k) + 2 + info[active[i]].ntau);
+        tab.chunk = 128;
+        tab.nchunk = (nsum + tab.chunk - 1) / tab.chunk;
+        {   // capacity for twice the current need, so the buffer grows a logarithmic number of times
+            const size_t per = sizeof(cplx) * (size_t)NG_MAXQ * 2 * NG_UMAXD * NG_UMAXD;
+            const size_t need = per * (size_t)tab.np * tab.nchunk;
+            if (need > c->ws_usrc_bytes && (st = ensure(c, &c->ws_usrc, &c->ws_usrc_bytes, 2 * need))) return st;
+            tab.src = (cplx*)c->ws_usrc;
+        }
         k_uminv<<<tab.np, 32, 0, s>>>(d_probs, tab, c->d_status);
         if ((st = check_launch(c, "k_uminv"))) return st;
         long e0 = prof_pair(c, 0);
@@ -499,9 +516,11 @@ ng_status ustep(ng_ctx* c, const UProb* d_probs, const std::vector<UHost>& info,
         if (e0 >= 0) cudaEventRecord(c->ev_pool[e0 + 1], s);
         long e1 = prof_pair(c, 1);
         if (e1 >= 0) cudaEventRecord(c->ev_pool[e1], s);
-        k_uboundary<<<tab.np, NG_UBND_THREADS, NG_UBND_SMEM, s>>>(d_probs, tab, c->d_status);
+        k_uboundary_ret<<<tab.np, NG_UBND_THREADS, NG_UBND_SMEM, s>>>(d_probs, tab, c->d_status);
+        k_usrc<<<dim3(tab.nchunk, NG_MAXQ, tab.np), NG_USRC_THREADS, 0, s>>>(d_probs, tab);
+        k_uboundary_les<<<tab.np, NG_UBND_THREADS, NG_UBND_SMEM, s>>>(d_probs, tab, c->d_status);
         if (e1 >= 0) cudaEventRecord(c->ev_pool[e1 + 1], s);
-        if ((st = check_launch(c, "k_uboundary"))) return st;
+        if ((st = check_launch(c, "k_uboundary_ret/k_usrc/k_uboundary_les"))) return st;
         if (c->prof) {
             for (size_t i = c0; i < c1; ++i) {
                 const UHost& u = info[active[i]];
@@ -664,6 +683,7 @@ void ng_destroy(ng_ctx* c) {
     cudaFree(c->ws_uni);
     cudaFree(c->ws_minv);
     cudaFree(c->ws_adj);
+    cudaFree(c->ws_usrc);
     delete c;
 }
 
@@ -1276,11 +1296,6 @@ ng_status ng_batch_step(ng_ctx* c, ng_batch* b, int n, int threads, void* stream
     for (int p = 0; p < b->np; ++p)
         if (n > b->info[p].k && n <= b->info[p].nt) active.push_back(p);
     if (active.empty()) return NG_OK;
-    static bool smem_set = false;
-    if (!smem_set) {
-        CUDA_TRY(c, cudaFuncSetAttribute(k_uboundary, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)NG_UBND_SMEM));
-        smem_set = true;
-    }
     return ustep(c, b->d_probs, b->info, active, n, threads, (cudaStream_t)stream);
 }
 

@@ -27,7 +27,12 @@ struct UTable {
     int start[NG_UMAXP + 1];
     int prob[NG_UMAXP];
     int nles[NG_UMAXP], ntv[NG_UMAXP];
+    // partial sums of the (A) rows' sources and histories: src[((i * NG_MAXQ + r) * nchunk +
+    // c) * 2 + {0: source, 1: history}][a * D + b], chunks of `chunk` summation indices
+    cplx* src;
+    int nchunk, chunk;
 };
+#define NG_USRC_THREADS 256
 
 // element (a,b) of a stored d x d block
 __device__ __forceinline__ cplx uel(const Comp& c, int64_t e, int D, int a, int b, int kb) {
@@ -241,22 +246,27 @@ __global__ void __launch_bounds__(256) k_ubulk(const UProb* probs, UTable tab, i
     (sizeof(cplx) * ((NG_KMAX * NG_UMAXD) * (NG_KMAX * NG_UMAXD) + (NG_KMAX * NG_UMAXD) * NG_UMAXD + \
                      NG_UBND_THREADS + 2 * (2 * NG_KMAX + 1) * NG_UMAXD * NG_UMAXD))
 
-// -i (C^<_2 + C^<_3)[Sigma,1,G](m,n) element (a,b), partial over j = j0, j0+js, ...
-__device__ cplx u_qlesA_part(const NgWeights& W, const Grid& g, const HermV& G, const HermV& S, int m, int n, int D,
-                             int a, int b, int kb, int j0, int js) {
+// -i (C^<_2 + C^<_3)[Sigma,1,G](m,n) element (a,b), partial over the summation indices
+// i = i0, i0+is, ... < i1 of the concatenated range: i <= jmax is the C^<_2 term j = i, the
+// rest the C^<_3 term j = i - jmax - 1 (jmax = max(n, k))
+__device__ cplx u_qlesA_range(const NgWeights& W, const Grid& g, const HermV& G, const HermV& S, int m, int n, int D,
+                              int a, int b, int kb, int i0, int i1, int is) {
     const int k = W.k, T = g.ntau, T1 = g.ntau + 1;
     cplx c2 = cz(), c3 = cz();
     const int jmax = n <= k ? k : n;
-    for (int j = j0; j <= jmax; j += js) {
-        const double w = n <= k ? W.greg[n][j] : gw(W, n, j);
-        for (int c = 0; c < D; ++c)   // Sigma^<(m,j) G^A(j,n), G^A(j,n)_cb = conj(G~^R(n,j)_bc)
-            c2 = cfma(cscal(w, ules(S, m, j, D, a, c, kb)), cconj(uretx(G, n, j, D, b, c, kb)), c2);
-    }
-    for (int j = j0; j <= T; j += js) {
-        const double w = gw(W, T, j);
-        for (int c = 0; c < D; ++c)   // Sigma^tv(m,j) [G^tv(n,T-j)]^dagger
-            c3 = cfma(cscal(w, uel(S.tv, (int64_t)m * T1 + j, D, a, c, kb)),
-                      cconj(uel(G.tv, (int64_t)n * T1 + T - j, D, b, c, kb)), c3);
+    for (int i = i0; i < i1; i += is) {
+        if (i <= jmax) {
+            const int j = i;
+            const double w = n <= k ? W.greg[n][j] : gw(W, n, j);
+            for (int c = 0; c < D; ++c)   // Sigma^<(m,j) G^A(j,n), G^A(j,n)_cb = conj(G~^R(n,j)_bc)
+                c2 = cfma(cscal(w, ules(S, m, j, D, a, c, kb)), cconj(uretx(G, n, j, D, b, c, kb)), c2);
+        } else {
+            const int j = i - jmax - 1;
+            const double w = gw(W, T, j);
+            for (int c = 0; c < D; ++c)   // Sigma^tv(m,j) [G^tv(n,T-j)]^dagger
+                c3 = cfma(cscal(w, uel(S.tv, (int64_t)m * T1 + j, D, a, c, kb)),
+                          cconj(uel(G.tv, (int64_t)n * T1 + T - j, D, b, c, kb)), c3);
+        }
     }
     return cadd(cscal(g.h, cmulmi(c2)), cscal((double)g.sig * g.htau, c3));
 }
@@ -274,19 +284,19 @@ __device__ void u_stepmat(const NgWeights& W, const UProb& P, int m, cplx* out) 
         }
 }
 
-__global__ void __launch_bounds__(NG_UBND_THREADS) k_uboundary(const UProb* probs, UTable tab, int* status) {
+// The boundary of step n runs in three launches: k_uboundary_ret (retarded (A) start-up along
+// row n and G^<(0,n), one block per problem), k_usrc (sources and partial histories of the
+// lesser (A) rows, O((k+1)(n + ntau) nf^3) per problem, over many blocks), k_uboundary_les (the
+// serial lesser (A) steps, one block per problem).
+__global__ void __launch_bounds__(NG_UBND_THREADS) k_uboundary_ret(const UProb* probs, UTable tab, int* status) {
     const UProb& P = probs[tab.prob[blockIdx.x]];
     const NgWeights& W = c_W[P.g.k - 1];
     const Grid& g = P.g;
     const int D = g.nf, DD = D * D, k = W.k, n = tab.n, kb = P.kb, t = threadIdx.x;
-    // dynamic shared memory (NG_UBND_SMEM bytes): A[(kD)^2], B[kD x D], red[threads],
-    // qs/hs[(2k+1) x D^2] (sources and partial histories of the (A) rows)
+    // dynamic shared memory (NG_UBND_SMEM bytes): A[(kD)^2], B[kD x D], ...
     extern __shared__ unsigned char ub_smem[];
     cplx* A = reinterpret_cast<cplx*>(ub_smem);
     cplx* B = A + (NG_KMAX * NG_UMAXD) * (NG_KMAX * NG_UMAXD);
-    cplx* red = B + (NG_KMAX * NG_UMAXD) * NG_UMAXD;
-    cplx(*qs)[NG_UMAXD * NG_UMAXD] = reinterpret_cast<cplx(*)[NG_UMAXD * NG_UMAXD]>(red + NG_UBND_THREADS);
-    cplx(*hs)[NG_UMAXD * NG_UMAXD] = qs + (2 * NG_KMAX + 1);
     const int N = k * D;
     // ---- retarded start-up along row n (conjugate VIDE, implementation (A)) ----------
     // transposed system: rows (j, a), columns (l, b): A = Mh[l][j]^T, B = -(y0 Mh[0][j])^T
@@ -325,36 +335,82 @@ __global__ void __launch_bounds__(NG_UBND_THREADS) k_uboundary(const UProb* prob
         const int a = q / D, b = q % D;
         ust(P.G.les, tri(n) + 0, D, a, b, kb, cneg(cconj(uel(P.G.tv, (int64_t)n * (g.ntau + 1), D, b, a, kb))));
     }
+}
+
+// Sources q_A(m,n) and partial histories sum_{l<m0} w_{m,l} Sigma^R(m,l) G^<(l,n) of the (A) rows
+// of every active problem, spread over blocks (chunk, row, problem); within a block, groups of
+// D^2 threads take the summation indices in turn and are combined in a fixed order.
+__global__ void __launch_bounds__(NG_USRC_THREADS) k_usrc(const UProb* probs, UTable tab) {
+    const int i = blockIdx.z, r = blockIdx.y, ch = blockIdx.x;
+    const UProb& P = probs[tab.prob[i]];
+    const NgWeights& W = c_W[P.g.k - 1];
+    const Grid& g = P.g;
+    const int D = g.nf, DD = D * D, k = W.k, n = tab.n, kb = P.kb, t = threadIdx.x;
+    const bool full = (n <= 2 * k);
+    const int m0 = full ? 1 : n - k;
+    const int nq = n - m0 + 1;
+    if (r >= nq) return;
+    const int m = m0 + r;
+    const int jmax = n <= k ? k : n;
+    const int nsum = jmax + 1 + g.ntau + 1;
+    const int i0 = ch * tab.chunk, i1 = min(nsum, i0 + tab.chunk);
+    const int ngrp = NG_USRC_THREADS / DD, grp = t / DD, ab = t % DD, a = ab / D, b = ab % D;
+    __shared__ cplx red[2][NG_USRC_THREADS];
+    cplx qv = cz(), hv = cz();
+    if (grp < ngrp && i0 < i1) {
+        qv = u_qlesA_range(W, g, P.G, P.S, m, n, D, a, b, kb, i0 + grp, i1, ngrp);
+        if (!full && m > k)
+            for (int l = i0 + grp; l < min(i1, m0); l += ngrp)
+                for (int c = 0; c < D; ++c)
+                    hv = cfma(cscal(gw(W, m, l), uel(P.S.ret, tri(m) + l, D, a, c, kb)),
+                              uel(P.G.les, tri(n) + l, D, c, b, kb), hv);
+    }
+    red[0][t] = qv;
+    red[1][t] = hv;
     __syncthreads();
+    if (t < DD) {
+        cplx sq = cz(), sh = cz();
+        for (int gi = 0; gi < ngrp; ++gi) {
+            sq = cadd(sq, red[0][gi * DD + t]);
+            sh = cadd(sh, red[1][gi * DD + t]);
+        }
+        cplx* dst = tab.src + ((int64_t)((i * NG_MAXQ + r) * tab.nchunk + ch) * 2) * (NG_UMAXD * NG_UMAXD);
+        dst[t] = sq;
+        dst[NG_UMAXD * NG_UMAXD + t] = sh;
+    }
+}
+
+__global__ void __launch_bounds__(NG_UBND_THREADS) k_uboundary_les(const UProb* probs, UTable tab, int* status) {
+    const UProb& P = probs[tab.prob[blockIdx.x]];
+    const NgWeights& W = c_W[P.g.k - 1];
+    const Grid& g = P.g;
+    const int D = g.nf, DD = D * D, k = W.k, n = tab.n, kb = P.kb, t = threadIdx.x;
+    // dynamic shared memory (NG_UBND_SMEM bytes): A[(kD)^2], B[kD x D], (unused)[threads],
+    // qs/hs[(2k+1) x D^2] (sources and partial histories of the (A) rows)
+    extern __shared__ unsigned char ub_smem[];
+    cplx* A = reinterpret_cast<cplx*>(ub_smem);
+    cplx* B = A + (NG_KMAX * NG_UMAXD) * (NG_KMAX * NG_UMAXD);
+    cplx* red = B + (NG_KMAX * NG_UMAXD) * NG_UMAXD;
+    cplx(*qs)[NG_UMAXD * NG_UMAXD] = reinterpret_cast<cplx(*)[NG_UMAXD * NG_UMAXD]>(red + NG_UBND_THREADS);
+    cplx(*hs)[NG_UMAXD * NG_UMAXD] = qs + (2 * NG_KMAX + 1);
+    const int N = k * D;
     // ---- lesser column: rows by (A) ----------------------------------------------------
     const bool full = (n <= 2 * k);
     const int m0 = full ? 1 : n - k;
     const int nq = n - m0 + 1;
-    const int ngrp = blockDim.x / DD;         // thread groups over j
-    const int grp = t / DD, ab = t % DD, a = ab / D, b = ab % D;
-    for (int r = 0; r < nq; ++r) {
-        const int m = m0 + r;
-        cplx qv = cz(), hv = cz();
-        if (grp < ngrp) {
-            qv = u_qlesA_part(W, g, P.G, P.S, m, n, D, a, b, kb, grp, ngrp);
-            if (!full && m > k)
-                for (int l = grp; l < m0; l += ngrp)
-                    for (int c = 0; c < D; ++c)
-                        hv = cfma(cscal(gw(W, m, l), uel(P.S.ret, tri(m) + l, D, a, c, kb)),
-                                  uel(P.G.les, tri(n) + l, D, c, b, kb), hv);
+    // sources and partial histories: chunk partials of k_usrc summed in chunk order
+    for (int q = t; q < nq * DD; q += blockDim.x) {
+        const int r = q / DD, ab = q % DD;
+        const cplx* src = tab.src + ((int64_t)(blockIdx.x * NG_MAXQ + r) * tab.nchunk * 2) * (NG_UMAXD * NG_UMAXD);
+        cplx sq = cz(), sh = cz();
+        for (int ch = 0; ch < tab.nchunk; ++ch) {
+            sq = cadd(sq, src[(2 * ch) * (NG_UMAXD * NG_UMAXD) + ab]);
+            sh = cadd(sh, src[(2 * ch + 1) * (NG_UMAXD * NG_UMAXD) + ab]);
         }
-        // reduce over groups (fixed order)
-        for (int pass = 0; pass < 2; ++pass) {
-            red[t] = pass == 0 ? qv : hv;
-            __syncthreads();
-            if (t < DD) {
-                cplx s = cz();
-                for (int gi = 0; gi < ngrp; ++gi) s = cadd(s, red[gi * DD + t]);
-                if (pass == 0) qs[r][t] = s; else hs[r][t] = s;
-            }
-            __syncthreads();
-        }
+        qs[r][ab] = sq;
+        hs[r][ab] = sh;
     }
+    __syncthreads();
     if (t != 0) return;
     int sing = 0;
     int mstep = m0;
