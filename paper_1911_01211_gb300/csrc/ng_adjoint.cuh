@@ -38,7 +38,7 @@ __device__ __forceinline__ cplx adj_sigT(const AdjStep& a, int m, int j) {   // 
 __device__ __forceinline__ cplx adj_mf(const AdjStep& a, int m, int kb) {
     return m == a.n ? a.mfc[kb] : a.mf[(int64_t)(m + 1) * a.g.nb + kb];
 }
-// c += v, with the conjugate for an element reached through Sigma~^R or Sigma^< (j < m)
+// *p += v (one writer per target: the callers map every contribution to its stored element)
 __device__ __forceinline__ void cacc_to(cplx* p, cplx v) { *p = cadd(*p, v); }
 
 // warp sum in a fixed butterfly order
