@@ -15,6 +15,9 @@ the W warm-up steps), so a short window measures the most expensive steps.
 
 Lines printed: one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on the
 host cores for the same metric (a bounded sample of k-point steps of the same workload).
+Other workloads: --workload uneven (64 independent clusters, the batch path; --compare-plain
+adds the same problems solved one after another) and --workload adjoint (gradient of the final
+kinetic energy on the 16 x 16 square lattice, with finite-difference checks).
 """
 import argparse
 import json
@@ -60,7 +63,8 @@ def parse():
     ap.add_argument("--compare-plain", action="store_true",
                     help="uneven: also solve the same problems one after another with the plain path")
     ap.add_argument("--precision", choices=["f64", "both"], default="both",
-                    help="f64: the FP64 headline only; both: also time the FP32-compensated mode")
+                    help="f64: the FP64 headline only; both: also re-propagate with the FP32-compensated "
+                         "(f32c) and double-float (df64) modes and report them beside the headline")
     return ap.parse_args()
 
 
