@@ -42,6 +42,24 @@ def fp64_peak_tflops(sm_mhz):
     return GB300_SMS * FP64_FLOP_PER_CLK_PER_SM * (sm_mhz or SM_MAX_MHZ) * 1e6 / 1e12
 
 
+def max_over_ranks(x, device="cuda"):
+    """Largest value of x over the ranks of the default process group (x itself when there is
+    none or it has one rank): the slowest rank's time sets the whole job's rate."""
+    import torch
+    import torch.distributed as td
+    if not (td.is_available() and td.is_initialized()) or td.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    """Units processed by all ranks per second of the slowest rank (weak scaling: every rank
+    runs the full workload)."""
+    return world * units_per_rank / seconds
+
+
 def parse():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -293,12 +311,9 @@ def run_ours(a):
 
     ms, prof, clk, t_job1 = propagate(ng.NG_FP64)
     st, flags = ctx.status_sync()
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * w.nbatch * K / (ms / 1e3)
-    e2e_value = world * w.nbatch * (w.nt - k) / (t_job1 - t_job0)
+    ms = max_over_ranks(ms)
+    value = whole_job_rate(w.nbatch * K, world, ms / 1e3)
+    e2e_value = whole_job_rate(w.nbatch * (w.nt - k), world, max_over_ranks(t_job1 - t_job0))
     # per step: extrapolation, then per corrector pass k-reduce, Hartree, 2B, M_n^-1 (+ bulk, boundary)
     launches = int(prof["bulk_launches"] + prof["boundary_launches"]) + K * (1 + 3 * 4)
     achieved = prof["bulk_flops"] / (prof["bulk_ms"] / 1e3) / 1e12
@@ -346,7 +361,7 @@ def run_ours(a):
             stm, flagsm = ctx.status_sync()
             err = {c: float((x - ref[c]).abs().max() / ref[c].abs().max()) for c, x in sl().items()}
             err["rho_loc_abs"] = float(np.abs(rho_host[k + 1:].numpy() - rho).max())
-            vm = world * w.nbatch * K / (msm / 1e3)
+            vm = whole_job_rate(w.nbatch * K, world, max_over_ranks(msm) / 1e3)
             cmacs = profm["bulk_flops"] / (8.0 * w.nf ** 3)
             modes[name] = {
                 "value": vm, "unit": "k-point timesteps/s", "ms_per_step": msm / K, "dtype": name,
