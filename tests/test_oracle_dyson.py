@@ -128,3 +128,24 @@ def test_planted_kernel_sign_error_is_caught(monkeypatch):
     monkeypatch.setattr(dyson, "tv_row", broken)
     G, ex, _ = embedded_level(20, 20, 2.0, 0.1)
     assert max_err(G, ex)["tv"] > 1e-4
+
+
+def test_equilibrium_time_translation_invariance():
+    """A time-independent problem in equilibrium (the embedded level, Sigma = V^2 g0) has
+    G(t, t') depending on t - t' only and a constant density: the discrete solution keeps
+    this to discretisation accuracy, and the deviation falls with h like the solver's error."""
+    devs = []
+    for N in (20, 40):
+        h = 2.0 / N
+        G, _, _ = embedded_level(N, 40, 2.0, h)
+        R, L = G.ret[..., 0, 0], G.les[..., 0, 0]
+        d = 0.0
+        for lag in range(0, N // 2):
+            r = np.array([R[n, n - lag] for n in range(lag, N + 1)])
+            l = np.array([L[n - lag, n] for n in range(lag, N + 1)])
+            d = max(d, np.abs(r - r[0]).max(), np.abs(l - l[0]).max())
+        dens = np.array([L[n, n] for n in range(N + 1)])
+        d = max(d, np.abs(dens - dens[0]).max())
+        devs.append(d)
+    assert devs[-1] < 1e-8, devs
+    assert devs[0] / devs[1] > 2 ** 5 * 0.7, devs
