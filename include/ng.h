@@ -336,7 +336,8 @@ ng_status ng_solve_fixed(ng_ctx *ctx, const ng_grid *grid, ng_herm G, ng_herm Si
  * walked backwards.  The start slices are a fixed point of the bootstrapping; their adjoint
  * is iterated to |change| <= p->boot_tol |mu| (default 1e-14), at most p->boot_maxiter times.
  * grad_eps0 (device, [nt+2][nbatch] double): dL/deps0_kb(t_n) at index n+1 (row 0 unused).
- * G, Gloc, Sigma and eps_mf are rewritten with bitwise-equal values by the recomputation.
+ * G, Sigma and eps_mf are rewritten with bitwise-equal values by the recomputation; Gloc is
+ * rewritten too (its slices 0..k from the final start slices of G).
  * info (host, may be NULL) receives {start-slice iterations, segments, segment length}.
  * Errors: NG_EUNSUPPORTED for nf != 1; NG_EINVAL for bad layouts; NG_ENOCONV if the start-slice
  * adjoint did not converge; NG_ENOMEM if the context workspace cannot be allocated. */
