@@ -36,8 +36,9 @@
  *  - Preconditions follow the paper's Table tab:dyson: a call at time step tstp reads
  *    slices < tstp of G and slices <= tstp of Sigma and eps.
  *  - Thread safety: one context per host thread.  A context may be used with several
- *    streams, but calls that share its workspace (ng_dyson_mat, ng_dyson_start,
- *    ng_distance) must not overlap on the device.
+ *    streams, but calls that share its workspaces (ng_dyson_mat, ng_dyson_start,
+ *    ng_distance_timestep, ng_dyson_timestep with nf = 4, 8 or a non-FP64 precision,
+ *    ng_run_2b, ng_batch_*, ng_adjoint_2b) must not overlap on the device.
  */
 #ifndef NG_H
 #define NG_H
@@ -56,7 +57,7 @@ typedef enum {
     NG_ENOCONV = 4,       /* a self-consistency loop hit its iteration limit             */
     NG_ETIMEOUT = 5,      /* reserved: a bounded device wait gave up                     */
     NG_ENONFINITE = 6,    /* a non-finite value was produced (device status word)        */
-    NG_EUNSUPPORTED = 7,  /* valid but not implemented here (e.g. nf > 2)                */
+    NG_EUNSUPPORTED = 7,  /* valid but not implemented here (e.g. NG_F32C with nf > 2)    */
     NG_ESCRATCH = 8       /* the problem needs more than the fixed static scratch of the  */
                           /* allocation-free entry point (nothing launched)              */
 } ng_status;
@@ -70,7 +71,7 @@ typedef struct ng_ctx ng_ctx;
 typedef struct {
     int nt;        /* number of real-time steps N_t (slices 0..nt)                       */
     int ntau;      /* number of imaginary-time intervals N_tau (points 0..ntau)            */
-    int nf;        /* orbital dimension d (1 or 2 in this build)                            */
+    int nf;        /* orbital dimension d: 1, 2, 4 or 8                                     */
     int nbatch;    /* number of problems stored innermost                                   */
     int korder;    /* solve order k, 1..5; requires nt >= 2k+2 and ntau >= 2k+2             */
     int sig;       /* -1: fermions (only value accepted)                                    */
