@@ -189,11 +189,13 @@ ng_status ng_dyson_timestep(ng_ctx *ctx, const ng_grid *grid, int tstp, ng_herm 
  *    library holds until the process exits; its first 256 bytes hold a status word.
  *  - Size limit: the call needs 256 + 16 nbatch ((k nf)^2 + k nf^2) bytes and returns
  *    NG_ESCRATCH, launching nothing, above 2 MiB (at k = 5: at most 4369 problems with nf = 1,
- *    1092 with nf = 2).  Other argument errors return NG_EINVAL / NG_EUNSUPPORTED.
+ *    1092 with nf = 2, 273 with nf = 4, 68 with nf = 8).  Other argument errors return
+ *    NG_EINVAL / NG_EUNSUPPORTED.
  *  - It calls no cudaMalloc, cudaFree or allocating library routine.
  *  - The first call on a device does one-time set-up with that device current: it copies the
- *    integration weights to constant memory (unless ng_create already did on that device) and
- *    looks up the array's device address with cudaGetSymbolAddress.  Make that first call from
+ *    integration weights to the constant memory of every part of the library (unless ng_create
+ *    already did on that device), so contexts created later on that device need no copy of
+ *    their own, and looks up the array's device address with cudaGetSymbolAddress.  Make that first call from
  *    one host thread, before any stream capture.
  *  - Every call uses the same array and leaves its contents there; the status word is cleared
  *    at the start of each call, and everything else is written before it is read.  Calls whose

@@ -78,6 +78,21 @@ namespace {
 
 bool g_weights_loaded[64] = {false};
 
+// Integration weights of every order into constant memory of device `dev` (current): this
+// file's c_W and the adjoint translation unit's own copy, together, once per device.
+ng_status load_weights_once(int dev) {
+    if (dev < 0 || dev >= 64) return NG_EUNSUPPORTED;
+    if (g_weights_loaded[dev]) return NG_OK;
+    NgWeights all[NG_KMAX];
+    for (int k = 1; k <= NG_KMAX; ++k) ng_make_weights(k, &all[k - 1]);
+    if (cudaMemcpyToSymbol(c_W, all, sizeof(all)) != cudaSuccess || adj_load_weights(all) != cudaSuccess) {
+        cudaGetLastError();
+        return NG_ECUDA;
+    }
+    g_weights_loaded[dev] = true;
+    return NG_OK;
+}
+
 ng_status fail(ng_ctx* c, ng_status s, const char* fmt, ...) {
     if (c) {
         va_list ap;
@@ -644,15 +659,9 @@ ng_status ng_create(int korder, int device, ng_ctx** out) {
     c->k = korder;
     c->device = device;
     ng_make_weights(korder, &c->W);
-    if (device >= 0 && device < 64 && !g_weights_loaded[device]) {
-        NgWeights all[NG_KMAX];
-        for (int k = 1; k <= NG_KMAX; ++k) ng_make_weights(k, &all[k - 1]);
-        if (cudaMemcpyToSymbol(c_W, all, sizeof(all)) != cudaSuccess || adj_load_weights(all) != cudaSuccess) {
-            cudaGetLastError();
-            delete c;
-            return NG_ECUDA;
-        }
-        g_weights_loaded[device] = true;
+    if (ng_status ws = load_weights_once(device)) {
+        delete c;
+        return ws;
     }
     if (cudaMalloc(&c->d_status, sizeof(int)) != cudaSuccess || cudaMalloc(&c->d_scalar, sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
@@ -1063,7 +1072,7 @@ extern "C" ng_status ng_dyson_start_noalloc(const ng_grid* grid, ng_herm G, ng_h
     if (q.korder < 1 || q.korder > NG_KMAX || q.sig != -1 || q.nbatch < 1 || !(q.h > 0.0) || !(q.beta > 0.0))
         return NG_EINVAL;
     if (q.nt < 2 * q.korder + 2 || q.ntau < 2 * q.korder + 2 || q.nf < 1) return NG_EINVAL;
-    if (q.nf > 2) return NG_EUNSUPPORTED;
+    if (q.nf != 1 && q.nf != 2 && q.nf != 4 && q.nf != 8) return NG_EUNSUPPORTED;
     if (G.ldk != q.nbatch || (S.ldk != 1 && S.ldk != q.nbatch) || (eps.ldk != 1 && eps.ldk != q.nbatch))
         return NG_EINVAL;
     const void* ptrs[] = {G.mat, G.ret, G.les, G.tv, S.mat, S.ret, S.les, S.tv, eps.val};
@@ -1077,12 +1086,7 @@ extern "C" ng_status ng_dyson_start_noalloc(const ng_grid* grid, ng_herm G, ng_h
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return NG_ECUDA; }
     if (dev < 0 || dev >= 64) return NG_EUNSUPPORTED;
-    if (!g_weights_loaded[dev]) {
-        NgWeights all[NG_KMAX];
-        for (int k = 1; k <= NG_KMAX; ++k) ng_make_weights(k, &all[k - 1]);
-        if (cudaMemcpyToSymbol(c_W, all, sizeof(all)) != cudaSuccess) { cudaGetLastError(); return NG_ECUDA; }
-        g_weights_loaded[dev] = true;
-    }
+    if (ng_status ws = load_weights_once(dev)) return ws;
     if (!g_noalloc_addr[dev]) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) { cudaGetLastError(); return NG_ECUDA; }
@@ -1110,7 +1114,12 @@ extern "C" ng_status ng_dyson_start_noalloc(const ng_grid* grid, ng_herm G, ng_h
     int* status = (int*)base;
     cplx* ws = (cplx*)(base + NG_NOALLOC_STATUS_BYTES);
     if (cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess) { cudaGetLastError(); return NG_ECUDA; }
-    return q.nf == 1 ? noalloc_start<1>(g, Gv, Sv, ev, ws, status, s) : noalloc_start<2>(g, Gv, Sv, ev, ws, status, s);
+    switch (q.nf) {
+        case 1: return noalloc_start<1>(g, Gv, Sv, ev, ws, status, s);
+        case 2: return noalloc_start<2>(g, Gv, Sv, ev, ws, status, s);
+        case 4: return noalloc_start<4>(g, Gv, Sv, ev, ws, status, s);
+        default: return noalloc_start<8>(g, Gv, Sv, ev, ws, status, s);
+    }
 }
 
 // =========================================================================================

@@ -7,9 +7,16 @@ managing device memory.  ng_dyson_start_noalloc serves them with a fixed static 
 instead of context-owned workspace.  These tests call it through the C ABI and check that it
 reproduces ng_dyson_start (the existing entry point) within the parity tolerance, on two
 calls in a row with different problem sizes, and that an oversized batch is refused before
-anything is launched.  The first call may be the first libng call of the process, so it
-also exercises the one-time per-device set-up.
+anything is launched.  When this file runs alone the first call is the first libng call of
+the process; the last test makes sure of that case whatever ran before, by running the
+allocation-free start-up first in a child process with its own CUDA context and checking
+that the contexts created after it still compute the same adjoint gradient.
 """
+import json
+import os
+import subprocess
+import sys
+
 import numpy as np
 import pytest
 import torch
@@ -52,7 +59,7 @@ def _max_rel(ng, g, A, B, k):
 def test_noalloc_start_matches_dyson_start_twice():
     import paper_1911_01211_gb300 as ng
     ng.load_library()
-    cases = [(1, 3, 41), (2, 2, 43)]   # (nf, nbatch, seed): two calls in a row, different sizes
+    cases = [(1, 3, 41), (2, 2, 43), (4, 1, 47)]   # (nf, nbatch, seed): calls in a row, different sizes
     prepared = [_inputs(ng, d, nb, seed) for d, nb, seed in cases]
     results = []
     for g, S, eps, G0 in prepared:    # allocation-free calls first (possibly the first libng calls)
@@ -81,3 +88,23 @@ def test_noalloc_start_rejects_oversized_batch():
     assert ng.dyson_start_noalloc(g, G, S, eps) == ng.NG_ESCRATCH
     torch.cuda.synchronize()
     assert float(G.tv.abs().max()) == 0.0      # nothing was launched
+
+
+def _child_gradient(order):
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-m", "tests.noalloc_child", order], cwd=root, capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-4000:]
+    line = [x for x in r.stdout.splitlines() if x.startswith("{")][-1]
+    return np.array(json.loads(line)["grad"])
+
+
+def test_noalloc_first_call_leaves_later_contexts_intact():
+    """The one-time set-up of a first allocation-free call loads the integration weights for the
+    whole library: an adjoint gradient computed after it in the same process equals the one of
+    a process that created its context first."""
+    g_first = _child_gradient("noalloc_first")
+    g_ref = _child_gradient("context_first")
+    scale = np.abs(g_ref).max()
+    assert scale > 1e-6
+    assert np.abs(g_first - g_ref).max() <= 1e-13 * scale, (g_first, g_ref)
