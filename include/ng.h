@@ -58,8 +58,9 @@ typedef enum {
     NG_ETIMEOUT = 5,      /* reserved: a bounded device wait gave up                     */
     NG_ENONFINITE = 6,    /* a non-finite value was produced (device status word)        */
     NG_EUNSUPPORTED = 7,  /* valid but not implemented here (e.g. NG_F32C with nf > 2)    */
-    NG_ESCRATCH = 8       /* the problem needs more than the fixed static scratch of the  */
+    NG_ESCRATCH = 8,      /* the problem needs more than the fixed static scratch of the  */
                           /* allocation-free entry point (nothing launched)              */
+    NG_ECOMM = 9          /* the caller's rank-exchange callback reported a failure       */
 } ng_status;
 
 /* device status word bits (ng_status_sync) */
@@ -97,6 +98,12 @@ typedef struct {
  * double-float arithmetic (each value an FP32 pair, 48 significand bits; products with their
  * cross terms, TwoSum accumulation), FP64-class accuracy on the FP32 pipes. */
 typedef enum { NG_FP64 = 0, NG_F32C = 1, NG_DF64 = 2 } ng_precision;
+
+/* Schedule of a time step (Sec. "Time stepping"): NG_MIXED is the paper's parallel variant
+ * (implementation (B) for the bulk of the retarded row and lesser column, (A) near the
+ * diagonal); NG_SERIAL is its serial variant, implementation (A) along the whole retarded row
+ * (conjugate VIDE) and the whole lesser column.  The two agree to discretisation level. */
+typedef enum { NG_MIXED = 0, NG_SERIAL = 1 } ng_schedule;
 
 /* Parameters of the self-consistent second-Born driver (ng_run_2b). */
 typedef struct {
@@ -173,9 +180,13 @@ ng_status ng_dyson_start(ng_ctx *ctx, const ng_grid *grid, ng_herm G, ng_herm Si
  * nbatch) and Sigma: slices < tstp are converted once when tstp first reaches them, Sigma's
  * slice tstp on every call.  Call ng_precision_reset after changing slices < tstp of G or
  * Sigma in place (the copies are also rebuilt when the buffers or the grid change).
- * Workspace: 8 bytes per complex element of G and Sigma. */
+ * Workspace: 8 bytes per complex element of G and Sigma.
+ * schedule: NG_MIXED (above) or NG_SERIAL (the retarded row by the conjugate VIDE start-up and
+ * steps along the whole row, the lesser column by the VIDE start-up and steps along the whole
+ * column, each step's sums as block reductions, one block per problem; NG_FP64 and nf <= 2 only,
+ * NG_EUNSUPPORTED otherwise). */
 ng_status ng_dyson_timestep(ng_ctx *ctx, const ng_grid *grid, int tstp, ng_herm G,
-                            ng_herm Sigma, ng_func eps, int precision, void *stream);
+                            ng_herm Sigma, ng_func eps, int precision, int schedule, void *stream);
 
 /* Allocation-free start-up: the same computation as ng_dyson_start, for callers that must
  * not allocate device memory.  Examples: a host application whose caching allocator already
@@ -210,13 +221,81 @@ ng_status ng_dyson_start_noalloc(const ng_grid *grid, ng_herm G, ng_herm Sigma, 
 /* Forget the FP32 copies kept for NG_F32C time steps (they are rebuilt on the next call). */
 ng_status ng_precision_reset(ng_ctx *ctx);
 
+/* ---- convolution (Table tab:convolution) ---------------------------------------------- */
+
+/* Time slice tstp of the contour convolution C = A * f * B (Sec. "Numerical details:
+ * convolution integrals on C", Eqs. cm1, cm2, cr1, ctv1-ctv3, cles1-cles3; Sec. "Implementation:
+ * convolution"), with the k-th order Gregory and boundary (R) quadratures of the context:
+ *   tstp = -1: C^M(tau_m), m = 0..ntau;
+ *   tstp >= 0: C^R(tstp, m) for m <= tstp, C^tv(tstp, m) for m = 0..ntau and C^<(m, tstp) for
+ *              m <= tstp.
+ * Acc and Bcc are the hermitian conjugates A^ddagger and B^ddagger, which supply the values
+ * outside the stored triangles (Eq. hermconjg); pass A itself when A is hermitian symmetric.
+ * f is a single-time function (f_{-1} enters the Matsubara and mixed pieces); f.val = NULL is
+ * the identity.  Reads slices 0..max(tstp, k) of A, Acc, B, Bcc and f (the start-up quadrature
+ * of tstp <= k uses slices up to k), writes slice tstp of C only.  C.ldk = nbatch (inputs with
+ * ldk 1 or nbatch) or C.ldk = 1 with every input shared.  nf = 1, 2, 4, 8. */
+ng_status ng_convolution_timestep(ng_ctx *ctx, const ng_grid *grid, int tstp, ng_herm C, ng_herm A, ng_herm Acc,
+                                  ng_func f, ng_herm B, ng_herm Bcc, void *stream);
+
 /* ---- slice operations ----------------------------------------------------------------- */
 
-/* Local Green's function slice tstp (-1 = Matsubara): Gloc = (1/nbatch) sum_kb Gk
- * (Sec. "GW for the translationally invariant Hubbard model", get_loc), summed in a fixed
- * order (deterministic).  Gloc must have ldk = 1, Gk ldk = nbatch. */
+/* Local Green's function slice tstp (-1 = Matsubara): Gloc = sum_kb w_kb Gk_kb
+ * (Sec. "GW for the translationally invariant Hubbard model", get_loc), w_kb = 1/nbatch when
+ * wk is NULL, else wk = device array of nbatch doubles (k-point weights).  Deterministic, in a
+ * fixed order that does not depend on a split of the k-points over ranks: the k axis is cut
+ * into blocks of 32 consecutive indices, each block's weighted values are summed in a fixed
+ * butterfly order, the block sums are added in block order, the 1/nbatch factor comes last.
+ * Gloc must have ldk = 1, Gk ldk = nbatch. */
 ng_status ng_kreduce_timestep(ng_ctx *ctx, const ng_grid *grid, int tstp, ng_herm Gloc,
-                              ng_herm Gk, void *stream);
+                              ng_herm Gk, const double *wk, void *stream);
+
+/* ---- k-point sharding over ranks (Sec. "MPI parallelization", Eq. dyson_kspace) --------
+ * nk k-points are split over nranks ranks (one GPU each) in whole blocks of 32: with
+ * B = ceil(nk / 32) blocks, rank r owns blocks [floor(r B / nranks), floor((r+1) B / nranks)),
+ * i.e. the k indices k_begin .. k_begin + k_count - 1.  Each rank keeps the G_k of its own
+ * k-points and a full copy of the shared Gloc and Sigma.  The only exchange is an allgather of
+ * every rank's 32-block sums of the slice being reduced (at most 2 (nt+1) + ntau + 1 elements
+ * of nf^2 complex values per block); adding them in block order on every rank gives bitwise the
+ * single-GPU ng_kreduce_timestep result, so every rank computes the same Sigma. */
+
+/* The share of rank `rank`: *k_begin, *k_count (may be NULL) and *send_bytes (may be NULL;
+ * needs grid for nt, ntau, nf), the size of the per-rank exchange buffer.  Host only, no
+ * device access.  NG_EINVAL if nranks exceeds 64 or the number of blocks. */
+ng_status ng_shard_plan(int nk, int rank, int nranks, const ng_grid *grid, int *k_begin, int *k_count,
+                        size_t *send_bytes);
+
+/* Block sums of slice tstp over the local problems of Gk (ldk = nbatch = the local count), whose
+ * global k indices start at k_begin (a multiple of 32): partial[(bl cnt + i) nf^2 + a nf + b]
+ * (complex128) for the local blocks bl and the slice elements i in the order ret row, les column,
+ * tv row (tstp >= 0; cnt = 2 (tstp+1) + ntau + 1) or mat (tstp = -1; cnt = ntau + 1).  wk: device
+ * weights of the local problems, or NULL (the 1/nk factor is then applied by the combine). */
+ng_status ng_kreduce_partial(ng_ctx *ctx, const ng_grid *grid, int tstp, void *partial, ng_herm Gk,
+                             const double *wk, int k_begin, void *stream);
+
+/* Gloc slice tstp from every rank's block sums: gathered is rank-major, each rank's chunk the
+ * maxb-block send buffer of ng_kreduce_partial (maxb = the largest block count of a rank; rows
+ * beyond a rank's own blocks are ignored).  weighted = 0 multiplies by 1/nk (no weights were
+ * given to the partials), 1 takes the sum as it is.  Gloc: ldk = 1. */
+ng_status ng_kreduce_combine(ng_ctx *ctx, const ng_grid *grid, int tstp, ng_herm Gloc, const void *gathered, int nk,
+                             int nranks, int weighted, void *stream);
+
+/* Rank-exchange description for ng_run_2b_sharded.  send and recv are caller-owned device
+ * buffers of send_bytes (>= the ng_shard_plan value) and nranks * send_bytes.  exchange(user,
+ * bytes) must allgather: after it returns, recv[r * bytes .. (r+1) * bytes) holds rank r's first
+ * `bytes` of send for every r, ordered on the run's stream (an NCCL or torch.distributed
+ * allgather issued on that stream does this); it returns 0 on success.  The driver calls it once
+ * per k-reduction (the block sums) and once per convergence check of the setup loops (one
+ * double, the rank's distance; the ranks' values are summed in rank order). */
+typedef struct {
+    int nk;                                       /* k-points over all ranks                */
+    int rank, nranks;                             /* this rank, number of ranks (<= 64)      */
+    void *send;                                   /* device, send_bytes                      */
+    size_t send_bytes;
+    void *recv;                                   /* device, nranks * send_bytes             */
+    int (*exchange)(void *user, size_t bytes);    /* allgather of `bytes` per rank           */
+    void *user;
+} ng_shard;
 
 /* Second-Born self-energy slice tstp (-1 = Matsubara) from a local G (Eq. sigma_hubb_2b):
  * Sigma_ab(t,t') = U(t)U(t') G_ab(t,t')^2 G_ba(t',t), components by the Langreth product
@@ -299,6 +378,13 @@ ng_status ng_profile_enable(ng_ctx *ctx, int enable);
  * out[4] = number of boundary launches.  `out` must hold 5 doubles. */
 ng_status ng_profile_read(ng_ctx *ctx, double *out);
 
+/* FP64 throughput of the current device, for the roofline of the FP64 kernels: out[0] = the
+ * sustained FP64 FMA-pipe rate (DFMA, 8 independent chains per thread, 8 blocks of 256 threads
+ * per SM) and out[1] = the FP64 tensor rate (DMMA, mma.sync m8n8k4 f64, 4 independent
+ * accumulators per warp), both in TFLOP/s (2 flop per multiply-add), out[2] = the SM count.
+ * Synchronises `stream`; takes about half a second.  `out` must hold 3 doubles. */
+ng_status ng_fp64_probe(double *out, void *stream);
+
 /* ---- driver --------------------------------------------------------------------------- */
 
 /* Self-consistent second-Born run for a batch of problems coupled through
@@ -315,6 +401,33 @@ ng_status ng_profile_read(ng_ctx *ctx, double *out);
 ng_status ng_run_2b(ng_ctx *ctx, const ng_grid *grid, ng_herm G, ng_herm Gloc, ng_herm Sigma,
                     ng_func eps0, ng_func eps_mf, ng_func U, const ng_run_params *p,
                     int *iters_out, void *stream);
+
+/* ng_run_2b with its inputs and outputs in host memory, for callers that keep them there:
+ * eps0_host (complex128, the layout of eps0: [nt+2][nf][nf][nbatch], index n+1 for t_n) is copied
+ * into the device eps0 slice by slice as the run reaches it (slices -1..k with the setup, slice n
+ * before step n), U_host (complex128 [nt+2]) into U once at the start, and after every step n
+ * (and after the bootstrapping for n = 0..k) Gloc^<(t_n, t_n) as the last corrector pass reduced
+ * it (before that pass's Dyson step) is copied to gdiag_host (complex128 [nt+1][nf][nf]; the
+ * local density matrix is -i times it).  All copies are
+ * stream-ordered cudaMemcpyAsync calls on `stream`; page-locked host buffers keep them
+ * asynchronous (pageable ones make every copy wait).  The host buffers must stay valid until
+ * the stream has passed the run.  shard: NULL for all k-points on this GPU, else this rank's
+ * share as in ng_run_2b_sharded (eps0_host then holds the rank's own k-points).  Otherwise as
+ * ng_run_2b; eps0.ldk must be nbatch. */
+ng_status ng_run_2b_host(ng_ctx *ctx, const ng_grid *grid, ng_herm G, ng_herm Gloc, ng_herm Sigma, ng_func eps0,
+                         ng_func eps_mf, ng_func U, const double *eps0_host, const double *U_host, double *gdiag_host,
+                         const ng_run_params *p, const ng_shard *shard, int *iters_out, void *stream);
+
+/* ng_run_2b for this rank's share of the k-points (see ng_shard): grid.nbatch, G, eps0 and
+ * eps_mf hold the rank's own k-points (k_begin .. k_begin + k_count - 1 of ng_shard_plan); Gloc,
+ * Sigma and U are full copies on every rank.  Every k-reduction goes through the exchange, so
+ * Gloc, Sigma and the rank's G_k are bitwise those of a single-GPU ng_run_2b over all nk
+ * k-points (up to the rounding of the convergence distances, which are summed per rank, so a
+ * setup loop could stop one iteration apart when its distance lands within rounding of the
+ * tolerance).  NG_ECOMM if the callback fails. */
+ng_status ng_run_2b_sharded(ng_ctx *ctx, const ng_grid *grid, ng_herm G, ng_herm Gloc, ng_herm Sigma,
+                            ng_func eps0, ng_func eps_mf, ng_func U, const ng_run_params *p, const ng_shard *shard,
+                            int *iters_out, void *stream);
 
 /* Fixed-Sigma solve: dyson_mat, dyson_start, then dyson_timestep for n = k+1..n_to
  * (Sec. "Test of accuracy and scaling analysis", three-step procedure). */

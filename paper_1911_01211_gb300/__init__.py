@@ -21,10 +21,12 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libng.so")
 
-NG_OK, NG_EINVAL, NG_ENOMEM, NG_ECUDA, NG_ENOCONV, NG_ETIMEOUT, NG_ENONFINITE, NG_EUNSUPPORTED, NG_ESCRATCH = range(9)
+(NG_OK, NG_EINVAL, NG_ENOMEM, NG_ECUDA, NG_ENOCONV, NG_ETIMEOUT, NG_ENONFINITE, NG_EUNSUPPORTED, NG_ESCRATCH,
+ NG_ECOMM) = range(10)
 NG_FP64, NG_F32C, NG_DF64 = 0, 1, 2
+NG_MIXED, NG_SERIAL = 0, 1
 _STATUS_NAMES = ["NG_OK", "NG_EINVAL", "NG_ENOMEM", "NG_ECUDA", "NG_ENOCONV", "NG_ETIMEOUT",
-                 "NG_ENONFINITE", "NG_EUNSUPPORTED", "NG_ESCRATCH"]
+                 "NG_ENONFINITE", "NG_EUNSUPPORTED", "NG_ESCRATCH", "NG_ECOMM"]
 
 
 class NgError(RuntimeError):
@@ -55,6 +57,15 @@ class ng_run_params(ctypes.Structure):
                 ("precision", ctypes.c_int)]
 
 
+EXCHANGE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t)
+
+
+class ng_shard(ctypes.Structure):
+    _fields_ = [("nk", ctypes.c_int), ("rank", ctypes.c_int), ("nranks", ctypes.c_int), ("send", ctypes.c_void_p),
+                ("send_bytes", ctypes.c_size_t), ("recv", ctypes.c_void_p), ("exchange", EXCHANGE_FN),
+                ("user", ctypes.c_void_p)]
+
+
 # every symbol the header declares, with its ctypes signature
 _P = ctypes.c_void_p
 _G = ctypes.POINTER(ng_grid)
@@ -67,8 +78,20 @@ SIGNATURES = {
     "ng_green_from_H_const": (ctypes.c_int, [_P, _G, ng_herm, ctypes.POINTER(ctypes.c_double), ctypes.c_double, _P]),
     "ng_dyson_mat": (ctypes.c_int, [_P, _G, ng_herm, ng_herm, ng_func, _P]),
     "ng_dyson_start": (ctypes.c_int, [_P, _G, ng_herm, ng_herm, ng_func, _P]),
-    "ng_dyson_timestep": (ctypes.c_int, [_P, _G, ctypes.c_int, ng_herm, ng_herm, ng_func, ctypes.c_int, _P]),
-    "ng_kreduce_timestep": (ctypes.c_int, [_P, _G, ctypes.c_int, ng_herm, ng_herm, _P]),
+    "ng_dyson_timestep": (ctypes.c_int, [_P, _G, ctypes.c_int, ng_herm, ng_herm, ng_func, ctypes.c_int, ctypes.c_int,
+                                         _P]),
+    "ng_kreduce_timestep": (ctypes.c_int, [_P, _G, ctypes.c_int, ng_herm, ng_herm, _P, _P]),
+    "ng_shard_plan": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _G, ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_size_t)]),
+    "ng_kreduce_partial": (ctypes.c_int, [_P, _G, ctypes.c_int, _P, ng_herm, _P, ctypes.c_int, _P]),
+    "ng_kreduce_combine": (ctypes.c_int, [_P, _G, ctypes.c_int, ng_herm, _P, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_int, _P]),
+    "ng_run_2b_host": (ctypes.c_int, [_P, _G, ng_herm, ng_herm, ng_herm, ng_func, ng_func, ng_func, _P, _P, _P,
+                                      ctypes.POINTER(ng_run_params), ctypes.POINTER(ng_shard),
+                                      ctypes.POINTER(ctypes.c_int), _P]),
+    "ng_run_2b_sharded": (ctypes.c_int, [_P, _G, ng_herm, ng_herm, ng_herm, ng_func, ng_func, ng_func,
+                                         ctypes.POINTER(ng_run_params), ctypes.POINTER(ng_shard),
+                                         ctypes.POINTER(ctypes.c_int), _P]),
     "ng_sigma2b_timestep": (ctypes.c_int, [_P, _G, ctypes.c_int, ng_herm, ng_herm, ng_func, _P]),
     "ng_hartree_timestep": (ctypes.c_int, [_P, _G, ctypes.c_int, ng_func, ng_func, ng_herm, ng_func,
                                            ctypes.c_double, _P]),
@@ -85,8 +108,11 @@ SIGNATURES = {
     "ng_batch_setup": (ctypes.c_int, [_P, _P, _P]),
     "ng_batch_step": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, _P]),
     "ng_batch_solve": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int), _P]),
+    "ng_convolution_timestep": (ctypes.c_int, [_P, _G, ctypes.c_int, ng_herm, ng_herm, ng_herm, ng_func, ng_herm,
+                                               ng_herm, _P]),
     "ng_observables": (ctypes.c_int, [_P, _G, ctypes.c_int, ng_herm, ng_herm, ng_func, ng_func, _P, _P]),
     "ng_dyson_start_noalloc": (ctypes.c_int, [_G, ng_herm, ng_herm, ng_func, _P]),
+    "ng_fp64_probe": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), _P]),
     "ng_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "ng_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
     "ng_adjoint_2b": (ctypes.c_int, [_P, _G, ng_herm, ng_herm, ng_herm, ng_func, ng_func, ng_func,
@@ -219,6 +245,28 @@ def dyson_start_noalloc(grid, G, S, eps, stream=None):
     return lib.ng_dyson_start_noalloc(ctypes.byref(grid.c()), G.c(), S.c(), eps.c(), _stream(stream))
 
 
+def shard_plan(nk, rank, nranks, grid=None):
+    """ng_shard_plan: (k_begin, k_count, send_bytes) of rank `rank` (send_bytes 0 without grid).
+    Host only."""
+    lib = load_library()
+    b, c, nb = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
+    st = lib.ng_shard_plan(nk, rank, nranks, ctypes.byref(grid.c()) if grid is not None else None, ctypes.byref(b),
+                           ctypes.byref(c), ctypes.byref(nb) if grid is not None else None)
+    if st != NG_OK:
+        raise NgError(st, f"ng_shard_plan(nk={nk}, rank={rank}, nranks={nranks}) failed")
+    return b.value, c.value, nb.value
+
+
+def fp64_probe(stream=None):
+    """ng_fp64_probe on the current device: {dfma_tflops, dmma_tflops, sms}."""
+    lib = load_library()
+    out = (ctypes.c_double * 3)()
+    st = lib.ng_fp64_probe(out, _stream(stream))
+    if st != NG_OK:
+        raise NgError(st, "ng_fp64_probe failed")
+    return {"dfma_tflops": out[0], "dmma_tflops": out[1], "sms": int(out[2])}
+
+
 def _stream(stream):
     if stream is None:
         return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
@@ -304,12 +352,31 @@ class Context:
     def dyson_start(self, grid, G, S, eps, stream=None):
         self._chk(self.lib.ng_dyson_start(self.h, ctypes.byref(grid.c()), G.c(), S.c(), eps.c(), _stream(stream)))
 
-    def dyson_timestep(self, grid, tstp, G, S, eps, precision=NG_FP64, stream=None):
+    def dyson_timestep(self, grid, tstp, G, S, eps, precision=NG_FP64, schedule=NG_MIXED, stream=None):
         self._chk(self.lib.ng_dyson_timestep(self.h, ctypes.byref(grid.c()), tstp, G.c(), S.c(), eps.c(),
-                                             precision, _stream(stream)))
+                                             precision, schedule, _stream(stream)))
 
-    def kreduce_timestep(self, grid, tstp, Gloc, Gk, stream=None):
-        self._chk(self.lib.ng_kreduce_timestep(self.h, ctypes.byref(grid.c()), tstp, Gloc.c(), Gk.c(), _stream(stream)))
+    def convolution_timestep(self, grid, tstp, C, A, Acc, f, B, Bcc, stream=None):
+        """Slice tstp (-1: Matsubara) of C = A * f * B; f = None is the identity."""
+        fc = f.c() if f is not None else ng_func(None, 1)
+        self._chk(self.lib.ng_convolution_timestep(self.h, ctypes.byref(grid.c()), tstp, C.c(), A.c(), Acc.c(), fc,
+                                                   B.c(), Bcc.c(), _stream(stream)))
+
+    def kreduce_timestep(self, grid, tstp, Gloc, Gk, wk=None, stream=None):
+        """wk: optional device float64 tensor of nbatch k-point weights (default 1/nbatch)."""
+        w = ctypes.c_void_p(wk.data_ptr()) if wk is not None else None
+        self._chk(self.lib.ng_kreduce_timestep(self.h, ctypes.byref(grid.c()), tstp, Gloc.c(), Gk.c(), w,
+                                               _stream(stream)))
+
+    def kreduce_partial(self, grid, tstp, partial, Gk, k_begin, wk=None, stream=None):
+        w = ctypes.c_void_p(wk.data_ptr()) if wk is not None else None
+        self._chk(self.lib.ng_kreduce_partial(self.h, ctypes.byref(grid.c()), tstp, ctypes.c_void_p(partial.data_ptr()),
+                                              Gk.c(), w, k_begin, _stream(stream)))
+
+    def kreduce_combine(self, grid, tstp, Gloc, gathered, nk, nranks, weighted=False, stream=None):
+        self._chk(self.lib.ng_kreduce_combine(self.h, ctypes.byref(grid.c()), tstp, Gloc.c(),
+                                              ctypes.c_void_p(gathered.data_ptr()), nk, nranks, 1 if weighted else 0,
+                                              _stream(stream)))
 
     def sigma2b_timestep(self, grid, tstp, S, Gloc, U, stream=None):
         self._chk(self.lib.ng_sigma2b_timestep(self.h, ctypes.byref(grid.c()), tstp, S.c(), Gloc.c(), U.c(),
@@ -339,6 +406,47 @@ class Context:
         iters = (ctypes.c_int * 2)()
         st = self.lib.ng_run_2b(self.h, ctypes.byref(grid.c()), G.c(), Gloc.c(), S.c(), eps0.c(), eps_mf.c(), U.c(),
                                 ctypes.byref(p), iters, _stream(stream))
+        if not (allow_noconv and st == NG_ENOCONV):
+            self._chk(st)
+        return list(iters)
+
+    def run_2b_host(self, grid, G, Gloc, S, eps0, eps_mf, U, eps0_host, U_host, gdiag_host, corrector=3,
+                    mats_tol=1e-12, mats_maxiter=200, boot_tol=1e-12, boot_maxiter=200, nbar=0.5, n_from=None,
+                    n_to=None, do_setup=True, stream=None, allow_noconv=False, precision=NG_FP64, exchange=None):
+        """ng_run_2b_host: eps0_host [nt+2, nf, nf, nbatch] and U_host [nt+2] complex128 CPU tensors
+        (pinned for asynchronous copies), gdiag_host [nt+1, nf, nf] complex128 CPU tensor
+        receiving Gloc^<(t_n, t_n).  exchange: this rank's shard.DistExchange (None: one GPU)."""
+        for t in (eps0_host, U_host, gdiag_host):
+            assert t.device.type == "cpu" and t.dtype == torch.complex128 and t.is_contiguous()
+        p = ng_run_params(corrector, mats_tol, mats_maxiter, boot_tol, boot_maxiter, nbar,
+                          grid.korder + 1 if n_from is None else n_from,
+                          grid.nt if n_to is None else n_to, 1 if do_setup else 0, precision)
+        iters = (ctypes.c_int * 2)()
+        st = self.lib.ng_run_2b_host(self.h, ctypes.byref(grid.c()), G.c(), Gloc.c(), S.c(), eps0.c(), eps_mf.c(),
+                                     U.c(), ctypes.c_void_p(eps0_host.data_ptr()), ctypes.c_void_p(U_host.data_ptr()),
+                                     ctypes.c_void_p(gdiag_host.data_ptr()), ctypes.byref(p),
+                                     ctypes.byref(exchange.c()) if exchange is not None else None, iters,
+                                     _stream(stream))
+        if exchange is not None and exchange.error is not None:
+            raise exchange.error
+        if not (allow_noconv and st == NG_ENOCONV):
+            self._chk(st)
+        return list(iters)
+
+    def run_2b_sharded(self, grid, G, Gloc, S, eps0, eps_mf, U, exchange, corrector=3, mats_tol=1e-12,
+                       mats_maxiter=200, boot_tol=1e-12, boot_maxiter=200, nbar=0.5, n_from=None, n_to=None,
+                       do_setup=True, stream=None, allow_noconv=False, precision=NG_FP64):
+        """ng_run_2b_sharded: grid, G, eps0, eps_mf hold this rank's k-points; `exchange` supplies
+        nk, rank, nranks, the send/recv device tensors and the allgather callback (see shard.py)."""
+        p = ng_run_params(corrector, mats_tol, mats_maxiter, boot_tol, boot_maxiter, nbar,
+                          grid.korder + 1 if n_from is None else n_from,
+                          grid.nt if n_to is None else n_to, 1 if do_setup else 0, precision)
+        sh = exchange.c()
+        iters = (ctypes.c_int * 2)()
+        st = self.lib.ng_run_2b_sharded(self.h, ctypes.byref(grid.c()), G.c(), Gloc.c(), S.c(), eps0.c(), eps_mf.c(),
+                                        U.c(), ctypes.byref(p), ctypes.byref(sh), iters, _stream(stream))
+        if exchange.error is not None:
+            raise exchange.error
         if not (allow_noconv and st == NG_ENOCONV):
             self._chk(st)
         return list(iters)

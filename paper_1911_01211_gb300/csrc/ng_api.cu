@@ -12,6 +12,7 @@
 #include "ng_obs.cuh"
 #include "ng_ubatch.cuh"
 #include "ng_stepdf.cuh"
+#include "ng_conv_launch.h"
 #include "ng_adjoint_types.h"
 #include <cmath>
 
@@ -79,13 +80,15 @@ namespace {
 bool g_weights_loaded[64] = {false};
 
 // Integration weights of every order into constant memory of device `dev` (current): this
-// file's c_W and the adjoint translation unit's own copy, together, once per device.
+// file's c_W and the own copies of the adjoint and convolution translation units, together,
+// once per device.
 ng_status load_weights_once(int dev) {
     if (dev < 0 || dev >= 64) return NG_EUNSUPPORTED;
     if (g_weights_loaded[dev]) return NG_OK;
     NgWeights all[NG_KMAX];
     for (int k = 1; k <= NG_KMAX; ++k) ng_make_weights(k, &all[k - 1]);
-    if (cudaMemcpyToSymbol(c_W, all, sizeof(all)) != cudaSuccess || adj_load_weights(all) != cudaSuccess) {
+    if (cudaMemcpyToSymbol(c_W, all, sizeof(all)) != cudaSuccess || adj_load_weights(all) != cudaSuccess ||
+        conv_load_weights(all) != cudaSuccess) {
         cudaGetLastError();
         return NG_ECUDA;
     }
@@ -462,11 +465,76 @@ ng_status launch_free(ng_ctx* c, const Grid& g, const HermV& G, const cplx* eps_
     return check_launch(c, "k_free_gf");
 }
 
-ng_status do_kreduce(ng_ctx* c, const Grid& g, int tstp, const HermV& L, const HermV& Gk, cudaStream_t s) {
+ng_status do_kreduce(ng_ctx* c, const Grid& g, int tstp, const HermV& L, const HermV& Gk, cudaStream_t s,
+                     const double* wk = nullptr) {
     const int cnt = tstp < 0 ? g.ntau + 1 : 2 * (tstp + 1) + g.ntau + 1;
     const int64_t warps = (int64_t)cnt * g.nf * g.nf;
-    k_kreduce<<<nblocks(warps * 32, 256), 256, 0, s>>>(g, tstp, L, Gk);
+    k_kreduce<<<nblocks(warps * 32, 256), 256, 0, s>>>(g, tstp, L, Gk, wk);
     return check_launch(c, "k_kreduce");
+}
+
+// ---- k-point sharding over ranks -----------------------------------------------------------
+// Rank r owns the whole blocks [floor(r B / P), floor((r+1) B / P)) of the B = ceil(nk / 32)
+// blocks of NG_KBLK consecutive k indices.
+void shard_map(int nk, int nranks, BlkMap* m) {
+    const int64_t B = (nk + NG_KBLK - 1) / NG_KBLK;
+    for (int r = 0; r <= nranks; ++r) m->first[r] = (int)(B * r / nranks);
+}
+int shard_maxb(const BlkMap& m, int nranks) {
+    int mb = 0;
+    for (int r = 0; r < nranks; ++r) mb = std::max(mb, m.first[r + 1] - m.first[r]);
+    return mb;
+}
+size_t shard_send_bytes(const Grid& g, int maxb) {
+    const size_t cnt_max = (size_t)2 * (g.nt + 1) + g.ntau + 1;
+    return std::max<size_t>(sizeof(double), (size_t)maxb * cnt_max * g.nf * g.nf * sizeof(cplx));
+}
+
+// resolved shard of one rank for the driver
+struct ShardRt {
+    const ng_shard* sh;
+    BlkMap map;
+    int maxb;
+    int kb0;  // global k index of local problem 0
+};
+
+ng_status check_shard(ng_ctx* c, const Grid& g, const ng_shard* sh, ShardRt* rt) {
+    if (sh->nranks < 1 || sh->nranks > NG_MAXRANKS) return fail(c, NG_EINVAL, "nranks = %d must be in 1..%d", sh->nranks, NG_MAXRANKS);
+    if (sh->rank < 0 || sh->rank >= sh->nranks) return fail(c, NG_EINVAL, "rank %d out of 0..%d", sh->rank, sh->nranks - 1);
+    if ((sh->nk + NG_KBLK - 1) / NG_KBLK < sh->nranks)
+        return fail(c, NG_EINVAL, "nk = %d gives fewer blocks of %d than ranks (%d)", sh->nk, NG_KBLK, sh->nranks);
+    rt->sh = sh;
+    shard_map(sh->nk, sh->nranks, &rt->map);
+    rt->maxb = shard_maxb(rt->map, sh->nranks);
+    rt->kb0 = rt->map.first[sh->rank] * NG_KBLK;
+    const int count = std::min(sh->nk, rt->map.first[sh->rank + 1] * NG_KBLK) - rt->kb0;
+    if (g.nb != count) return fail(c, NG_EINVAL, "grid.nbatch = %d, but rank %d owns %d k-points", g.nb, sh->rank, count);
+    if (!sh->exchange) return fail(c, NG_EINVAL, "shard exchange callback is NULL");
+    if (!sh->send || !sh->recv || !aligned16(sh->send) || !aligned16(sh->recv))
+        return fail(c, NG_EINVAL, "shard send/recv buffers are NULL or not 16-byte aligned");
+    if (sh->send_bytes < shard_send_bytes(g, rt->maxb))
+        return fail(c, NG_EINVAL, "shard send_bytes %zu < %zu needed", sh->send_bytes, shard_send_bytes(g, rt->maxb));
+    return NG_OK;
+}
+
+// Gloc slice tstp: on one GPU the single-kernel fixed-order reduction; over ranks, the block sums
+// of the local k-points, the exchange of all ranks' block sums, and their sum in block order.
+ng_status do_kreduce_rt(ng_ctx* c, const Grid& g, int tstp, const HermV& L, const HermV& Gk, cudaStream_t s,
+                        const ShardRt* rt) {
+    if (!rt) return do_kreduce(c, g, tstp, L, Gk, s);
+    const ng_shard* sh = rt->sh;
+    const int cnt = tstp < 0 ? g.ntau + 1 : 2 * (tstp + 1) + g.ntau + 1;
+    const int dd = g.nf * g.nf;
+    const int nbl = rt->map.first[sh->rank + 1] - rt->map.first[sh->rank];
+    const int64_t warps = (int64_t)nbl * cnt * dd;
+    k_kreduce_partial<<<nblocks(warps * 32, 256), 256, 0, s>>>(g, tstp, Gk, nullptr, rt->kb0, (cplx*)sh->send);
+    ng_status st = check_launch(c, "k_kreduce_partial");
+    if (st) return st;
+    if (sh->exchange(sh->user, (size_t)rt->maxb * cnt * dd * sizeof(cplx)) != 0)
+        return fail(c, NG_ECOMM, "the exchange of the k-block sums failed (slice %d)", tstp);
+    k_kreduce_combine<<<nblocks((int64_t)cnt * dd, 128), 128, 0, s>>>(g, tstp, L, (const cplx*)sh->recv, sh->nk,
+                                                                      sh->nranks, rt->maxb, rt->map, 0);
+    return check_launch(c, "k_kreduce_combine");
 }
 ng_status do_sigma(ng_ctx* c, const Grid& g, int tstp, const HermV& S, const HermV& L, const FuncV& U, cudaStream_t s) {
     const int cnt = tstp < 0 ? g.ntau + 1 : 2 * (tstp + 1) + g.ntau + 1;
@@ -583,6 +651,21 @@ ng_status utimestep_uniform(ng_ctx* c, const Grid& g, int n, const HermV& G, con
     std::vector<int> active(g.nb);
     for (int kb = 0; kb < g.nb; ++kb) active[kb] = kb;
     return ustep(c, d_probs, info, active, n, 128, s);
+}
+
+// serial schedule: the left-mixing row by the bulk kernel (its other tasks empty), then the whole
+// retarded row and lesser column by implementation (A), one block per problem
+template <int D>
+ng_status launch_timestep_serial(ng_ctx* c, const Grid& g, int n, const HermV& G, const HermV& S, const FuncV& eps,
+                                 cudaStream_t s) {
+    const int thr = 128;
+    const int b_tv = (int)nblocks((int64_t)g.nb * (g.ntau + 1), thr);
+    ng_status st = launch_minv<D>(c, g, n, S, eps, s);
+    if (st) return st;
+    k_step_bulk<D><<<b_tv, thr, 0, s>>>(g, n, G, S, eps, (const cplx*)c->ws_minv, 0, b_tv, 0, c->d_status);
+    if ((st = check_launch(c, "k_step_bulk"))) return st;
+    k_step_serial<D><<<g.nb, NG_BND_THREADS, 0, s>>>(g, n, G, S, eps, c->d_status);
+    return check_launch(c, "k_step_serial");
 }
 
 ng_status do_timestep(ng_ctx* c, const Grid& g, int n, const HermV& G, const HermV& S, const FuncV& eps, cudaStream_t s,
@@ -790,7 +873,7 @@ ng_status ng_dyson_start(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm S, n
 }
 
 ng_status ng_dyson_timestep(ng_ctx* c, const ng_grid* grid, int tstp, ng_herm G, ng_herm S, ng_func eps, int precision,
-                            void* stream) {
+                            int schedule, void* stream) {
     Grid g;
     HermV Gv, Sv;
     FuncV ev;
@@ -802,7 +885,40 @@ ng_status ng_dyson_timestep(ng_ctx* c, const ng_grid* grid, int tstp, ng_herm G,
     if ((st = check_herm(c, g, G, "G", true, &Gv, g.nb))) return st;
     if ((st = check_herm(c, g, S, "Sigma", true, &Sv, 0))) return st;
     if ((st = check_func(c, g, eps, "eps", &ev))) return st;
+    if (schedule == NG_SERIAL) {
+        if (precision != NG_FP64) return fail(c, NG_EUNSUPPORTED, "the serial schedule runs in NG_FP64 only");
+        if (g.nf > 2) return fail(c, NG_EUNSUPPORTED, "the serial schedule supports nf <= 2");
+        return g.nf == 1 ? launch_timestep_serial<1>(c, g, tstp, Gv, Sv, ev, (cudaStream_t)stream)
+                         : launch_timestep_serial<2>(c, g, tstp, Gv, Sv, ev, (cudaStream_t)stream);
+    }
+    if (schedule != NG_MIXED) return fail(c, NG_EINVAL, "unknown schedule %d", schedule);
     return do_timestep(c, g, tstp, Gv, Sv, ev, (cudaStream_t)stream, precision);
+}
+
+ng_status ng_convolution_timestep(ng_ctx* c, const ng_grid* grid, int tstp, ng_herm C, ng_herm A, ng_herm Acc,
+                                  ng_func f, ng_herm B, ng_herm Bcc, void* stream) {
+    Grid g;
+    HermV Cv, Av, Accv, Bv, Bccv;
+    ng_status st;
+    if ((st = check_grid(c, grid, &g))) return st;
+    if (tstp < -1 || tstp > g.nt) return fail(c, NG_EINVAL, "tstp = %d must be in -1..nt = %d", tstp, g.nt);
+    const bool rt = tstp >= 0;
+    if ((st = check_herm(c, g, C, "C", rt, &Cv, 0))) return st;
+    if ((st = check_herm(c, g, A, "A", rt, &Av, 0))) return st;
+    if ((st = check_herm(c, g, Acc, "Acc", rt, &Accv, 0))) return st;
+    if ((st = check_herm(c, g, B, "B", rt, &Bv, 0))) return st;
+    if ((st = check_herm(c, g, Bcc, "Bcc", rt, &Bccv, 0))) return st;
+    FuncV fv{nullptr, 1};
+    if (f.val && (st = check_func(c, g, f, "f", &fv))) return st;
+    const int nbe = C.ldk;
+    if (nbe == 1 && g.nb > 1 &&
+        (A.ldk != 1 || Acc.ldk != 1 || B.ldk != 1 || Bcc.ldk != 1 || (f.val && f.ldk != 1)))
+        return fail(c, NG_EINVAL, "C.ldk = 1 needs every input shared (ldk = 1)");
+    if (conv_launch(g, tstp, Cv, Av, Accv, fv, Bv, Bccv, nbe, c->d_status, (cudaStream_t)stream) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, NG_ECUDA, "launch of k_conv_slice failed");
+    }
+    return NG_OK;
 }
 
 ng_status ng_observables(ng_ctx* c, const ng_grid* grid, int tstp, ng_herm G, ng_herm S, ng_func eps0, ng_func epsmf,
@@ -841,7 +957,8 @@ ng_status ng_precision_reset(ng_ctx* c) {
     return NG_OK;
 }
 
-ng_status ng_kreduce_timestep(ng_ctx* c, const ng_grid* grid, int tstp, ng_herm Gloc, ng_herm Gk, void* stream) {
+ng_status ng_kreduce_timestep(ng_ctx* c, const ng_grid* grid, int tstp, ng_herm Gloc, ng_herm Gk, const double* wk,
+                              void* stream) {
     Grid g;
     HermV L, K;
     ng_status st;
@@ -850,7 +967,66 @@ ng_status ng_kreduce_timestep(ng_ctx* c, const ng_grid* grid, int tstp, ng_herm 
     if (Gloc.ldk != 1) return fail(c, NG_EINVAL, "Gloc.ldk must be 1");
     if ((st = check_herm(c, g, Gloc, "Gloc", tstp >= 0, &L, 1))) return st;
     if ((st = check_herm(c, g, Gk, "Gk", tstp >= 0, &K, g.nb))) return st;
-    return do_kreduce(c, g, tstp, L, K, (cudaStream_t)stream);
+    if (wk && ((uintptr_t)wk & 7u)) return fail(c, NG_EINVAL, "wk is not 8-byte aligned");
+    return do_kreduce(c, g, tstp, L, K, (cudaStream_t)stream, wk);
+}
+
+ng_status ng_shard_plan(int nk, int rank, int nranks, const ng_grid* grid, int* k_begin, int* k_count,
+                        size_t* send_bytes) {
+    if (nk < 1 || nranks < 1 || nranks > NG_MAXRANKS || rank < 0 || rank >= nranks) return NG_EINVAL;
+    if ((nk + NG_KBLK - 1) / NG_KBLK < nranks) return NG_EINVAL;
+    BlkMap m;
+    shard_map(nk, nranks, &m);
+    const int b = m.first[rank] * NG_KBLK, e = std::min(nk, m.first[rank + 1] * NG_KBLK);
+    if (k_begin) *k_begin = b;
+    if (k_count) *k_count = e - b;
+    if (send_bytes) {
+        if (!grid) return NG_EINVAL;
+        Grid g{};
+        g.nt = grid->nt;
+        g.ntau = grid->ntau;
+        g.nf = grid->nf;
+        *send_bytes = shard_send_bytes(g, shard_maxb(m, nranks));
+    }
+    return NG_OK;
+}
+
+ng_status ng_kreduce_partial(ng_ctx* c, const ng_grid* grid, int tstp, void* partial, ng_herm Gk, const double* wk,
+                             int k_begin, void* stream) {
+    Grid g;
+    HermV K;
+    ng_status st;
+    if ((st = check_grid(c, grid, &g))) return st;
+    if (tstp < -1 || tstp > g.nt) return fail(c, NG_EINVAL, "tstp = %d out of range", tstp);
+    if ((st = check_herm(c, g, Gk, "Gk", tstp >= 0, &K, g.nb))) return st;
+    if (k_begin < 0 || k_begin % NG_KBLK) return fail(c, NG_EINVAL, "k_begin = %d must be a multiple of %d", k_begin, NG_KBLK);
+    if (!partial || !aligned16(partial)) return fail(c, NG_EINVAL, "partial is NULL or not 16-byte aligned");
+    if (wk && ((uintptr_t)wk & 7u)) return fail(c, NG_EINVAL, "wk is not 8-byte aligned");
+    const int cnt = tstp < 0 ? g.ntau + 1 : 2 * (tstp + 1) + g.ntau + 1;
+    const int64_t warps = (int64_t)((g.nb + NG_KBLK - 1) / NG_KBLK) * cnt * g.nf * g.nf;
+    k_kreduce_partial<<<nblocks(warps * 32, 256), 256, 0, (cudaStream_t)stream>>>(g, tstp, K, wk, k_begin,
+                                                                                  (cplx*)partial);
+    return check_launch(c, "k_kreduce_partial");
+}
+
+ng_status ng_kreduce_combine(ng_ctx* c, const ng_grid* grid, int tstp, ng_herm Gloc, const void* gathered, int nk,
+                             int nranks, int weighted, void* stream) {
+    Grid g;
+    HermV L;
+    ng_status st;
+    if ((st = check_grid(c, grid, &g))) return st;
+    if (tstp < -1 || tstp > g.nt) return fail(c, NG_EINVAL, "tstp = %d out of range", tstp);
+    if (Gloc.ldk != 1) return fail(c, NG_EINVAL, "Gloc.ldk must be 1");
+    if ((st = check_herm(c, g, Gloc, "Gloc", tstp >= 0, &L, 0))) return st;
+    if (nk < 1 || nranks < 1 || nranks > NG_MAXRANKS || (nk + NG_KBLK - 1) / NG_KBLK < nranks)
+        return fail(c, NG_EINVAL, "nk = %d, nranks = %d invalid", nk, nranks);
+    if (!gathered || !aligned16(gathered)) return fail(c, NG_EINVAL, "gathered is NULL or not 16-byte aligned");
+    BlkMap m;
+    shard_map(nk, nranks, &m);
+    const int cnt = tstp < 0 ? g.ntau + 1 : 2 * (tstp + 1) + g.ntau + 1;
+    k_kreduce_combine<<<nblocks((int64_t)cnt * g.nf * g.nf, 128), 128, 0, (cudaStream_t)stream>>>(
+        g, tstp, L, (const cplx*)gathered, nk, nranks, shard_maxb(m, nranks), m, weighted ? 1 : 0);
+    return check_launch(c, "k_kreduce_combine");
 }
 
 ng_status ng_sigma2b_timestep(ng_ctx* c, const ng_grid* grid, int tstp, ng_herm S, ng_herm Gloc, ng_func U, void* stream) {
@@ -925,8 +1101,18 @@ ng_status ng_solve_fixed(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm S, n
     return NG_OK;
 }
 
-ng_status ng_run_2b(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm Gloc, ng_herm S, ng_func eps0, ng_func epsmf,
-                    ng_func U, const ng_run_params* p, int* iters_out, void* stream) {
+// host buffers of ng_run_2b_host (all NULL otherwise)
+struct HostIO {
+    const cplx* eps0;   // [nt+2][nf][nf][nbatch]
+    const cplx* U;      // [nt+2]
+    cplx* gdiag;        // [nt+1][nf][nf]: Gloc^<(t_n, t_n)
+};
+
+// the second-Born driver; sh = NULL: all k-points on this GPU, else this rank's share;
+// io = NULL: inputs and outputs stay on the device
+static ng_status run_2b_impl(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm Gloc, ng_herm S, ng_func eps0,
+                             ng_func epsmf, ng_func U, const ng_run_params* p, const ng_shard* sh, const HostIO* io,
+                             int* iters_out, void* stream) {
     Grid g;
     HermV Gv, Lv, Sv;
     FuncV e0, mf, uv;
@@ -947,8 +1133,49 @@ ng_status ng_run_2b(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm Gloc, ng_
         return fail(c, NG_EINVAL, "unknown precision %d", p->precision);
     if (p->n_to > g.nt || (p->n_to >= p->n_from && p->n_from <= g.k))
         return fail(c, NG_EINVAL, "stepping range %d..%d invalid (k = %d, nt = %d)", p->n_from, p->n_to, g.k, g.nt);
+    ShardRt rt;
+    const ShardRt* rtp = nullptr;
+    if (sh) {
+        if ((st = check_shard(c, g, sh, &rt))) return st;
+        rtp = &rt;
+    }
+    // problems summed by the convergence distances (all ranks')
+    const double nk_all = sh ? (double)sh->nk : (double)G.ldk;
     cudaStream_t s = (cudaStream_t)stream;
+    // distance accumulated in c->d_scalar, summed over the ranks in rank order
+    auto read_distance = [&](double* err) -> ng_status {
+        if (!rtp) {
+            CUDA_TRY(c, cudaMemcpyAsync(err, c->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, s));
+            CUDA_TRY(c, cudaStreamSynchronize(s));
+            return NG_OK;
+        }
+        double per[NG_MAXRANKS];
+        CUDA_TRY(c, cudaMemcpyAsync(sh->send, c->d_scalar, sizeof(double), cudaMemcpyDeviceToDevice, s));
+        if (sh->exchange(sh->user, sizeof(double)) != 0) return fail(c, NG_ECOMM, "the exchange of distances failed");
+        CUDA_TRY(c, cudaMemcpyAsync(per, sh->recv, sizeof(double) * sh->nranks, cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(c, cudaStreamSynchronize(s));
+        *err = 0.0;
+        for (int r = 0; r < sh->nranks; ++r) *err += per[r];
+        return NG_OK;
+    };
     const int k = g.k, dd = g.nf * g.nf, T = g.ntau;
+    // host I/O: eps0 slices (index n+1) and the whole U in, Gloc^<(t_n, t_n) out
+    const size_t eps_slice = sizeof(cplx) * dd * (size_t)eps0.ldk;
+    auto eps_in = [&](int from, int to) -> ng_status {   // slices from..to (index from+1..to+1)
+        if (!io || to < from) return NG_OK;
+        CUDA_TRY(c, cudaMemcpyAsync((char*)eps0.val + (size_t)(from + 1) * eps_slice,
+                                    (const char*)io->eps0 + (size_t)(from + 1) * eps_slice,
+                                    (size_t)(to - from + 1) * eps_slice, cudaMemcpyHostToDevice, s));
+        return NG_OK;
+    };
+    auto gdiag_out = [&](int from, int to) -> ng_status {
+        if (!io) return NG_OK;
+        for (int n = from; n <= to; ++n)
+            CUDA_TRY(c, cudaMemcpyAsync(io->gdiag + (size_t)n * dd, Lv.les.p + (size_t)(tri(n) + n) * dd,
+                                        sizeof(cplx) * dd, cudaMemcpyDeviceToHost, s));
+        return NG_OK;
+    };
+    if (io) CUDA_TRY(c, cudaMemcpyAsync(U.val, io->U, sizeof(cplx) * (size_t)(g.nt + 2), cudaMemcpyHostToDevice, s));
     int mats_it = 0, boot_it = 0;
     bool noconv = false;
     if (p->do_setup) {
@@ -965,15 +1192,16 @@ ng_status ng_run_2b(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm Gloc, ng_
         Pv.tv = Comp{Pv.les.p + el_tri * dd * G.ldk, G.ldk, dd};
         const size_t fslice = sizeof(cplx) * dd * (size_t)epsmf.ldk;
         // ---- Matsubara loop ----
+        if ((st = eps_in(-1, k))) return st;
         CUDA_TRY(c, cudaMemcpyAsync(epsmf.val, eps0.val, fslice, cudaMemcpyDeviceToDevice, s));
         CUDA_TRY(c, cudaMemsetAsync(S.mat, 0, sizeof(cplx) * dd * el_mat, s));
         if ((st = do_mat(c, g, Gv, Sv, mf, s))) return st;
         double err = 0.0;
         // stopping floors: a summed distance cannot fall below round-off, about 1e-15 per element
-        const double nel_mat = (double)G.ldk * el_mat * dd;
+        const double nel_mat = nk_all * el_mat * dd;
         const double mats_stop = std::max(p->mats_tol, 1e-15 * nel_mat);
         for (mats_it = 0; mats_it < p->mats_maxiter; ++mats_it) {
-            if ((st = do_kreduce(c, g, -1, Lv, Gv, s))) return st;
+            if ((st = do_kreduce_rt(c, g, -1, Lv, Gv, s, rtp))) return st;
             if ((st = do_hartree(c, g, -1, mf, e0, Lv, uv, p->nbar, s))) return st;
             if ((st = do_sigma(c, g, -1, Sv, Lv, uv, s))) return st;
             CUDA_TRY(c, cudaMemcpyAsync(Pv.mat.p, Gv.mat.p, per * el_mat, cudaMemcpyDeviceToDevice, s));
@@ -984,13 +1212,12 @@ ng_status ng_run_2b(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm Gloc, ng_
             if (!refined && (st = do_mat(c, g, Gv, Sv, mf, s))) return st;
             CUDA_TRY(c, cudaMemsetAsync(c->d_scalar, 0, sizeof(double), s));
             if ((st = do_distance(c, g, -1, Gv, Pv, c->d_scalar, s))) return st;
-            CUDA_TRY(c, cudaMemcpyAsync(&err, c->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, s));
-            CUDA_TRY(c, cudaStreamSynchronize(s));
+            if ((st = read_distance(&err))) return st;
             if (err < mats_stop) break;
         }
         if (mats_it == p->mats_maxiter) noconv = true;
         ++mats_it;
-        if ((st = do_kreduce(c, g, -1, Lv, Gv, s))) return st;
+        if ((st = do_kreduce_rt(c, g, -1, Lv, Gv, s, rtp))) return st;
         if ((st = do_hartree(c, g, -1, mf, e0, Lv, uv, p->nbar, s))) return st;
         if ((st = do_sigma(c, g, -1, Sv, Lv, uv, s))) return st;
         // ---- bootstrapping ----
@@ -1001,7 +1228,7 @@ ng_status ng_run_2b(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm Gloc, ng_
         if ((st = do_start(c, g, Gv, Sv, mf, s))) return st;
         for (boot_it = 0; boot_it < p->boot_maxiter; ++boot_it) {
             for (int n = 0; n <= k; ++n) {
-                if ((st = do_kreduce(c, g, n, Lv, Gv, s))) return st;
+                if ((st = do_kreduce_rt(c, g, n, Lv, Gv, s, rtp))) return st;
                 if ((st = do_hartree(c, g, n, mf, e0, Lv, uv, p->nbar, s))) return st;
                 if ((st = do_sigma(c, g, n, Sv, Lv, uv, s))) return st;
             }
@@ -1012,22 +1239,24 @@ ng_status ng_run_2b(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm Gloc, ng_
             CUDA_TRY(c, cudaMemsetAsync(c->d_scalar, 0, sizeof(double), s));
             for (int n = 0; n <= k; ++n)
                 if ((st = do_distance(c, g, n, Gv, Pv, c->d_scalar, s))) return st;
-            CUDA_TRY(c, cudaMemcpyAsync(&err, c->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, s));
-            CUDA_TRY(c, cudaStreamSynchronize(s));
-            if (err < std::max(p->boot_tol, 1e-15 * (double)G.ldk * dd * (2.0 * el_tri + el_tv)) && boot_it > 2) break;
+            if ((st = read_distance(&err))) return st;
+            if (err < std::max(p->boot_tol, 1e-15 * nk_all * dd * (2.0 * el_tri + el_tv)) && boot_it > 2) break;
         }
         if (boot_it == p->boot_maxiter) noconv = true;
         ++boot_it;
+        if ((st = gdiag_out(0, k))) return st;
     }
     // ---- time stepping: predictor, then fixed corrector iterations ----
     for (int n = p->n_from; n <= p->n_to; ++n) {
+        if ((st = eps_in(n, n))) return st;
         if ((st = do_extrap(c, g, n - 1, Gv, s))) return st;
         for (int it = 0; it < p->corrector; ++it) {
-            if ((st = do_kreduce(c, g, n, Lv, Gv, s))) return st;
+            if ((st = do_kreduce_rt(c, g, n, Lv, Gv, s, rtp))) return st;
             if ((st = do_hartree(c, g, n, mf, e0, Lv, uv, p->nbar, s))) return st;
             if ((st = do_sigma(c, g, n, Sv, Lv, uv, s))) return st;
             if ((st = do_timestep(c, g, n, Gv, Sv, mf, s, p->precision))) return st;
         }
+        if ((st = gdiag_out(n, n))) return st;
     }
     if (iters_out) {
         iters_out[0] = mats_it;
@@ -1035,6 +1264,29 @@ ng_status ng_run_2b(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm Gloc, ng_
     }
     if (noconv) return fail(c, NG_ENOCONV, "setup loop reached its iteration limit (mats %d, boot %d)", mats_it, boot_it);
     return NG_OK;
+}
+
+ng_status ng_run_2b(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm Gloc, ng_herm S, ng_func eps0, ng_func epsmf,
+                    ng_func U, const ng_run_params* p, int* iters_out, void* stream) {
+    return run_2b_impl(c, grid, G, Gloc, S, eps0, epsmf, U, p, nullptr, nullptr, iters_out, stream);
+}
+
+ng_status ng_run_2b_host(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm Gloc, ng_herm S, ng_func eps0,
+                         ng_func epsmf, ng_func U, const double* eps0_host, const double* U_host, double* gdiag_host,
+                         const ng_run_params* p, const ng_shard* shard, int* iters_out, void* stream) {
+    if (!c) return NG_EINVAL;
+    if (!eps0_host || !U_host || !gdiag_host) return fail(c, NG_EINVAL, "a host buffer is NULL");
+    if (eps0.ldk != (grid ? grid->nbatch : 0)) return fail(c, NG_EINVAL, "eps0.ldk must be nbatch");
+    const HostIO io{(const cplx*)eps0_host, (const cplx*)U_host, (cplx*)gdiag_host};
+    return run_2b_impl(c, grid, G, Gloc, S, eps0, epsmf, U, p, shard, &io, iters_out, stream);
+}
+
+ng_status ng_run_2b_sharded(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm Gloc, ng_herm S, ng_func eps0,
+                            ng_func epsmf, ng_func U, const ng_run_params* p, const ng_shard* shard, int* iters_out,
+                            void* stream) {
+    if (!c) return NG_EINVAL;
+    if (!shard) return fail(c, NG_EINVAL, "shard is NULL");
+    return run_2b_impl(c, grid, G, Gloc, S, eps0, epsmf, U, p, shard, nullptr, iters_out, stream);
 }
 
 }  // extern "C"

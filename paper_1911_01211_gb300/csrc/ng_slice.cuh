@@ -29,9 +29,42 @@ __device__ __forceinline__ const Comp& comp_of(const HermV& X, int c) {
     return c == 0 ? X.mat : (c == 1 ? X.ret : (c == 2 ? X.les : X.tv));
 }
 
-// Gloc = (1/nb) sum_kb Gk, one warp per (slice element, a, b); lanes take kb = lane, lane+32,
-// ... and the warp combines the 32 partial sums in a fixed butterfly order.
-__global__ void k_kreduce(Grid g, int tstp, HermV Gloc, HermV Gk) {
+// ---------------------------------------------------------------------------------------
+// k-point reduction Gloc = sum_kb w_kb Gk (w_kb = 1/nk without weights), in one fixed order
+// that does not depend on how the k-points are split over ranks: the k axis is cut into
+// blocks of NG_KBLK = 32 consecutive global k indices; a block's weighted values are added
+// across a warp in a fixed butterfly order; the block sums are added in block order starting
+// from zero; the 1/nk factor comes last.  A rank owning whole blocks produces the same block
+// sums (k_kreduce_partial), and adding everybody's block sums in block order
+// (k_kreduce_combine) gives bitwise the single-GPU result (k_kreduce).
+// ---------------------------------------------------------------------------------------
+#define NG_KBLK 32
+#define NG_MAXRANKS 64
+
+// first global block of every rank (first[nranks] = number of blocks), passed by value
+struct BlkMap {
+    int first[NG_MAXRANKS + 1];
+};
+
+// Block b of one slice element (kb = NG_KBLK b + lane global; local index kb - kb0 of the nbl
+// local problems, value stride 1); every lane returns the same block sum (each butterfly stage
+// adds a pair in both lanes, and floating-point addition commutes).
+__device__ __forceinline__ cplx kblock_sum(const cplx* p, const double* wk, int b, int kb0, int nbl, int lane) {
+    const int kl = b * NG_KBLK + lane - kb0;
+    cplx v = cz();
+    if (kl >= 0 && kl < nbl) {
+        v = p[kl];
+        if (wk) v = cscal(wk[kl], v);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    return v;
+}
+
+// Single GPU holding all nb problems: one warp per (slice element, a, b).
+__global__ void k_kreduce(Grid g, int tstp, HermV Gloc, HermV Gk, const double* wk) {
     const int dd = g.nf * g.nf;
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -42,13 +75,52 @@ __global__ void k_kreduce(Grid g, int tstp, HermV Gloc, HermV Gk) {
     const Comp& src = comp_of(Gk, s.comp);
     const Comp& dst = comp_of(Gloc, s.comp);
     const cplx* p = src.p + (s.e * dd + ab) * (int64_t)src.ldk;
+    const int nblk = (g.nb + NG_KBLK - 1) / NG_KBLK;
     cplx acc = cz();
-    for (int kb = lane; kb < g.nb; kb += 32) acc = cadd(acc, p[kb]);
-    for (int o = 16; o > 0; o >>= 1) {
-        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-    }
-    if (lane == 0) dst.p[(s.e * dd + ab) * (int64_t)dst.ldk] = cscal(1.0 / g.nb, acc);
+    for (int b = 0; b < nblk; ++b) acc = cadd(acc, kblock_sum(p, wk, b, 0, g.nb, lane));
+    if (lane == 0) dst.p[(s.e * dd + ab) * (int64_t)dst.ldk] = wk ? acc : cscal(1.0 / g.nb, acc);
+}
+
+// One rank's block sums: the local problems are global k indices kb0..kb0+nb-1 (kb0 a multiple
+// of NG_KBLK); out[(bl * cnt + i) * dd + ab] for the local blocks bl = 0..nblk_local-1.
+// One warp per (local block, slice element, a, b).
+__global__ void k_kreduce_partial(Grid g, int tstp, HermV Gk, const double* wk, int kb0, cplx* out) {
+    const int dd = g.nf * g.nf;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int cnt = slice_count(g, tstp);
+    const int nblk = (g.nb + NG_KBLK - 1) / NG_KBLK;
+    if (w >= (int64_t)nblk * cnt * dd) return;
+    const int ab = (int)(w % dd);
+    const int64_t r = w / dd;
+    const int i = (int)(r % cnt), bl = (int)(r / cnt);
+    const SliceEl s = slice_el(g, tstp, i);
+    const Comp& src = comp_of(Gk, s.comp);
+    const cplx* p = src.p + (s.e * dd + ab) * (int64_t)src.ldk;
+    const cplx v = kblock_sum(p, wk, kb0 / NG_KBLK + bl, kb0, g.nb, lane);
+    if (lane == 0) out[((int64_t)bl * cnt + i) * dd + ab] = v;
+}
+
+// Every rank's block sums gathered rank by rank, maxb block rows per rank (rows beyond a rank's
+// own blocks unused); global block b of rank r sits in row r maxb + (b - first block of r).
+// Adds them in global block order; one thread per (slice element, a, b).  nk: global problem
+// count, map.first[r]: first global block of rank r (r = 0..nranks).
+__global__ void k_kreduce_combine(Grid g, int tstp, HermV Gloc, const cplx* gathered, int nk, int nranks, int maxb,
+                                  BlkMap map, int weighted) {
+    const int dd = g.nf * g.nf;
+    const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int cnt = slice_count(g, tstp);
+    if (item >= (int64_t)cnt * dd) return;
+    const int ab = (int)(item % dd), i = (int)(item / dd);
+    const SliceEl s = slice_el(g, tstp, i);
+    const Comp& dst = comp_of(Gloc, s.comp);
+    cplx acc = cz();
+    for (int r = 0; r < nranks; ++r)
+        for (int b = map.first[r]; b < map.first[r + 1]; ++b) {
+            const int64_t row = (int64_t)r * maxb + (b - map.first[r]);
+            acc = cadd(acc, gathered[(row * cnt + i) * dd + ab]);
+        }
+    dst.p[(s.e * dd + ab) * (int64_t)dst.ldk] = weighted ? acc : cscal(1.0 / nk, acc);
 }
 
 // Second-Born slice (Eq. sigma_hubb_2b), orbital-elementwise:

@@ -1,4 +1,5 @@
-// Time-step kernels of libng: slice n > k of G for a batch of problems (mixed schedule).
+// Time-step kernels of libng: slice n > k of G for a batch of problems (mixed schedule, and
+// the serial one in k_step_serial).
 //
 // Sec. "Time stepping" of the NESSi paper:
 //   retarded row   : (B) single VIDE steps for columns m <= n-k-1 (Eq. MBCVSAMx_t with
@@ -303,6 +304,83 @@ __device__ Mat<D> block_sum(Mat<D> x, cplx* red /* blockDim.x * D*D */) {
 #define NG_BND_THREADS 128
 #define NG_MAXQ (2 * NG_KMAX + 1)
 
+// Conjugate VIDE start-up along row n (implementation (A), Eq. MBCVSAMx_cc_start): G^R(n, n) = -i
+// and G^R(n, n-l), l = 1..k, by one (k nf)^2 solve.  One thread; Ash, Bsh: shared scratch.
+template <int D>
+__device__ void ret_row_startup(const NgWeights& W, const Grid& g, int n, const HermV& G, const HermV& S,
+                                const FuncV& eps, int kb, cplx* Ash, cplx* Bsh, int* status) {
+    const int k = W.k;
+    // unknowns y_1..y_k (y_j = G^R(n, n-j)), y_0 = -i; sum_{l>=1} y_l Mh[l][j] = -y_0 Mh[0][j]
+    // with Mh[l][j] = D_{j,l}/h + delta_{lj} i(eps_{n-j} - mu) + h s_{j,l} i Sigma~^R(n-l, n-j).
+    // Transposed: sum_l Mh[l][j]^T y_l^T = -(y_0 Mh[0][j])^T.
+    const int N = k * D;
+    for (int j = 1; j <= k; ++j) {
+        for (int l = 0; l <= k; ++l) {
+            Mat<D> Mh = meye<D>(cr(W.D[j][l] / g.h));
+            Mh = madd<D>(Mh, mscal<D>(g.h * W.greg[j][l], mmuli<D>(gretx<D>(S, n - l, n - j, kb))));
+            if (l == j) {
+                Mat<D> e = ldf<D>(eps, n - j, kb);
+                for (int a = 0; a < D; ++a) e.v[a][a].x -= g.mu;
+                Mh = madd<D>(Mh, mmuli<D>(e));
+            }
+            if (l == 0) {
+                Mat<D> r = mmul<D>(meye<D>(make_double2(0.0, -1.0)), Mh);  // y_0 Mh[0][j]
+                for (int a = 0; a < D; ++a)
+                    for (int c = 0; c < D; ++c) Bsh[((j - 1) * D + a) * D + c] = cneg(r.v[c][a]);
+            } else {
+                for (int a = 0; a < D; ++a)
+                    for (int b = 0; b < D; ++b) Ash[((j - 1) * D + a) * N + (l - 1) * D + b] = Mh.v[b][a];
+            }
+        }
+    }
+    if (dense_solve(Ash, N, Bsh, D)) atomicOr(status, NGF_SINGULAR);
+    st<D>(G.ret, tri(n) + n, kb, meye<D>(make_double2(0.0, -1.0)));
+    for (int l = 1; l <= k; ++l) {
+        Mat<D> y;
+        for (int a = 0; a < D; ++a)
+            for (int c = 0; c < D; ++c) y.v[c][a] = Bsh[((l - 1) * D + a) * D + c];
+        if (!mfinite<D>(y)) atomicOr(status, NGF_NONFINITE);
+        st<D>(G.ret, tri(n) + n - l, kb, y);
+    }
+}
+
+// VIDE start-up of column n for the rows m = 1..k (Eq. vdiff_start): sum_l M_{m,l} y_l =
+// q_m - M_{m,0} y_0 with y_0 = G^<(0, n) and the sources q_m in qsrc[m-1].  One thread.
+template <int D>
+__device__ void les_col_startup(const NgWeights& W, const Grid& g, int n, const HermV& G, const HermV& S,
+                                const FuncV& eps, int kb, const cplx (*qsrc)[D][D], cplx* Ash, cplx* Bsh,
+                                int* status) {
+    const int k = W.k;
+    const int N = k * D;
+    Mat<D> y0 = ld<D>(G.les, tri(n) + 0, kb);
+    for (int m = 1; m <= k; ++m) {
+        Mat<D> e = ldf<D>(eps, m, kb);
+        for (int a = 0; a < D; ++a) e.v[a][a].x -= g.mu;
+        Mat<D> rhs;
+        for (int a = 0; a < D; ++a)
+            for (int b = 0; b < D; ++b) rhs.v[a][b] = qsrc[m - 1][a][b];
+        for (int l = 0; l <= k; ++l) {
+            Mat<D> M = meye<D>(cr(W.D[m][l] / g.h));
+            M = madd<D>(M, mscal<D>(g.h * W.greg[m][l], mmuli<D>(gretx<D>(S, m, l, kb))));
+            if (l == m) M = madd<D>(M, mmuli<D>(e));
+            if (l == 0) rhs = msub<D>(rhs, mmul<D>(M, y0));
+            else
+                for (int a = 0; a < D; ++a)
+                    for (int b = 0; b < D; ++b) Ash[((m - 1) * D + a) * N + (l - 1) * D + b] = M.v[a][b];
+        }
+        for (int a = 0; a < D; ++a)
+            for (int c = 0; c < D; ++c) Bsh[((m - 1) * D + a) * D + c] = rhs.v[a][c];
+    }
+    if (dense_solve(Ash, N, Bsh, D)) atomicOr(status, NGF_SINGULAR);
+    for (int m = 1; m <= k; ++m) {
+        Mat<D> y;
+        for (int a = 0; a < D; ++a)
+            for (int c = 0; c < D; ++c) y.v[a][c] = Bsh[((m - 1) * D + a) * D + c];
+        if (!mfinite<D>(y)) atomicOr(status, NGF_NONFINITE);
+        st<D>(G.les, tri(n) + m, kb, y);
+    }
+}
+
 // Per-problem boundary of step n: retarded start-up (A) for m = n-k..n, then the lesser
 // column's G^<(0,n) and serial (A) part.  One block per problem.
 template <int D>
@@ -320,38 +398,7 @@ __global__ void __launch_bounds__(NG_BND_THREADS) k_step_boundary(Grid g, int n,
 
     // ---- retarded: conjugate start-up along row n (implementation (A)) -------------
     if (t == 0) {
-        // unknowns y_1..y_k (y_j = G^R(n, n-j)), y_0 = -i; sum_{l>=1} y_l Mh[l][j] = -y_0 Mh[0][j]
-        // with Mh[l][j] = D_{j,l}/h + delta_{lj} i(eps_{n-j} - mu) + h s_{j,l} i Sigma~^R(n-l, n-j).
-        // Transposed: sum_l Mh[l][j]^T y_l^T = -(y_0 Mh[0][j])^T.
-        const int N = k * D;
-        for (int j = 1; j <= k; ++j) {
-            for (int l = 0; l <= k; ++l) {
-                Mat<D> Mh = meye<D>(cr(W.D[j][l] / g.h));
-                Mh = madd<D>(Mh, mscal<D>(g.h * W.greg[j][l], mmuli<D>(gretx<D>(S, n - l, n - j, kb))));
-                if (l == j) {
-                    Mat<D> e = ldf<D>(eps, n - j, kb);
-                    for (int a = 0; a < D; ++a) e.v[a][a].x -= g.mu;
-                    Mh = madd<D>(Mh, mmuli<D>(e));
-                }
-                if (l == 0) {
-                    Mat<D> r = mmul<D>(meye<D>(make_double2(0.0, -1.0)), Mh);  // y_0 Mh[0][j]
-                    for (int a = 0; a < D; ++a)
-                        for (int c = 0; c < D; ++c) Bsh[((j - 1) * D + a) * D + c] = cneg(r.v[c][a]);
-                } else {
-                    for (int a = 0; a < D; ++a)
-                        for (int b = 0; b < D; ++b) Ash[((j - 1) * D + a) * N + (l - 1) * D + b] = Mh.v[b][a];
-                }
-            }
-        }
-        if (dense_solve(Ash, N, Bsh, D)) atomicOr(status, NGF_SINGULAR);
-        st<D>(G.ret, tri(n) + n, kb, meye<D>(make_double2(0.0, -1.0)));
-        for (int l = 1; l <= k; ++l) {
-            Mat<D> y;
-            for (int a = 0; a < D; ++a)
-                for (int c = 0; c < D; ++c) y.v[c][a] = Bsh[((l - 1) * D + a) * D + c];
-            if (!mfinite<D>(y)) atomicOr(status, NGF_NONFINITE);
-            st<D>(G.ret, tri(n) + n - l, kb, y);
-        }
+        ret_row_startup<D>(W, g, n, G, S, eps, kb, Ash, Bsh, status);
         // G^<(0,n) = -[G^tv(n,0)]^dagger  (Eq. dyson_ini_les)
         st<D>(G.les, tri(n) + 0, kb, mscal<D>(-1.0, mdag<D>(gtv<D>(G, g, n, 0, kb))));
     }
@@ -381,35 +428,7 @@ __global__ void __launch_bounds__(NG_BND_THREADS) k_step_boundary(Grid g, int n,
     int sing = 0;
     int mstep = m0;
     if (full) {
-        // VIDE start-up for m = 1..k (Eq. vdiff_start): sum_l M_{m,l} y_l = q_m - M_{m,0} y_0
-        const int N = k * D;
-        Mat<D> y0 = ld<D>(G.les, tri(n) + 0, kb);
-        for (int m = 1; m <= k; ++m) {
-            Mat<D> e = ldf<D>(eps, m, kb);
-            for (int a = 0; a < D; ++a) e.v[a][a].x -= g.mu;
-            Mat<D> rhs;
-            for (int a = 0; a < D; ++a)
-                for (int b = 0; b < D; ++b) rhs.v[a][b] = qsrc[m - 1][a][b];
-            for (int l = 0; l <= k; ++l) {
-                Mat<D> M = meye<D>(cr(W.D[m][l] / g.h));
-                M = madd<D>(M, mscal<D>(g.h * W.greg[m][l], mmuli<D>(gretx<D>(S, m, l, kb))));
-                if (l == m) M = madd<D>(M, mmuli<D>(e));
-                if (l == 0) rhs = msub<D>(rhs, mmul<D>(M, y0));
-                else
-                    for (int a = 0; a < D; ++a)
-                        for (int b = 0; b < D; ++b) Ash[((m - 1) * D + a) * N + (l - 1) * D + b] = M.v[a][b];
-            }
-            for (int a = 0; a < D; ++a)
-                for (int c = 0; c < D; ++c) Bsh[((m - 1) * D + a) * D + c] = rhs.v[a][c];
-        }
-        if (dense_solve(Ash, N, Bsh, D)) atomicOr(status, NGF_SINGULAR);
-        for (int m = 1; m <= k; ++m) {
-            Mat<D> y;
-            for (int a = 0; a < D; ++a)
-                for (int c = 0; c < D; ++c) y.v[a][c] = Bsh[((m - 1) * D + a) * D + c];
-            if (!mfinite<D>(y)) atomicOr(status, NGF_NONFINITE);
-            st<D>(G.les, tri(n) + m, kb, y);
-        }
+        les_col_startup<D>(W, g, n, G, S, eps, kb, qsrc, Ash, Bsh, status);
         mstep = k + 1;
     }
     // serial VIDE steps (Eq. MBCVSAMx_t) in the first argument, m = mstep..n
@@ -429,6 +448,81 @@ __global__ void __launch_bounds__(NG_BND_THREADS) k_step_boundary(Grid g, int n,
         Mat<D> y = mmul<D>(minv<D>(Mm, &sing), acc);
         if (!mfinite<D>(y)) atomicOr(status, NGF_NONFINITE);
         st<D>(G.les, tri(n) + m, kb, y);
+    }
+    if (sing) atomicOr(status, NGF_SINGULAR);
+}
+
+// Serial schedule of step n (the paper's dyson_timestep): the retarded row by the conjugate
+// VIDE (A) along the whole row (start-up for l = 1..k, then single steps in l = n - m for
+// l = k+1..n), and the lesser column by the VIDE (A) along the whole column (G^<(0, n) from
+// Eq. dyson_ini_les, start-up for m = 1..k, then single steps m = k+1..n with the sources
+// -i (C^<_2 + C^<_3)[Sigma, 1, G](m, n)).  The left-mixing row comes from the bulk launch
+// before this one.  One block per problem; every step's sums are block reductions in a fixed
+// order, the step itself runs on thread 0.
+template <int D>
+__global__ void __launch_bounds__(NG_BND_THREADS) k_step_serial(Grid g, int n, HermV G, HermV S, FuncV eps,
+                                                                int* status) {
+    const NgWeights& W = c_W[g.k - 1];
+    const int k = W.k;
+    const int kb = blockIdx.x;
+    const int t = threadIdx.x;
+    __shared__ cplx red[NG_BND_THREADS * D * D];
+    __shared__ cplx qsrc[NG_MAXQ + 1][D][D];
+    __shared__ cplx Ash[(NG_KMAX * D) * (NG_KMAX * D)];
+    __shared__ cplx Bsh[(NG_KMAX * D) * D];
+    int sing = 0;
+
+    // ---- retarded row: y_l = G^R(n, n-l), kernel i Sigma^R(n-l, n-j) ----------------------
+    if (t == 0) ret_row_startup<D>(W, g, n, G, S, eps, kb, Ash, Bsh, status);
+    __syncthreads();
+    for (int j = k + 1; j <= n; ++j) {
+        Mat<D> part = mzero<D>();
+        for (int l = t; l < j; l += blockDim.x)
+            mfma<D>(part, mscal<D>(gw(W, j, l), gret<D>(G, n, n - l, kb)), gret<D>(S, n - l, n - j, kb));
+        Mat<D> hs = block_sum<D>(part, red);
+        if (t == 0) {
+            Mat<D> bdf = mzero<D>();
+            for (int l = 1; l <= k; ++l) bdf = madd<D>(bdf, mscal<D>(W.a[l], gret<D>(G, n, n - j + l, kb)));
+            Mat<D> rhs = msub<D>(mscal<D>(-1.0 / g.h, bdf), mscal<D>(g.h, mmuli<D>(hs)));
+            Mat<D> e = ldf<D>(eps, n - j, kb);
+            for (int a = 0; a < D; ++a) e.v[a][a].x -= g.mu;
+            Mat<D> Mj = meye<D>(cr(W.a[0] / g.h));
+            Mj = madd<D>(Mj, mmuli<D>(e));
+            Mj = madd<D>(Mj, mscal<D>(g.h * gw(W, j, j), mmuli<D>(gret<D>(S, n - j, n - j, kb))));
+            Mat<D> y = mmul<D>(rhs, minv<D>(Mj, &sing));
+            if (!mfinite<D>(y)) atomicOr(status, NGF_NONFINITE);
+            st<D>(G.ret, tri(n) + n - j, kb, y);
+        }
+        __syncthreads();
+    }
+
+    // ---- lesser column ------------------------------------------------------------------
+    if (t == 0) st<D>(G.les, tri(n) + 0, kb, mscal<D>(-1.0, mdag<D>(gtv<D>(G, g, n, 0, kb))));
+    for (int m = 1; m <= k; ++m) {
+        Mat<D> q = block_sum<D>(q_lesA_part<D>(W, g, G, S, m, n, kb, t, blockDim.x), red);
+        if (t == 0)
+            for (int a = 0; a < D; ++a)
+                for (int b = 0; b < D; ++b) qsrc[m - 1][a][b] = q.v[a][b];
+    }
+    __syncthreads();
+    if (t == 0) les_col_startup<D>(W, g, n, G, S, eps, kb, qsrc, Ash, Bsh, status);
+    __syncthreads();
+    for (int m = k + 1; m <= n; ++m) {
+        Mat<D> q = block_sum<D>(q_lesA_part<D>(W, g, G, S, m, n, kb, t, blockDim.x), red);
+        Mat<D> hp = mzero<D>();
+        for (int l = t; l < m; l += blockDim.x)
+            mfma<D>(hp, mscal<D>(gw(W, m, l), gret<D>(S, m, l, kb)), ld<D>(G.les, tri(n) + l, kb));
+        Mat<D> hsum = block_sum<D>(hp, red);
+        if (t == 0) {
+            Mat<D> bdf = mzero<D>();
+            for (int l = 1; l <= k; ++l) bdf = madd<D>(bdf, mscal<D>(W.a[l], ld<D>(G.les, tri(n) + m - l, kb)));
+            Mat<D> acc = msub<D>(q, mscal<D>(1.0 / g.h, bdf));
+            acc = msub<D>(acc, mscal<D>(g.h, mmuli<D>(hsum)));
+            Mat<D> y = mmul<D>(minv<D>(step_matrix<D>(W, g, S, eps, m, kb), &sing), acc);
+            if (!mfinite<D>(y)) atomicOr(status, NGF_NONFINITE);
+            st<D>(G.les, tri(n) + m, kb, y);
+        }
+        __syncthreads();
     }
     if (sing) atomicOr(status, NGF_SINGULAR);
 }

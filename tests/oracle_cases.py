@@ -60,4 +60,4 @@ def embedded_cluster(d, nbath, N, T, beta, h, seed, k=5, schedule="mixed", vscal
     eps = Func(N, d)
     eps.val[:] = hc
     drivers.solve_fixed_sigma(G, S, eps, 0.0, beta, h, Weights(k), schedule=schedule)
-    return G, ex, S
+    return G, ex, S, eps

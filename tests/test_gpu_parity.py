@@ -122,10 +122,12 @@ def _oracle_problem_set(d, nb, N, T, beta, h, k, seed):
     return W, Gs, Ss, epss
 
 
+@pytest.mark.parametrize("schedule", ["mixed", "serial"])
 @pytest.mark.parametrize("d", [1, 2])
-def test_timestep_from_oracle_history(ng, d):
-    """ng_dyson_timestep on the oracle's history reproduces the oracle's step for n in
-    {k+1, 2k, 2k+1, 2k+2, N} (all schedule branches), with per-problem Sigma."""
+def test_timestep_from_oracle_history(ng, d, schedule):
+    """ng_dyson_timestep on the oracle's history reproduces the oracle's step in the same
+    schedule for n in {k+1, 2k, 2k+1, 2k+2, N} (all branches of the mixed schedule), with
+    per-problem Sigma."""
     k, N, T, beta, h, nb = 5, 26, 18, 2.5, 0.06, 3
     W, Gs, Ss, epss = _oracle_problem_set(d, nb, N, T, beta, h, k, seed=11 + d)
     g = ng.Grid(nt=N, ntau=T, nf=d, nbatch=nb, korder=k, h=h, beta=beta)
@@ -135,12 +137,12 @@ def test_timestep_from_oracle_history(ng, d):
     funcs_to_device(epss, eps)
     for n in (k + 1, 2 * k, 2 * k + 1, 2 * k + 2, N):
         oracle_to_herm(Gs, G, g, nmax=n - 1)
-        ctx.dyson_timestep(g, n, G, S, eps)
+        ctx.dyson_timestep(g, n, G, S, eps, schedule=ng.NG_SERIAL if schedule == "serial" else ng.NG_MIXED)
         _status_ok(ctx, ng)
         for kb in range(nb):
             ref = Gs[kb].copy()
             # the oracle's own step n from the same history
-            dyson.dyson_timestep(n, ref, Ss[kb], epss[kb], 0.0, beta, h, W)
+            dyson.dyson_timestep(n, ref, Ss[kb], epss[kb], 0.0, beta, h, W, schedule=schedule)
             got = herm_to_oracle(G, g, kb)
             e = {}
             for c, x, y in (("ret", got.ret[n, :n + 1], ref.ret[n, :n + 1]),
@@ -148,6 +150,35 @@ def test_timestep_from_oracle_history(ng, d):
                             ("tv", got.tv[n], ref.tv[n])):
                 e[c] = np.abs(x - y).max() / np.abs(y).max()
             assert max(e.values()) < TOL, (n, kb, e)
+
+
+def test_serial_schedule_propagation(ng):
+    """A whole fixed-Sigma propagation with every step in the serial schedule (d = 2, two
+    problems) against the oracle's serial solve, and the serial-mixed difference at
+    discretisation level."""
+    from tests.oracle_cases import embedded_cluster
+    k, N, T, beta, h = 5, 24, 16, 1.0, 0.05
+    Gos, Sos, epss = [], [], []
+    for seed in (3, 4):
+        Go, _, So, eo = embedded_cluster(2, 2, N, T, beta, h, seed=seed, schedule="serial")
+        Gos.append(Go), Sos.append(So), epss.append(eo)
+    g = ng.Grid(nt=N, ntau=T, nf=2, nbatch=2, korder=k, h=h, beta=beta)
+    ctx = ng.Context(k)
+    G, S, eps = ng.Herm(g), ng.Herm(g), ng.Func(g)
+    oracle_to_herm(Sos, S, g)
+    funcs_to_device(epss, eps)
+    ctx.dyson_mat(g, G, S, eps)
+    ctx.dyson_start(g, G, S, eps)
+    for n in range(k + 1, N + 1):
+        ctx.dyson_timestep(g, n, G, S, eps, schedule=ng.NG_SERIAL)
+    _status_ok(ctx, ng)
+    Gm = ng.Herm(g)
+    ctx.solve_fixed(g, Gm, S, eps)
+    _status_ok(ctx, ng)
+    for kb in range(2):
+        assert_close(herm_to_oracle(G, g, kb), Gos[kb])
+        diff = relerr(herm_to_oracle(Gm, g, kb), Gos[kb])
+        assert 0 < max(diff.values()) < 1e-4, diff
 
 
 @pytest.mark.parametrize("d", [1, 2])

@@ -158,7 +158,7 @@ from tests.oracle_cases import embedded_cluster  # noqa: E402
 def _cluster_errs(d, nbath, Ns, seed, schedule="mixed"):
     out = []
     for N in Ns:
-        G, ex, _ = embedded_cluster(d, nbath, N, 64, 1.0, 1.0 / N, seed=seed, schedule=schedule)
+        G, ex, _, _ = embedded_cluster(d, nbath, N, 64, 1.0, 1.0 / N, seed=seed, schedule=schedule)
         out.append(max_err(G, ex, sub=(slice(0, d), slice(0, d))))
     return out
 
