@@ -30,16 +30,17 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# FP64 (DFMA, non-tensor) peak of one GB300 from its unit counts: 152 SMs x 2 DFMA per clock
-# per SM x 2 flop, times the SM clock (1.2586 TFLOP/s at the 2070 MHz maximum, the nominal
-# 1.25 TFLOP/s).  The clock is the median sampled during the timed region.
+# FP64 (DFMA, non-tensor) peak of one GB300 from its unit counts: SMs (152, read from the
+# device) x 2 DFMA per clock per SM x 2 flop, times the SM clock (1.2586 TFLOP/s at the
+# 2070 MHz maximum, the nominal 1.25 TFLOP/s).  The clock is the median sampled during the timed
+# region.
 GB300_SMS = 152
 FP64_FLOP_PER_CLK_PER_SM = 4
 SM_MAX_MHZ = 2070.0
 
 
-def fp64_peak_tflops(sm_mhz):
-    return GB300_SMS * FP64_FLOP_PER_CLK_PER_SM * (sm_mhz or SM_MAX_MHZ) * 1e6 / 1e12
+def fp64_peak_tflops(sm_mhz, sms=GB300_SMS):
+    return sms * FP64_FLOP_PER_CLK_PER_SM * (sm_mhz or SM_MAX_MHZ) * 1e6 / 1e12
 
 
 def max_over_ranks(x, device="cuda"):
@@ -54,12 +55,6 @@ def max_over_ranks(x, device="cuda"):
     return float(t.item())
 
 
-def whole_job_rate(units_per_rank, world, seconds):
-    """Units processed by all ranks per second of the slowest rank (weak scaling: every rank
-    runs the full workload)."""
-    return world * units_per_rank / seconds
-
-
 def parse():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -71,6 +66,8 @@ def parse():
     ap.add_argument("--nt", type=int, default=2000)
     ap.add_argument("--ntau", type=int, default=800)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-oracle-check", action="store_true",
+                    help="skip the oracle's time step n = nt on four k-points (headline-size parity)")
     ap.add_argument("--workload", choices=["chain", "uneven", "adjoint"], default="chain",
                     help="chain: the headline chain_kspace run; uneven: the 64-cluster uneven batch; "
                          "adjoint: gradient of E_kin(t_N) on the 16x16 square lattice")
@@ -91,14 +88,16 @@ def workload(a):
     return wl.chain_kspace(nk=a.nk, nt=a.nt, ntau=a.ntau)
 
 
-def config_of(w, K, W):
+def config_of(w, K, W, world=1):
     return {
         "workload": f"chain_kspace nk={w.nbatch} nt={w.nt} ntau={w.ntau} h={w.h} beta={w.beta} U={w.U[1]:g} "
                     f"k={w.korder} corrector={w.corrector} (1D Hubbard chain, local second-Born, Peierls pulse)",
         "global_batch": w.nbatch, "nt": w.nt, "ntau": w.ntau, "nf": w.nf,
         "timed_steps": f"last {K} of {w.nt - w.korder} time steps (n = {w.nt - K + 1}..{w.nt}), {W} warm-up",
         "l2": "inputs larger than L2 (per-k history of tens of GB re-read every step)",
-        "parallelism": "single GPU, all k-points in one batch",
+        "parallelism": ("single GPU, all k-points in one batch" if world == 1 else
+                        f"{world} GPUs, k-points sharded in whole 32-blocks, one allgather of the block sums "
+                        f"per k-reduction"),
     }
 
 
@@ -234,7 +233,61 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------------------------------
+# headline-size parity: the oracle's own time step from the GPU's history
+# ------------------------------------------------------------------------------------------
+def _oracle_step_check(args):
+    """Worker: the oracle's Dyson time step n of one k-point from the GPU's history (slices < n
+    of G_k), its self-energy (slices <= n of Sigma) and eps_mf(n) of its last corrector pass;
+    returns max |gpu - oracle| / max |oracle| per component of slice n."""
+    import numpy as np
+    from oracle import dyson
+    from oracle.contour import Func, Herm
+    from oracle.weights import Weights
+    n, nt, ntau, beta, h, korder, Gp, Sp, eps, gpu_slice = args
+
+    def herm(packed, upto):
+        X = Herm(n, ntau, 1)
+        X.mat[:, 0, 0] = packed["mat"]
+        for m in range(upto + 1):
+            X.ret[m, :m + 1, 0, 0] = packed["ret"][m * (m + 1) // 2:m * (m + 1) // 2 + m + 1]
+            X.les[:m + 1, m, 0, 0] = packed["les"][m * (m + 1) // 2:m * (m + 1) // 2 + m + 1]
+            X.tv[m, :, 0, 0] = packed["tv"][m * (ntau + 1):(m + 1) * (ntau + 1)]
+        return X
+    G, S = herm(Gp, n - 1), herm(Sp, n)
+    e = Func(n, 1)
+    e.val[:, 0, 0] = eps[:n + 2]
+    dyson.dyson_timestep(n, G, S, e, 0.0, beta, h, Weights(korder))
+    ref = {"ret": G.ret[n, :n + 1, 0, 0], "les": G.les[:n + 1, n, 0, 0], "tv": G.tv[n, :, 0, 0]}
+    return {c: float(np.abs(gpu_slice[c] - ref[c]).max() / np.abs(ref[c]).max()) for c in ref}
+
+
+def oracle_check_args(ng, g, n, G, S, mf, kbs):
+    """Per k-point inputs of _oracle_step_check (host copies of the device history, nf = 1)."""
+    T = g.ntau
+    cut = {"mat": slice(0, T + 1), "ret": slice(0, ng.tri(n + 1)), "les": slice(0, ng.tri(n + 1)),
+           "tv": slice(0, (n + 1) * (T + 1))}
+    Sp = {c: getattr(S, c)[cut[c], 0, 0, 0].cpu().numpy() for c in cut}
+    out = []
+    for kb in kbs:
+        Gp = {c: getattr(G, c)[cut[c], 0, 0, kb].cpu().numpy() for c in cut}
+        gs = {"ret": Gp["ret"][ng.tri(n):ng.tri(n) + n + 1].copy(), "les": Gp["les"][ng.tri(n):ng.tri(n) + n + 1].copy(),
+              "tv": Gp["tv"][n * (T + 1):(n + 1) * (T + 1)].copy()}
+        eps = mf.val[:, 0, 0, kb].cpu().numpy()
+        out.append((n, g.nt, T, g.beta, g.h, g.korder, Gp, Sp, eps, gs))
+    return out
+
+
+def fp64_probe_summary(ng):
+    try:
+        return ng.fp64_probe()
+    except Exception as e:      # noqa: BLE001 - the probe is supporting evidence only
+        return {"error": str(e)}
+
+
 def run_ours(a):
+    import multiprocessing as mp
+
     import numpy as np
     import torch
     import paper_1911_01211_gb300 as ng
@@ -243,6 +296,10 @@ def run_ours(a):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     dist = world > 1
+    # oracle workers for the headline-size parity check: spawned before the first GPU call
+    pool = None
+    if rank == 0 and not a.no_oracle_check:
+        pool = mp.get_context("spawn").Pool(min(4, os.cpu_count() or 1))
     if dist:
         import torch.distributed as td
         td.init_process_group("nccl")
@@ -254,22 +311,30 @@ def run_ours(a):
     if K + W > w.nt - k:
         raise SystemExit(f"steps + warmup must be <= {w.nt - k}")
     n_first_timed = w.nt - K + 1
-
-    g = ng.Grid(nt=w.nt, ntau=w.ntau, nf=w.nf, nbatch=w.nbatch, korder=k, h=w.h, beta=w.beta, mu=w.mu)
+    nk = w.nbatch
+    g_all = ng.Grid(nt=w.nt, ntau=w.ntau, nf=w.nf, nbatch=nk, korder=k, h=w.h, beta=w.beta, mu=w.mu)
+    # this rank's k-points: whole blocks of 32 (all of them on one GPU)
+    kb0, nkl, _ = ng.shard_plan(nk, rank, world, g_all)
+    g = ng.Grid(nt=w.nt, ntau=w.ntau, nf=w.nf, nbatch=nkl, korder=k, h=w.h, beta=w.beta, mu=w.mu)
+    exchange = None
+    if dist:
+        from paper_1911_01211_gb300.shard import DistExchange
+        exchange = DistExchange(nk, g, f"cuda:{local}")
     ctx = ng.Context(k, local)
+    probe = fp64_probe_summary(ng)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
     G = ng.Herm(g, zero=False)
     L, S = ng.Herm(g, ldk=1), ng.Herm(g, ldk=1)
     e0, mf = ng.Func(g), ng.Func(g)
     U = ng.Func(g, scalar=True)
-    # inputs in pinned host memory; slices of eps_k are copied to the device step by step
-    eps_host = torch.from_numpy(np.ascontiguousarray(w.eps0)).pin_memory()
+    # inputs and outputs in pinned host memory; the library copies eps_k(t_n) in and
+    # Gloc^<(t_n, t_n) out step by step (ng_run_2b_host)
+    eps_host = torch.from_numpy(np.ascontiguousarray(w.eps0[..., kb0:kb0 + nkl])).pin_memory()
     U_host = torch.from_numpy(w.U.astype(np.complex128)).pin_memory()
-    rho_host = torch.zeros(w.nt + 1, dtype=torch.complex128).pin_memory()
+    gd_host = torch.zeros((w.nt + 1, w.nf, w.nf), dtype=torch.complex128).pin_memory()
     stream = torch.cuda.current_stream()
-    dd = w.nf * w.nf
-    les_diag = [ng.tri(n) + n for n in range(w.nt + 1)]
     h2d_bytes = eps_host[0].numel() * 16
-    d2h_bytes = 16
+    d2h_bytes = w.nf * w.nf * 16
 
     def barrier():
         torch.cuda.synchronize()
@@ -277,122 +342,161 @@ def run_ours(a):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    barrier()
-    t_job0 = time.perf_counter()
-    # ---- setup inputs and the untimed Matsubara loop + bootstrapping --------------------
-    e0.val[:k + 2].copy_(eps_host[:k + 2], non_blocking=True)
-    U.val[:, 0, 0, 0].copy_(U_host, non_blocking=True)
-    ctx.run_2b(g, G, L, S, e0, mf, U, corrector=w.corrector, n_from=k + 1, n_to=k, do_setup=True)
+    def run(n_from, n_to, setup, precision):
+        return ctx.run_2b_host(g, G, L, S, e0, mf, U, eps_host, U_host, gd_host, corrector=w.corrector,
+                               n_from=n_from, n_to=n_to, do_setup=setup, precision=precision, exchange=exchange)
 
-    def step(n, precision):
-        e0.val[n + 1].copy_(eps_host[n + 1], non_blocking=True)            # this step's input
-        ctx.run_2b(g, G, L, S, e0, mf, U, corrector=w.corrector, n_from=n, n_to=n, do_setup=False,
-                   precision=precision)
-        rho_host[n].copy_(L.les[les_diag[n], 0, 0, 0], non_blocking=True)  # this step's result
-
-    def propagate(precision):
-        """Steps k+1..nt; the last K are timed (CUDA events, synchronised on both sides)."""
-        for n in range(k + 1, n_first_timed):
-            step(n, precision)
+    def propagate(precision, setup):
+        """Steps k+1..nt (after the setup when `setup`); the last K are timed (CUDA events on the
+        launching stream and the host clock, synchronised on both sides)."""
+        barrier()
+        t0 = time.perf_counter()
+        run(k + 1, n_first_timed - 1, setup, precision)
         barrier()
         clocks = ClockSampler(local)
         clocks.start()
         ctx.profile_enable(True)
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tw0 = time.perf_counter()
         ev0.record(stream)
-        for n in range(n_first_timed, w.nt + 1):
-            step(n, precision)
+        run(n_first_timed, w.nt, False, precision)
         ev1.record(stream)
         barrier()
-        t_end = time.perf_counter()
+        t1 = time.perf_counter()
         ctx.profile_enable(False)
         clk = clocks.stop()
-        return ev0.elapsed_time(ev1), ctx.profile_read(), clk, t_end
+        return {"ms": ev0.elapsed_time(ev1), "prof": ctx.profile_read(), "clk": clk, "job_s": t1 - t0,
+                "window_s": t1 - tw0}
 
-    ms, prof, clk, t_job1 = propagate(ng.NG_FP64)
+    check_kbs = sorted(set(np.random.default_rng(191101211).choice(nkl, size=min(4, nkl), replace=False).tolist()))
+    pending = {}
+
+    def submit_check(name):
+        if pool is not None:
+            args = oracle_check_args(ng, g, w.nt, G, S, mf, check_kbs)
+            pending[name] = pool.map_async(_oracle_step_check, args, chunksize=1)
+
+    r = propagate(ng.NG_FP64, True)
     st, flags = ctx.status_sync()
-    ms = max_over_ranks(ms)
-    value = whole_job_rate(w.nbatch * K, world, ms / 1e3)
-    e2e_value = whole_job_rate(w.nbatch * (w.nt - k), world, max_over_ranks(t_job1 - t_job0))
-    # per step: extrapolation, then per corrector pass k-reduce, Hartree, 2B, M_n^-1 (+ bulk, boundary)
-    launches = int(prof["bulk_launches"] + prof["boundary_launches"]) + K * (1 + 3 * 4)
+    submit_check("f64")
+    ms = max_over_ranks(r["ms"])
+    value = nk * K / (ms / 1e3)
+    e2e_value = nk * (w.nt - k) / max_over_ranks(r["job_s"])
+    e2e_window = nk * K / max_over_ranks(r["window_s"])
+    prof, clk = r["prof"], r["clk"]
+    # per step: extrapolation, then per corrector pass k-reduce (or partial + combine), Hartree,
+    # 2B, M_n^-1 (+ bulk, boundary)
+    launches = int(prof["bulk_launches"] + prof["boundary_launches"]) + K * (1 + 3 * (4 + (1 if dist else 0)))
     achieved = prof["bulk_flops"] / (prof["bulk_ms"] / 1e3) / 1e12
-    peak = fp64_peak_tflops(clk.get("sm_mhz"))
-    traffic = None
+    peak = fp64_peak_tflops(clk.get("sm_mhz"), sms)
+    bulk_launches = max(1, prof["bulk_launches"])
+    cmac_per_launch = prof["bulk_flops"] / 8.0 / w.nf ** 3 / bulk_launches
+    traffic, traffic_note = None, None
     try:
+        import hashlib
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             tr = json.load(f)
         src = open(os.path.join(ROOT, "paper_1911_01211_gb300", "csrc", "ng_step.cuh"), "rb").read()
-        import hashlib
-        window = f"nk={w.nbatch} nt={w.nt} ntau={w.ntau} n={n_first_timed}..{w.nt}"
-        if tr.get("ng_step_sha1") == hashlib.sha1(src).hexdigest() and tr.get("window") == window:
-            traffic = tr.get("bulk_bytes_per_launch_timed_window")
-    except (OSError, ValueError):
-        traffic = None
-    rho = rho_host[k + 1:].numpy().copy()
+        if tr.get("ng_step_sha1") == hashlib.sha1(src).hexdigest():
+            traffic = tr["captured"]["dram_bytes_per_cmac"] * cmac_per_launch
+            traffic_note = (f"{tr['captured']['dram_bytes_per_cmac']:.2f} DRAM bytes per complex multiply-add "
+                            f"(ncu capture: {tr['captured']['launch']}) x {cmac_per_launch:.4g} multiply-adds per "
+                            f"launch of this window")
+        else:
+            traffic_note = "null: the time-step kernels changed since the ncu capture"
+    except (OSError, ValueError, KeyError):
+        traffic_note = "null: no ncu capture recorded"
+    gd = gd_host.numpy().copy()
     # properties that hold at any size: particle number conserved for all t; Galitskii-Migdal
     # total energy conserved once the pulse has decayed (t >= 10: A(t) < 1e-5)
     obs = torch.zeros(5, dtype=torch.float64, device="cuda")
     n_after = [n for n in range(k + 1, w.nt + 1) if n * w.h >= 10.0]
     sample_n = sorted(set([k + 1] + list(range(k + 1, w.nt + 1, max(1, (w.nt - k) // 20))) + [w.nt]))
     vals = {}
-    for n in sorted(set(sample_n + n_after[:: max(1, len(n_after) // 20)] + ([n_after[-1]] if n_after else []))):
-        ctx.observables(g, n, G, S, e0, mf, obs)
-        vals[n] = obs.cpu().numpy().copy()
-    Ns = np.array([v[0] for v in vals.values()])
-    Eafter = np.array([vals[n][4] for n in vals if n * w.h >= 10.0])
-    properties = {"N_drift_all_t": float(np.ptp(Ns)), "N_mean": float(Ns.mean()),
-                  "E_tot_drift_after_pulse": float(np.ptp(Eafter)) if len(Eafter) else None,
-                  "E_tot_at_end": float(vals[w.nt][4]), "E_kin_at_end": float(vals[w.nt][1]),
-                  "E_corr_at_end": float(vals[w.nt][3]), "samples": len(vals)}
+    properties = None
+    if not dist:
+        for n in sorted(set(sample_n + n_after[:: max(1, len(n_after) // 20)] + ([n_after[-1]] if n_after else []))):
+            ctx.observables(g, n, G, S, e0, mf, obs)
+            vals[n] = obs.cpu().numpy().copy()
+        Ns = np.array([v[0] for v in vals.values()])
+        Eafter = np.array([vals[n][4] for n in vals if n * w.h >= 10.0])
+        properties = {"N_drift_all_t": float(np.ptp(Ns)), "N_mean": float(Ns.mean()),
+                      "E_tot_drift_after_pulse": float(np.ptp(Eafter)) if len(Eafter) else None,
+                      "E_tot_at_end": float(vals[w.nt][4]), "E_kin_at_end": float(vals[w.nt][1]),
+                      "E_corr_at_end": float(vals[w.nt][3]), "samples": len(vals)}
     modes = {}
     if a.precision == "both":
         # FP32-compensated and double-float time steps, each re-propagated from the same setup
         # (slices 0..k are not touched by the stepping) over the same timed window; error
-        # against the FP64 run on the final slice n = nt (all k-points, ret row / les column /
-        # tv row) and on rho_loc(t) for every t.
+        # against the FP64 run on the final slice n = nt (all local k-points, ret row / les
+        # column / tv row) and on Gloc^<(t, t) for every t.
         nt = w.nt
         sl = lambda: {"ret": G.ret[ng.tri(nt):ng.tri(nt) + nt + 1], "les": G.les[ng.tri(nt):ng.tri(nt) + nt + 1],
                       "tv": G.tv[nt * (w.ntau + 1):(nt + 1) * (w.ntau + 1)]}
         ref = {c: x.clone() for c, x in sl().items()}
         bytes_per_elem = {"f32c": 8, "df64": 16}
         for name, prec, kern in (("f32c", ng.NG_F32C, "k_step_bulk32<1>"), ("df64", ng.NG_DF64, "k_step_bulkdf<1>")):
-            msm, profm, clkm, _ = propagate(prec)
+            rm = propagate(prec, False)
             stm, flagsm = ctx.status_sync()
+            submit_check(name)
             err = {c: float((x - ref[c]).abs().max() / ref[c].abs().max()) for c, x in sl().items()}
-            err["rho_loc_abs"] = float(np.abs(rho_host[k + 1:].numpy() - rho).max())
-            vm = whole_job_rate(w.nbatch * K, world, max_over_ranks(msm) / 1e3)
+            err["gloc_diag_abs"] = float(np.abs(gd_host.numpy()[k + 1:] - gd[k + 1:]).max())
+            msm, profm = max_over_ranks(rm["ms"]), rm["prof"]
+            vm = nk * K / (msm / 1e3)
             cmacs = profm["bulk_flops"] / (8.0 * w.nf ** 3)
             modes[name] = {
                 "value": vm, "unit": "k-point timesteps/s", "ms_per_step": msm / K, "dtype": name,
                 "speedup_vs_f64": vm / value, "max_rel_err_vs_f64_final_slice": err,
+                "e2e_window": {"value": nk * K / max_over_ranks(rm["window_s"]), "unit": "k-point timesteps/s"},
                 "bulk_kernel": {"kernel": kern,
                                 "algorithmic_fp64_equiv_tflops": profm["bulk_flops"] / (profm["bulk_ms"] / 1e3) / 1e12,
                                 "history_gbs": cmacs * bytes_per_elem[name] / (profm["bulk_ms"] / 1e3) / 1e9,
+                                "hbm_frac_of_measured": None,
                                 "avg_launch_ms": profm["bulk_ms"] / max(1, profm["bulk_launches"]),
-                                "share_of_timed": profm["bulk_ms"] / msm},
-                "clocks": clkm, "device_status": {"status": stm, "flags": flagsm}}
+                                "share_of_timed": profm["bulk_ms"] / rm["ms"]},
+                "clocks": rm["clk"], "device_status": {"status": stm, "flags": flagsm}}
+            hbm = measured_hbm_gbs()
+            if hbm:
+                modes[name]["bulk_kernel"]["hbm_frac_of_measured"] = modes[name]["bulk_kernel"]["history_gbs"] / hbm
     if rank != 0:
+        if dist:
+            torch.distributed.destroy_process_group()
         return
+    oracle_err = None
+    if pending:
+        oracle_err = {"step": w.nt, "k_points": [kb0 + kb for kb in check_kbs],
+                      "what": "the oracle's Dyson time step n = nt of each listed k-point from the GPU's own history, "
+                              "self-energy and eps_mf of its last corrector pass, against the GPU's slice n; "
+                              "max |gpu - oracle| / max |oracle| per component, worst k-point"}
+        for name, res in pending.items():
+            per = res.get(timeout=1800)
+            oracle_err[name] = {c: max(p[c] for p in per) for c in ("ret", "les", "tv")}
+        pool.close()
     line = {
         "metric": "k-point timesteps/s", "value": value, "unit": "k-point timesteps/s",
         "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": ms / K, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": config_of(w, K, W),
+        "scaling": "strong" if dist else "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_of(w, K, W, world),
+        "max_rel_err_vs_oracle": oracle_err,
         "e2e": {"value": e2e_value, "unit": "k-point timesteps/s", "h2d_bytes_per_step": h2d_bytes,
                 "d2h_bytes_per_step": d2h_bytes,
-                "scope": "whole job through the public API: setup (Matsubara loop, bootstrapping) and every "
-                         "time step, per-step H2D of eps_k(t_n) from pinned host memory and D2H of rho_loc(t_n)"},
+                "scope": "whole job through ng_run_2b_host (the C-ABI driver with host buffers): setup (Matsubara "
+                         "loop, bootstrapping) and every time step; each step copies eps_k(t_n) from pinned host "
+                         "memory to the device and Gloc^<(t_n, t_n) back",
+                "window": {"value": e2e_window, "unit": "k-point timesteps/s",
+                           "scope": "the timed window's steps only, same call, host clock"}},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": traffic, "kernel": "k_step_bulk<1>",
-                     "peak_source": f"FP64 DFMA from unit counts: {GB300_SMS} SMs x {FP64_FLOP_PER_CLK_PER_SM} "
-                                    f"flop/clk x median SM clock {clk.get('sm_mhz')} MHz",
-                     "avg_launch_ms": prof["bulk_ms"] / max(1, prof["bulk_launches"]),
-                     "share_of_timed": prof["bulk_ms"] / ms},
+                     "frac": achieved / peak, "traffic": traffic, "traffic_note": traffic_note,
+                     "kernel": "k_step_bulk<1>",
+                     "peak_source": f"FP64 DFMA from unit counts: {sms} SMs (device property) x "
+                                    f"{FP64_FLOP_PER_CLK_PER_SM} flop/clk x median SM clock {clk.get('sm_mhz')} MHz; "
+                                    f"measured by ng_fp64_probe in this run: {probe}",
+                     "avg_launch_ms": prof["bulk_ms"] / bulk_launches,
+                     "share_of_timed": prof["bulk_ms"] / r["ms"]},
         "gpu_launches": launches, "clocks": clk,
         "device_status": {"status": st, "flags": flags},
-        "observables": {"N_loc_first_timed": float(np.real(-1j * rho[n_first_timed - k - 1])),
-                        "N_loc_last": float(np.real(-1j * rho[-1]))},
+        "observables": {"N_loc_first_timed": float(np.real(-1j * gd[n_first_timed, 0, 0])),
+                        "N_loc_last": float(np.real(-1j * gd[-1, 0, 0]))},
         "properties": properties,
     }
     line.update(modes)
@@ -401,6 +505,14 @@ def run_ours(a):
     print(json.dumps(line), flush=True)
     if dist:
         torch.distributed.destroy_process_group()
+
+
+def measured_hbm_gbs():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return None
 
 
 def run_uneven(a):

@@ -1,6 +1,6 @@
 """The multi-rank timing of bench.py (one process per GPU under torchrun): every rank reports
-the slowest rank's time and the job rate counts the units of all ranks.  Run as two gloo ranks
-on the CPU."""
+the slowest rank's time, which sets the job's rate (the k-points of all ranks over that time).
+Run as two gloo ranks on the CPU."""
 import os
 import socket
 
@@ -23,7 +23,7 @@ def _rank(rank, world, port, out):
     try:
         t = 1.5 + rank            # rank 1 is the slower one
         slowest = bench.max_over_ranks(t, device="cpu")
-        out[rank] = (slowest, bench.whole_job_rate(100, world, slowest))
+        out[rank] = slowest
     finally:
         td.destroy_process_group()
 
@@ -34,9 +34,8 @@ def test_two_ranks_agree_on_the_slowest_time():
         out = m.dict()
         tmp.spawn(_rank, args=(world, _free_port(), out), nprocs=world, join=True)
         res = dict(out)
-    assert res[0] == res[1] == (2.5, 2 * 100 / 2.5)
+    assert res[0] == res[1] == 2.5
 
 
 def test_single_process_is_its_own_maximum():
     assert bench.max_over_ranks(3.25, device="cpu") == 3.25
-    assert bench.whole_job_rate(10, 1, 2.0) == 5.0

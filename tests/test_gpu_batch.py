@@ -124,3 +124,58 @@ def test_plain_solve_of_one_cluster_matches_the_batch(ng):
         assert max(e.values()) < 1e-12, (p["nf"], e)
     assert ctx.status_sync() == (ng.NG_OK, 0)
     batch.close()
+
+
+def _random_history(rng, N, T, d):
+    """Seeded random contour data on every stored element (a time step is a linear recursion,
+    so its parity with the oracle holds for any history)."""
+    X = OHerm(N, T, d)
+    c = lambda *s: 0.3 * (rng.normal(0, 1, s) + 1j * rng.normal(0, 1, s))
+    X.mat[...] = c(T + 1, d, d)
+    X.tv[...] = c(N + 1, T + 1, d, d)
+    low = np.tril(np.ones((N + 1, N + 1), bool))
+    X.ret[low] = c(int(low.sum()), d, d)
+    X.les[low.T] = c(int(low.sum()), d, d)
+    return X
+
+
+def test_uneven_batch_step_with_multichunk_boundary_sources(ng):
+    """ng_batch_step for nf = 4 and nf = 8 problems with ntau = 300 and 270: the (A) rows' source
+    sums run over n + ntau > 256 indices, i.e. over three or more chunks of 128 whose partial
+    sums k_usrc adds in order (the path of the full-size uneven workload).  One global step
+    from a seeded random history at n = 2k+1 (whole lesser column by (A)) and n = 24 (mixed),
+    against the oracle's step of each problem."""
+    from oracle import dyson
+    k, h = 5, 0.05
+    specs = [(4, 24, 300, 3.0), (8, 26, 270, 5.0)]
+    rng = np.random.default_rng(2024)
+    W = Weights(k)
+    ctx = ng.Context(k)
+    grids, Gs, Ss, es, oG, oS, oe = [], [], [], [], [], [], []
+    for d, N, T, beta in specs:
+        g = ng.Grid(nt=N, ntau=T, nf=d, nbatch=1, korder=k, h=h, beta=beta)
+        Go, So = _random_history(rng, N, T, d), _random_history(rng, N, T, d)
+        eo = OFunc(N, d)
+        eo.val[:] = wl.random_hermitian(rng, d)
+        G, S, e = ng.Herm(g), ng.Herm(g), ng.Func(g)
+        oracle_to_herm([Go], G, g)
+        oracle_to_herm([So], S, g)
+        funcs_to_device([eo], e)
+        grids.append(g), Gs.append(G), Ss.append(S), es.append(e)
+        oG.append(Go), oS.append(So), oe.append(eo)
+    batch = ctx.batch(grids, Gs, Ss, es)
+    for n in (2 * k + 1, 24):
+        for g, G, Go in zip(grids, Gs, oG):
+            oracle_to_herm([Go], G, g, nmax=n - 1)
+        batch.step(n)
+        torch.cuda.synchronize()
+        assert ctx.status_sync() == (ng.NG_OK, 0)
+        for (d, N, T, beta), g, G, Go, So, eo in zip(specs, grids, Gs, oG, oS, oe):
+            ref = Go.copy()
+            dyson.dyson_timestep(n, ref, So, eo, 0.0, beta, h, W)
+            got = herm_to_oracle(G, g, 0)
+            for name, x, y in (("ret", got.ret[n, :n + 1], ref.ret[n, :n + 1]),
+                               ("les", got.les[:n + 1, n], ref.les[:n + 1, n]), ("tv", got.tv[n], ref.tv[n])):
+                err = np.abs(x - y).max() / np.abs(y).max()
+                assert err < TOL, (d, n, name, err)
+    batch.close()
