@@ -99,6 +99,17 @@ typedef struct {
  * cross terms, TwoSum accumulation), FP64-class accuracy on the FP32 pipes. */
 typedef enum { NG_FP64 = 0, NG_F32C = 1, NG_DF64 = 2 } ng_precision;
 
+/* Evaluation of the left-mixing Matsubara source -i (C^tv_2 + C^tv_3)[Sigma, 1, G^M](n, tau_m) of
+ * a time step (Eqs. ctv2, ctv3), set per context with ng_set_tv_source.  NG_TVSRC_DIRECT: the
+ * quadrature sums as written, O(ntau^2) complex multiply-adds per problem and step.
+ * NG_TVSRC_AUTO (default): the unit-weight part of both pieces is one correlation over tau,
+ * evaluated for all tau_m by an FP64 FFT of length L (the power of two >= 2 ntau + 1; one
+ * block per problem, transforms in shared memory), and the time-step kernels add the O(k)
+ * Gregory end and boundary (R) corrections per element; used for nf = 1, 2 when the transforms
+ * fit the shared memory (nf = 1: ntau <= 2047, nf = 2: ntau <= 511), the direct sums otherwise.
+ * Both evaluate the same quadrature; they differ by rounding only. */
+typedef enum { NG_TVSRC_AUTO = 0, NG_TVSRC_DIRECT = 1 } ng_tv_source;
+
 /* Schedule of a time step (Sec. "Time stepping"): NG_MIXED is the paper's parallel variant
  * (implementation (B) for the bulk of the retarded row and lesser column, (A) near the
  * diagonal); NG_SERIAL is its serial variant, implementation (A) along the whole retarded row
@@ -217,6 +228,9 @@ ng_status ng_dyson_timestep(ng_ctx *ctx, const ng_grid *grid, int tstp, ng_herm 
  * Arguments as for ng_dyson_start (G with ldk = nbatch; Sigma and eps with ldk = 1 or
  * nbatch); runs on the device that is current when it is called, stream-ordered on `stream`. */
 ng_status ng_dyson_start_noalloc(const ng_grid *grid, ng_herm G, ng_herm Sigma, ng_func eps, void *stream);
+
+/* Choose the evaluation of the left-mixing source for later time steps on ctx (ng_tv_source). */
+ng_status ng_set_tv_source(ng_ctx *ctx, int mode);
 
 /* Forget the FP32 copies kept for NG_F32C time steps (they are rebuilt on the next call). */
 ng_status ng_precision_reset(ng_ctx *ctx);
@@ -360,22 +374,27 @@ ng_status ng_batch_setup(ng_ctx *ctx, ng_batch *batch, void *stream);
 ng_status ng_batch_step(ng_ctx *ctx, ng_batch *batch, int n, int threads, void *stream);
 
 /* Setup, then every global time step until each problem reaches its nt.  The bulk block size
- * is tuned once, by timing each candidate on a re-run of one representative step (a step is
- * idempotent); *tuned_threads (may be NULL) receives the choice. */
+ * is tuned by timing each candidate on a re-run of one representative step (a step is
+ * idempotent), once per batch shape and context: the context keeps the choice for batches with
+ * the same number of problems of each nf, the same largest ntau and the same largest nt (in
+ * steps of 256) and reuses it without timing.  *tuned_threads (may be NULL) receives it. */
 ng_status ng_batch_solve(ng_ctx *ctx, ng_batch *batch, int *tuned_threads, void *stream);
 
 /* ---- measurement ---------------------------------------------------------------------- */
 
 /* Start (enable = 1, clearing any previous record) or stop (enable = 0) per-launch timing of
- * the two time-step kernels of ng_dyson_timestep: CUDA events are recorded on the launching
- * stream around every launch of the merged bulk kernel and of the boundary kernel. */
+ * the time-step kernels of ng_dyson_timestep: CUDA events are recorded on the launching
+ * stream around every launch of the merged bulk kernel, of the boundary kernel and of the FFT
+ * pre-pass of the left-mixing source. */
 ng_status ng_profile_enable(ng_ctx *ctx, int enable);
 
 /* Read the record (synchronises on the last recorded event).  out[0] = total bulk-kernel
  * time in ms, out[1] = number of bulk launches, out[2] = algorithmic FP64 flops of those
  * launches (8 real flops per complex multiply-add of the history and source sums, nf^3
- * complex multiply-adds per d x d block product), out[3] = total boundary-kernel time in ms,
- * out[4] = number of boundary launches.  `out` must hold 5 doubles. */
+ * complex multiply-adds per d x d block product; with the FFT source, its quadrature
+ * corrections in place of the O(ntau^2) sums), out[3] = total boundary-kernel time in ms,
+ * out[4] = number of boundary launches, out[5] = total time of the FFT source pre-pass in ms,
+ * out[6] = its launches.  `out` must hold 7 doubles. */
 ng_status ng_profile_read(ng_ctx *ctx, double *out);
 
 /* FP64 throughput of the current device, for the roofline of the FP64 kernels: out[0] = the

@@ -25,6 +25,7 @@ LIB_PATH = os.path.join(_HERE, "libng.so")
  NG_ECOMM) = range(10)
 NG_FP64, NG_F32C, NG_DF64 = 0, 1, 2
 NG_MIXED, NG_SERIAL = 0, 1
+NG_TVSRC_AUTO, NG_TVSRC_DIRECT = 0, 1
 _STATUS_NAMES = ["NG_OK", "NG_EINVAL", "NG_ENOMEM", "NG_ECUDA", "NG_ENOCONV", "NG_ETIMEOUT",
                  "NG_ENONFINITE", "NG_EUNSUPPORTED", "NG_ESCRATCH", "NG_ECOMM"]
 
@@ -112,6 +113,7 @@ SIGNATURES = {
                                                ng_herm, _P]),
     "ng_observables": (ctypes.c_int, [_P, _G, ctypes.c_int, ng_herm, ng_herm, ng_func, ng_func, _P, _P]),
     "ng_dyson_start_noalloc": (ctypes.c_int, [_G, ng_herm, ng_herm, ng_func, _P]),
+    "ng_set_tv_source": (ctypes.c_int, [_P, ctypes.c_int]),
     "ng_fp64_probe": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), _P]),
     "ng_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "ng_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
@@ -328,10 +330,15 @@ class Context:
         self._chk(self.lib.ng_profile_enable(self.h, 1 if on else 0))
 
     def profile_read(self):
-        """{bulk_ms, bulk_launches, bulk_flops, boundary_ms, boundary_launches}"""
-        out = (ctypes.c_double * 5)()
+        """{bulk_ms, bulk_launches, bulk_flops, boundary_ms, boundary_launches, tvfft_ms, tvfft_launches}"""
+        out = (ctypes.c_double * 7)()
         self._chk(self.lib.ng_profile_read(self.h, out))
-        return dict(zip(("bulk_ms", "bulk_launches", "bulk_flops", "boundary_ms", "boundary_launches"), list(out)))
+        return dict(zip(("bulk_ms", "bulk_launches", "bulk_flops", "boundary_ms", "boundary_launches", "tvfft_ms",
+                         "tvfft_launches"), list(out)))
+
+    def set_tv_source(self, mode):
+        """NG_TVSRC_AUTO (FFT where supported) or NG_TVSRC_DIRECT."""
+        self._chk(self.lib.ng_set_tv_source(self.h, mode))
 
     def status_sync(self, stream=None):
         f = ctypes.c_int()

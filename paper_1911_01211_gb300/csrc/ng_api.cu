@@ -13,6 +13,7 @@
 #include "ng_ubatch.cuh"
 #include "ng_stepdf.cuh"
 #include "ng_conv_launch.h"
+#include "ng_tvfft.h"
 #include "ng_adjoint_types.h"
 #include <cmath>
 
@@ -58,7 +59,7 @@ struct ng_ctx {
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
     double prof_flops = 0.0;
-    std::vector<int> ev_kind;        // 0 bulk, 1 boundary, per event pair
+    std::vector<int> ev_kind;        // 0 bulk, 1 boundary, 2 FFT source pre-pass, per event pair
     Shadow shG, shS;                 // FP32 copies of G and Sigma for NG_F32C
     ShadowDF dfG, dfS;               // double-float copies of G and Sigma for NG_DF64
     void* ws_obs = nullptr;          // per-problem observables before the batch sum
@@ -73,6 +74,15 @@ struct ng_ctx {
     size_t ws_usrc_bytes = 0;
     void* ws_adj = nullptr;          // adjoint: iterate store, work vectors, start-slice buffers
     size_t ws_adj_bytes = 0;
+    // tuned bulk block sizes of earlier batches, by batch shape (problems per nf, largest
+    // ntau, largest nt in steps of 256)
+    std::vector<std::pair<std::vector<int>, int>> tune_cache;
+    int tvsrc = NG_TVSRC_AUTO;       // evaluation of the left-mixing Matsubara source
+    void* ws_tvq = nullptr;          // FFT correlation of the source, [m][a][b][kb]
+    size_t ws_tvq_bytes = 0;
+    void* ws_tw = nullptr;           // twiddle table of length tw_L
+    size_t ws_tw_bytes = 0;
+    int tw_L = 0;
 };
 
 namespace {
@@ -202,12 +212,21 @@ long prof_pair(ng_ctx* c, int kind) {
 }
 
 // algorithmic complex block multiply-adds of one bulk launch at step n (history and source
-// sums of the three bulk tasks; the BDF terms and the per-item matrix inverse are not counted)
-double bulk_cmacs(const Grid& g, int n) {
+// sums of the three bulk tasks; the BDF terms and the per-item matrix inverse are not counted).
+// fft: the left-mixing source comes from the FFT pre-pass, the bulk items add only the
+// quadrature corrections (q_tv_fft).
+double bulk_cmacs(const Grid& g, int n, bool fft = false) {
     const int k = g.k, T = g.ntau;
+    auto corr = [&](int L) {   // correction terms of one piece with row length L
+        return L <= k ? (k + 1) * (k + 1) + L + 1 : (L <= 2 * k + 1 ? L + 1 : 2 * (k + 1));
+    };
     double per_tv = 0.0;
     for (int m = 0; m <= T; ++m) {
         per_tv += n;                                              // history j = 0..n-1
+        if (fft) {
+            per_tv += corr(m) + corr(T - m);
+            continue;
+        }
         per_tv += (m <= k) ? (k + 1) * (k + 1) : (m + 1);         // C^tv_2
         per_tv += (m >= T - k) ? (k + 1) * (k + 1) : (T - m + 1); // C^tv_3
     }
@@ -230,6 +249,32 @@ ng_status launch_minv(ng_ctx* c, const Grid& g, int n, const HermV& S, const Fun
     return check_launch(c, "k_minv_step");
 }
 
+// FFT pre-pass of the left-mixing source of step n (*tvq = nullptr when the direct sums are
+// used: NG_TVSRC_DIRECT, or nf / ntau outside what the transforms support)
+ng_status prep_tvfft(ng_ctx* c, const Grid& g, int n, const HermV& G, const HermV& S, cudaStream_t s,
+                     const cplx** tvq) {
+    *tvq = nullptr;
+    if (c->tvsrc == NG_TVSRC_DIRECT || !tvfft_supported(g.nf, g.ntau)) return NG_OK;
+    ng_status st;
+    const int L = tvfft_length(g.ntau);
+    if (c->tw_L != L) {
+        if ((st = ensure(c, &c->ws_tw, &c->ws_tw_bytes, sizeof(cplx) * (size_t)(L / 2)))) return st;
+        if (tvfft_twiddles((cplx*)c->ws_tw, L, s) != cudaSuccess) return check_launch(c, "k_twiddle");
+        c->tw_L = L;
+    }
+    const size_t need = sizeof(cplx) * (size_t)(g.ntau + 1) * g.nf * g.nf * g.nb;
+    if ((st = ensure(c, &c->ws_tvq, &c->ws_tvq_bytes, need))) return st;
+    long e = prof_pair(c, 2);
+    if (e >= 0) cudaEventRecord(c->ev_pool[e], s);
+    if (tvfft_launch(g, n, S.tv, G.mat, (const cplx*)c->ws_tw, (cplx*)c->ws_tvq, s) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, NG_ECUDA, "launch of k_tvsrc_fft failed");
+    }
+    if (e >= 0) cudaEventRecord(c->ev_pool[e + 1], s);
+    *tvq = (const cplx*)c->ws_tvq;
+    return NG_OK;
+}
+
 template <int D>
 ng_status launch_timestep(ng_ctx* c, const Grid& g, int n, const HermV& G, const HermV& S, const FuncV& eps,
                           cudaStream_t s) {
@@ -238,17 +283,19 @@ ng_status launch_timestep(ng_ctx* c, const Grid& g, int n, const HermV& G, const
     const int64_t it_tv = (int64_t)g.nb * (g.ntau + 1);
     const int64_t it_ret = (int64_t)g.nb * (n - k);
     const int b_les = (int)nblocks(it_les, thr), b_tv = (int)nblocks(it_tv, thr), b_ret = (int)nblocks(it_ret, thr);
+    const cplx* tvq = nullptr;
+    ng_status sm = prep_tvfft(c, g, n, G, S, s, &tvq);
+    if (sm) return sm;
     long e0 = prof_pair(c, 0);
     if (e0 >= 0) cudaEventRecord(c->ev_pool[e0], s);
-    ng_status sm = launch_minv<D>(c, g, n, S, eps, s);
-    if (sm) return sm;
+    if ((sm = launch_minv<D>(c, g, n, S, eps, s))) return sm;
     k_step_bulk<D><<<b_les + b_tv + b_ret, thr, 0, s>>>(g, n, G, S, eps, (const cplx*)c->ws_minv, b_les, b_tv, b_ret,
-                                                        c->d_status);
+                                                        tvq, c->d_status);
     ng_status st = check_launch(c, "k_step_bulk");
     if (st) return st;
     if (e0 >= 0) {
         cudaEventRecord(c->ev_pool[e0 + 1], s);
-        c->prof_flops += 8.0 * D * D * D * bulk_cmacs(g, n);
+        c->prof_flops += 8.0 * D * D * D * bulk_cmacs(g, n, tvq != nullptr);
     }
     long e1 = prof_pair(c, 1);
     if (e1 >= 0) cudaEventRecord(c->ev_pool[e1], s);
@@ -341,14 +388,16 @@ ng_status launch_timestepdf(ng_ctx* c, const Grid& g, int n, const HermV& G, con
     const int64_t it_ret = (int64_t)g.nb * (n - k);
     const int b_les = (int)nblocks(it_les, thr), b_tv = (int)nblocks(it_tv, thr), b_ret = (int)nblocks(it_ret, thr);
     if ((st = launch_minv<D>(c, g, n, S, eps, s))) return st;
+    const cplx* tvq = nullptr;
+    if ((st = prep_tvfft(c, g, n, G, S, s, &tvq))) return st;
     long e0 = prof_pair(c, 0);
     if (e0 >= 0) cudaEventRecord(c->ev_pool[e0], s);
-    k_step_bulkdf<D><<<b_les + b_tv + b_ret, thr, 0, s>>>(g, n, G, c->dfG.v, c->dfS.v, (const cplx*)c->ws_minv, b_les,
-                                                          b_tv, b_ret, c->d_status);
+    k_step_bulkdf<D><<<b_les + b_tv + b_ret, thr, 0, s>>>(g, n, G, S, c->dfG.v, c->dfS.v, (const cplx*)c->ws_minv,
+                                                          b_les, b_tv, b_ret, tvq, c->d_status);
     if ((st = check_launch(c, "k_step_bulkdf"))) return st;
     if (e0 >= 0) {
         cudaEventRecord(c->ev_pool[e0 + 1], s);
-        c->prof_flops += 8.0 * D * D * D * bulk_cmacs(g, n);
+        c->prof_flops += 8.0 * D * D * D * bulk_cmacs(g, n, tvq != nullptr);
     }
     long e1 = prof_pair(c, 1);
     if (e1 >= 0) cudaEventRecord(c->ev_pool[e1], s);
@@ -368,16 +417,27 @@ ng_status launch_timestep32(ng_ctx* c, const Grid& g, int n, const HermV& G, con
     const int64_t it_tv = (int64_t)g.nb * (g.ntau + 1);
     const int64_t it_ret = (int64_t)g.nb * (n - k);
     const int b_les = (int)nblocks(it_les, thr), b_tv = (int)nblocks(it_tv, thr), b_ret = (int)nblocks(it_ret, thr);
+    const cplx* tvq = nullptr;
+    if ((st = prep_tvfft(c, g, n, G, S, s, &tvq))) return st;
     long e0 = prof_pair(c, 0);
     if (e0 >= 0) cudaEventRecord(c->ev_pool[e0], s);
     if ((st = launch_minv<D>(c, g, n, S, eps, s))) return st;
-    k_step_bulk32<D><<<b_les + b_tv + b_ret, thr, 0, s>>>(g, n, G, S, c->shG.v, c->shS.v, eps,
-                                                          (const cplx*)c->ws_minv, b_les, b_tv, b_ret,
-                                                          c->d_status);
+    if (D == 1 && g.nb % 2 == 0) {
+        // two problems per thread (16-byte loads of the FP32 copies)
+        const int np = g.nb / 2;
+        const int p_les = it_les ? (int)nblocks((int64_t)np * (n - k - 1), thr) : 0;
+        const int p_tv = (int)nblocks((int64_t)np * (g.ntau + 1), thr), p_ret = (int)nblocks((int64_t)np * (n - k), thr);
+        k_step_bulk32p<<<p_les + p_tv + p_ret, thr, 0, s>>>(g, n, G, S, c->shG.v, c->shS.v, (const cplx*)c->ws_minv,
+                                                            p_les, p_tv, p_ret, tvq, c->d_status);
+    } else {
+        k_step_bulk32<D><<<b_les + b_tv + b_ret, thr, 0, s>>>(g, n, G, S, c->shG.v, c->shS.v, eps,
+                                                              (const cplx*)c->ws_minv, b_les, b_tv, b_ret, tvq,
+                                                              c->d_status);
+    }
     if ((st = check_launch(c, "k_step_bulk32"))) return st;
     if (e0 >= 0) {
         cudaEventRecord(c->ev_pool[e0 + 1], s);
-        c->prof_flops += 8.0 * D * D * D * bulk_cmacs(g, n);
+        c->prof_flops += 8.0 * D * D * D * bulk_cmacs(g, n, tvq != nullptr);
     }
     long e1 = prof_pair(c, 1);
     if (e1 >= 0) cudaEventRecord(c->ev_pool[e1], s);
@@ -662,7 +722,9 @@ ng_status launch_timestep_serial(ng_ctx* c, const Grid& g, int n, const HermV& G
     const int b_tv = (int)nblocks((int64_t)g.nb * (g.ntau + 1), thr);
     ng_status st = launch_minv<D>(c, g, n, S, eps, s);
     if (st) return st;
-    k_step_bulk<D><<<b_tv, thr, 0, s>>>(g, n, G, S, eps, (const cplx*)c->ws_minv, 0, b_tv, 0, c->d_status);
+    const cplx* tvq = nullptr;
+    if ((st = prep_tvfft(c, g, n, G, S, s, &tvq))) return st;
+    k_step_bulk<D><<<b_tv, thr, 0, s>>>(g, n, G, S, eps, (const cplx*)c->ws_minv, 0, b_tv, 0, tvq, c->d_status);
     if ((st = check_launch(c, "k_step_bulk"))) return st;
     k_step_serial<D><<<g.nb, NG_BND_THREADS, 0, s>>>(g, n, G, S, eps, c->d_status);
     return check_launch(c, "k_step_serial");
@@ -776,6 +838,8 @@ void ng_destroy(ng_ctx* c) {
     cudaFree(c->ws_minv);
     cudaFree(c->ws_adj);
     cudaFree(c->ws_usrc);
+    cudaFree(c->ws_tvq);
+    cudaFree(c->ws_tw);
     delete c;
 }
 
@@ -792,6 +856,13 @@ ng_status ng_status_sync(ng_ctx* c, void* stream, int* flags) {
     return NG_OK;
 }
 
+ng_status ng_set_tv_source(ng_ctx* c, int mode) {
+    if (!c) return NG_EINVAL;
+    if (mode != NG_TVSRC_AUTO && mode != NG_TVSRC_DIRECT) return fail(c, NG_EINVAL, "unknown source mode %d", mode);
+    c->tvsrc = mode;
+    return NG_OK;
+}
+
 ng_status ng_profile_enable(ng_ctx* c, int enable) {
     if (!c) return NG_EINVAL;
     if (enable) {
@@ -805,13 +876,14 @@ ng_status ng_profile_enable(ng_ctx* c, int enable) {
 
 ng_status ng_profile_read(ng_ctx* c, double* out) {
     if (!c || !out) return NG_EINVAL;
-    for (int i = 0; i < 5; ++i) out[i] = 0.0;
+    for (int i = 0; i < 7; ++i) out[i] = 0.0;
     if (c->ev_used) CUDA_TRY(c, cudaEventSynchronize(c->ev_pool[c->ev_used - 1]));
     for (size_t p = 0; p < c->ev_kind.size(); ++p) {
         float ms = 0.f;
         CUDA_TRY(c, cudaEventElapsedTime(&ms, c->ev_pool[2 * p], c->ev_pool[2 * p + 1]));
-        if (c->ev_kind[p] == 0) { out[0] += ms; out[1] += 1; }
-        else { out[3] += ms; out[4] += 1; }
+        const int kind = c->ev_kind[p];
+        out[kind == 0 ? 0 : (kind == 1 ? 3 : 5)] += ms;
+        out[kind == 0 ? 1 : (kind == 1 ? 4 : 6)] += 1;
     }
     out[2] = c->prof_flops;
     return NG_OK;
@@ -1571,8 +1643,18 @@ ng_status ng_batch_solve(ng_ctx* c, ng_batch* b, int* tuned_threads, void* strea
         ntmax = std::max(ntmax, u.nt);
         ntmin = std::min(ntmin, u.nt);
     }
-    // autotune the bulk block size once, on a representative step (re-running a step is
-    // idempotent: slice n is recomputed from slices < n)
+    // autotune the bulk block size once per batch shape and context, on a representative step
+    // (re-running a step is idempotent: slice n is recomputed from slices < n)
+    std::vector<int> key(6, 0);
+    for (const UHost& u : b->info) {
+        key[u.D == 1 ? 0 : u.D == 2 ? 1 : u.D == 4 ? 2 : 3] += 1;
+        key[4] = std::max(key[4], u.ntau);
+        key[5] = std::max(key[5], (u.nt + 255) / 256);
+    }
+    if (b->threads == 0)
+        for (const auto& e : c->tune_cache)
+            if (e.first == key) b->threads = e.second;
+    const bool tune = b->threads == 0;
     const int n_tune = std::max(2 * kmin + 2, ntmin / 2);
     for (int n = kmin + 1; n <= ntmax; ++n) {
         if (n == n_tune && b->threads == 0) {
@@ -1600,6 +1682,7 @@ ng_status ng_batch_solve(ng_ctx* c, ng_batch* b, int* tuned_threads, void* strea
         }
         if ((st = ng_batch_step(c, b, n, 0, stream))) return st;
     }
+    if (tune && b->threads) c->tune_cache.push_back({key, b->threads});
     if (tuned_threads) *tuned_threads = b->threads;
     return NG_OK;
 }

@@ -95,6 +95,55 @@ __device__ Mat<D> q_tv(const NgWeights& W, const Grid& g, const HermV& G, const 
     return mscal<D>(g.htau, mmuli<D>(mscal<D>(-1.0, madd<D>(c2, c3))));
 }
 
+// The same source from the unit-weight correlation F(m) of the FFT pre-pass (ng_tvfft.cu):
+// q(m) = -i h_tau [F(m) + the difference between the quadrature of Eqs. ctv2, ctv3 and unit
+// weights], i.e. (w - 1) terms at the Gregory ends of each piece (rows longer than 2k+1), every
+// term of short rows, and the boundary (R) formulas minus their unit-weight sums for m <= k and
+// m >= ntau - k.  Q: [m][a][b][kb] with ldk = nb.
+template <int D>
+__device__ Mat<D> q_tv_fft(const NgWeights& W, const Grid& g, const HermV& G, const HermV& S, int n, int m, int kb,
+                           const cplx* Q) {
+    const int k = W.k, T = g.ntau;
+    const double xi = (double)g.sig;
+    Mat<D> c2 = mzero<D>(), c3 = mzero<D>();   // corrections, C2 without its factor xi
+    // C2: sum_l w_{m,l} S(m-l) G^M(T-l)
+    auto t2 = [&](int l, double dw) { mfma<D>(c2, mscal<D>(dw, gtv<D>(S, g, n, m - l, kb)), gmat<D>(G, T - l, kb)); };
+    if (m <= k) {
+        for (int j = 0; j <= k; ++j) {
+            Mat<D> gm = gmat<D>(G, T - j, kb);
+            for (int l = 0; l <= k; ++l) mfma<D>(c2, mscal<D>(W.R[m][j][l], gtv<D>(S, g, n, l, kb)), gm);
+        }
+        for (int l = 0; l <= m; ++l) t2(l, -1.0);
+    } else if (m <= 2 * k + 1) {
+        for (int l = 0; l <= m; ++l) t2(l, W.greg[m][l] - 1.0);
+    } else {
+        for (int l = 0; l <= k; ++l) t2(l, W.omega[l] - 1.0);
+        for (int l = m - k; l <= m; ++l) t2(l, W.omega[m - l] - 1.0);
+    }
+    // C3: sum_l w_{T-m,l} S(m+l) G^M(l)
+    const int L3 = T - m;
+    auto t3 = [&](int l, double dw) { mfma<D>(c3, mscal<D>(dw, gtv<D>(S, g, n, m + l, kb)), gmat<D>(G, l, kb)); };
+    if (L3 <= k) {
+        for (int j = 0; j <= k; ++j) {
+            Mat<D> gm = gmat<D>(G, j, kb);
+            for (int l = 0; l <= k; ++l) mfma<D>(c3, mscal<D>(W.R[L3][j][l], gtv<D>(S, g, n, T - l, kb)), gm);
+        }
+        for (int l = 0; l <= L3; ++l) t3(l, -1.0);
+    } else if (L3 <= 2 * k + 1) {
+        for (int l = 0; l <= L3; ++l) t3(l, W.greg[L3][l] - 1.0);
+    } else {
+        for (int l = 0; l <= k; ++l) t3(l, W.omega[l] - 1.0);
+        for (int l = L3 - k; l <= L3; ++l) t3(l, W.omega[L3 - l] - 1.0);
+    }
+    Mat<D> F;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = 0; b < D; ++b) F.v[a][b] = Q[((int64_t)m * (D * D) + a * D + b) * g.nb + kb];
+    Mat<D> v = madd<D>(F, madd<D>(mscal<D>(xi, c2), c3));
+    return mscal<D>(g.htau, mmuli<D>(mscal<D>(-1.0, v)));
+}
+
 // Partial sums of the (A)-source of the lesser column, -i (C^<_2 + C^<_3)[Sigma,1,G](m,n)
 // (Eqs. cles2, cles3), over the terms j = j0, j0+js, ...  (j0 = 0, js = 1 for the full sum).
 template <int D>
@@ -137,14 +186,14 @@ __device__ __forceinline__ void ret_item(const NgWeights& W, const Grid& g, cons
 
 template <int D>
 __device__ __forceinline__ void tv_item(const NgWeights& W, const Grid& g, const HermV& G, const HermV& S,
-                                        const Mat<D>& Minv, int n, int m, int kb, int* status) {
+                                        const Mat<D>& Minv, int n, int m, int kb, const cplx* tvq, int* status) {
     Mat<D> acc = mzero<D>();
     greg_for(W, n, n - 1, [&](int j, double w) {
         mfma<D>(acc, mscal<D>(w, gret<D>(S, n, j, kb)), gtv<D>(G, g, j, m, kb));
     });
     Mat<D> bdf = mzero<D>();
     for (int l = 1; l <= W.k; ++l) bdf = madd<D>(bdf, mscal<D>(W.a[l], gtv<D>(G, g, n - l, m, kb)));
-    Mat<D> rhs = q_tv<D>(W, g, G, S, n, m, kb);
+    Mat<D> rhs = tvq ? q_tv_fft<D>(W, g, G, S, n, m, kb, tvq) : q_tv<D>(W, g, G, S, n, m, kb);
     rhs = msub<D>(rhs, mscal<D>(1.0 / g.h, bdf));
     rhs = msub<D>(rhs, mscal<D>(g.h, mmuli<D>(acc)));
     Mat<D> y = mmul<D>(Minv, rhs);
@@ -219,9 +268,10 @@ __device__ __forceinline__ Mat<D> ld_minv(const cplx* minv_ws, int kb) {
     return r;
 }
 
+// tvq: the FFT pre-pass's correlation of the left-mixing source (nullptr: direct sums)
 template <int D>
-__global__ void __launch_bounds__(128) k_step_bulk(Grid g, int n, HermV G, HermV S, FuncV eps, const cplx* minv_ws,
-                                                   int nb_les, int nb_tv, int nb_ret, int* status) {
+__global__ void __launch_bounds__(128, D == 1 ? 6 : 1) k_step_bulk(Grid g, int n, HermV G, HermV S, FuncV eps, const cplx* minv_ws,
+                                                   int nb_les, int nb_tv, int nb_ret, const cplx* tvq, int* status) {
     const NgWeights& W = c_W[g.k - 1];
     int blk = blockIdx.x;
     int task;
@@ -238,7 +288,7 @@ __global__ void __launch_bounds__(128) k_step_bulk(Grid g, int n, HermV G, HermV
     if (col >= ncol) return;
     const Mat<D> Minv = ld_minv<D>(minv_ws, kb);
     if (task == 0) les_item<D>(W, g, G, S, Minv, n, (int)col + 1, kb, status);
-    else if (task == 1) tv_item<D>(W, g, G, S, Minv, n, (int)col, kb, status);
+    else if (task == 1) tv_item<D>(W, g, G, S, Minv, n, (int)col, kb, tvq, status);
     else ret_item<D>(W, g, G, S, Minv, n, (int)col, kb, status);
 }
 

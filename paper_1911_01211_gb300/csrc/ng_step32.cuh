@@ -173,7 +173,7 @@ __device__ __forceinline__ void ret_item32(const NgWeights& W, const Grid& g, co
 template <int D>
 __device__ __forceinline__ void tv_item32(const NgWeights& W, const Grid& g, const HermV& G, const HermV& S,
                                           const HermV32& G32, const HermV32& S32, const Mat<D>& Minv, int n,
-                                          int m, int kb, int* status) {
+                                          int m, int kb, const cplx* tvq, int* status) {
     KMat<D> acc = kzero<D>();
     const int64_t rowS = tri(n);
     const int T1 = g.ntau + 1;
@@ -182,7 +182,7 @@ __device__ __forceinline__ void tv_item32(const NgWeights& W, const Grid& g, con
     });
     Mat<D> bdf = mzero<D>();
     for (int l = 1; l <= W.k; ++l) bdf = madd<D>(bdf, mscal<D>(W.a[l], gtv<D>(G, g, n - l, m, kb)));
-    Mat<D> rhs = q_tv32<D>(W, g, G32, S32, n, m, kb);
+    Mat<D> rhs = tvq ? q_tv_fft<D>(W, g, G, S, n, m, kb, tvq) : q_tv32<D>(W, g, G32, S32, n, m, kb);
     rhs = msub<D>(rhs, mscal<D>(1.0 / g.h, bdf));
     rhs = msub<D>(rhs, mscal<D>(g.h, mmuli<D>(kval<D>(acc))));
     Mat<D> y = mmul<D>(Minv, rhs);
@@ -232,7 +232,7 @@ __device__ __forceinline__ void les_item32(const NgWeights& W, const Grid& g, co
 template <int D>
 __global__ void __launch_bounds__(128) k_step_bulk32(Grid g, int n, HermV G, HermV S, HermV32 G32, HermV32 S32,
                                                      FuncV eps, const cplx* minv_ws, int nb_les, int nb_tv,
-                                                     int nb_ret, int* status) {
+                                                     int nb_ret, const cplx* tvq, int* status) {
     const NgWeights& W = c_W[g.k - 1];
     int blk = blockIdx.x;
     int task;
@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(128) k_step_bulk32(Grid g, int n, HermV G, Her
     if (col >= ncol) return;
     const Mat<D> Minv = ld_minv<D>(minv_ws, kb);
     if (task == 0) les_item32<D>(W, g, G, S, G32, S32, Minv, n, (int)col + 1, kb, status);
-    else if (task == 1) tv_item32<D>(W, g, G, S, G32, S32, Minv, n, (int)col, kb, status);
+    else if (task == 1) tv_item32<D>(W, g, G, S, G32, S32, Minv, n, (int)col, kb, tvq, status);
     else ret_item32<D>(W, g, G, S, G32, S32, Minv, n, (int)col, kb, status);
 }
 
@@ -278,4 +278,169 @@ __global__ void k_shadow(Grid g, int n0, int n1, HermV X, HermV32 Y, int ldk) {
         const cplx v = src[off];
         dst[off] = make_float2((float)v.x, (float)v.y);
     }
+}
+
+// ----------------------------------------------------------------------------------------
+// nf = 1 with two adjacent problems per thread: every history element of the pair is one
+// 16-byte load (the FP32 copies keep the problem index innermost), and the two problems'
+// compensated sums are independent chains, so each thread keeps twice the bytes and the
+// arithmetic in flight.  Same formulas, order of terms and rounding as the one-problem items.
+// Needs nb even (then every pair offset is 16-byte aligned).
+// ----------------------------------------------------------------------------------------
+struct P32 {
+    float2 a, b;   // problems kb, kb+1
+};
+__device__ __forceinline__ P32 ldp(const Comp32& c, int64_t e, int kb) {
+    if (c.ldk == 1) {
+        const float2 v = c.p[e];
+        return P32{v, v};
+    }
+    const float4 v = *reinterpret_cast<const float4*>(c.p + e * c.ldk + kb);
+    return P32{make_float2(v.x, v.y), make_float2(v.z, v.w)};
+}
+__device__ __forceinline__ P32 pscal(float w, P32 x) {
+    x.a.x *= w, x.a.y *= w, x.b.x *= w, x.b.y *= w;
+    return x;
+}
+__device__ __forceinline__ P32 pndag(P32 x) {   // -conj, per problem
+    x.a.x = -x.a.x, x.b.x = -x.b.x;
+    return x;
+}
+struct KP {
+    KSum re[2], im[2];
+};
+__device__ __forceinline__ KP kpzero() {
+    KP r;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) r.re[i] = KSum{0.f, 0.f}, r.im[i] = KSum{0.f, 0.f};
+    return r;
+}
+__device__ __forceinline__ void kcadd(KSum& re, KSum& im, float2 x, float2 y) {   // += x y
+    kadd(re, x.x, y.x);
+    kadd(re, -x.y, y.y);
+    kadd(im, x.x, y.y);
+    kadd(im, x.y, y.x);
+}
+__device__ __forceinline__ void kcadd_db(KSum& re, KSum& im, float2 x, float2 y) {   // += x conj(y)
+    kadd(re, x.x, y.x);
+    kadd(re, x.y, y.y);
+    kadd(im, -x.x, y.y);
+    kadd(im, x.y, y.x);
+}
+__device__ __forceinline__ void kpfma(KP& k, const P32& x, const P32& y) {
+    kcadd(k.re[0], k.im[0], x.a, y.a);
+    kcadd(k.re[1], k.im[1], x.b, y.b);
+}
+__device__ __forceinline__ void kpfma_db(KP& k, const P32& x, const P32& y) {
+    kcadd_db(k.re[0], k.im[0], x.a, y.a);
+    kcadd_db(k.re[1], k.im[1], x.b, y.b);
+}
+__device__ __forceinline__ Mat<1> kpval(const KP& k, int i) {
+    Mat<1> r;
+    r.v[0][0] = make_double2((double)k.re[i].s - (double)k.re[i].c, (double)k.im[i].s - (double)k.im[i].c);
+    return r;
+}
+
+__device__ __forceinline__ void ret_item32p(const NgWeights& W, const Grid& g, const HermV& G, const HermV32& G32,
+                                            const HermV32& S32, const cplx* minv_ws, int n, int m, int kb,
+                                            int* status) {
+    const int L = n - m;
+    KP acc = kpzero();
+    const int64_t rowS = tri(n);
+    greg_for(W, L, L - 1, [&](int l, double w) {
+        kpfma(acc, pscal((float)w, ldp(S32.ret, rowS + m + l, kb)), ldp(G32.ret, tri(m + l) + m, kb));
+    });
+    for (int i = 0; i < 2; ++i) {
+        Mat<1> bdf = mzero<1>();
+        for (int l = 1; l <= W.k; ++l) bdf = madd<1>(bdf, mscal<1>(W.a[l], gret<1>(G, n - l, m, kb + i)));
+        Mat<1> rhs = msub<1>(mscal<1>(-1.0 / g.h, bdf), mscal<1>(g.h, mmuli<1>(kpval(acc, i))));
+        Mat<1> y = mmul<1>(ld_minv<1>(minv_ws, kb + i), rhs);
+        if (!mfinite<1>(y)) atomicOr(status, NGF_NONFINITE);
+        st<1>(G.ret, tri(n) + m, kb + i, y);
+    }
+}
+
+__device__ __forceinline__ void tv_item32p(const NgWeights& W, const Grid& g, const HermV& G, const HermV& S,
+                                           const HermV32& G32, const HermV32& S32, const cplx* minv_ws, int n, int m,
+                                           int kb, const cplx* tvq, int* status) {
+    KP acc = kpzero();
+    const int64_t rowS = tri(n);
+    const int T1 = g.ntau + 1;
+    greg_for(W, n, n - 1, [&](int j, double w) {
+        kpfma(acc, pscal((float)w, ldp(S32.ret, rowS + j, kb)), ldp(G32.tv, (int64_t)j * T1 + m, kb));
+    });
+    for (int i = 0; i < 2; ++i) {
+        Mat<1> bdf = mzero<1>();
+        for (int l = 1; l <= W.k; ++l) bdf = madd<1>(bdf, mscal<1>(W.a[l], gtv<1>(G, g, n - l, m, kb + i)));
+        Mat<1> rhs = tvq ? q_tv_fft<1>(W, g, G, S, n, m, kb + i, tvq) : q_tv32<1>(W, g, G32, S32, n, m, kb + i);
+        rhs = msub<1>(rhs, mscal<1>(1.0 / g.h, bdf));
+        rhs = msub<1>(rhs, mscal<1>(g.h, mmuli<1>(kpval(acc, i))));
+        Mat<1> y = mmul<1>(ld_minv<1>(minv_ws, kb + i), rhs);
+        if (!mfinite<1>(y)) atomicOr(status, NGF_NONFINITE);
+        st<1>(G.tv, (int64_t)n * T1 + m, kb + i, y);
+    }
+}
+
+__device__ __forceinline__ void les_item32p(const NgWeights& W, const Grid& g, const HermV& G, const HermV32& G32,
+                                            const HermV32& S32, const cplx* minv_ws, int n, int m, int kb,
+                                            int* status) {
+    const int k = W.k, T = g.ntau, T1 = g.ntau + 1;
+    const int64_t colS = tri(n);
+    KP c1 = kpzero();
+    if (m <= k) {
+        for (int j = 0; j <= k; ++j) {
+            P32 gr = (j <= m) ? ldp(G32.ret, tri(m) + j, kb) : pndag(ldp(G32.ret, tri(j) + m, kb));
+            kpfma(c1, pscal((float)W.greg[m][j], gr), ldp(S32.les, colS + j, kb));
+        }
+    } else {
+        const int64_t rowG = tri(m);
+        greg_for(W, m, m, [&](int j, double w) {
+            kpfma(c1, pscal((float)w, ldp(G32.ret, rowG + j, kb)), ldp(S32.les, colS + j, kb));
+        });
+    }
+    KP c3 = kpzero();
+    const int64_t rowGt = (int64_t)m * T1, rowSt = (int64_t)n * T1;
+    greg_for(W, T, T, [&](int j, double w) {
+        kpfma_db(c3, pscal((float)w, ldp(G32.tv, rowGt + j, kb)), ldp(S32.tv, rowSt + T - j, kb));
+    });
+    KP hist = kpzero();
+    const int64_t rowS = tri(n), colM = tri(m);
+    greg_for(W, n, n - 1, [&](int l, double w) {
+        P32 gl = (l >= m) ? ldp(G32.les, tri(l) + m, kb) : pndag(ldp(G32.les, colM + l, kb));
+        kpfma_db(hist, pscal((float)w, gl), ldp(S32.ret, rowS + l, kb));
+    });
+    for (int i = 0; i < 2; ++i) {
+        Mat<1> q = msub<1>(mscal<1>(g.h, mmuli<1>(kpval(c1, i))), mscal<1>((double)g.sig * g.htau, kpval(c3, i)));
+        Mat<1> bdf = mzero<1>();
+        for (int l = 1; l <= k; ++l) bdf = madd<1>(bdf, mscal<1>(W.a[l], ld<1>(G.les, tri(n - l) + m, kb + i)));
+        Mat<1> rhs = msub<1>(q, mscal<1>(1.0 / g.h, bdf));
+        rhs = madd<1>(rhs, mscal<1>(g.h, mmuli<1>(kpval(hist, i))));
+        Mat<1> y = mmul<1>(rhs, mdag<1>(ld_minv<1>(minv_ws, kb + i)));
+        if (!mfinite<1>(y)) atomicOr(status, NGF_NONFINITE);
+        st<1>(G.les, tri(n) + m, kb + i, y);
+    }
+}
+
+// nf = 1, nb even: items are (column, problem pair), pair index fastest
+__global__ void __launch_bounds__(128, 8) k_step_bulk32p(Grid g, int n, HermV G, HermV S, HermV32 G32, HermV32 S32,
+                                                      const cplx* minv_ws, int nb_les, int nb_tv, int nb_ret,
+                                                      const cplx* tvq, int* status) {
+    const NgWeights& W = c_W[g.k - 1];
+    int blk = blockIdx.x;
+    int task;
+    if (blk < nb_les) task = 0;
+    else if ((blk -= nb_les) < nb_tv) task = 1;
+    else { blk -= nb_tv; task = 2; }
+    const int np = g.nb >> 1;
+    const int64_t item = (int64_t)blk * blockDim.x + threadIdx.x;
+    const int kb = 2 * (int)(item % np);
+    const int64_t col = item / np;
+    int ncol;
+    if (task == 0) ncol = n - W.k - 1;
+    else if (task == 1) ncol = g.ntau + 1;
+    else ncol = n - W.k;
+    if (col >= ncol) return;
+    if (task == 0) les_item32p(W, g, G, G32, S32, minv_ws, n, (int)col + 1, kb, status);
+    else if (task == 1) tv_item32p(W, g, G, S, G32, S32, minv_ws, n, (int)col, kb, tvq, status);
+    else ret_item32p(W, g, G, G32, S32, minv_ws, n, (int)col, kb, status);
 }

@@ -197,8 +197,9 @@ __device__ __forceinline__ void ret_itemdf(const NgWeights& W, const Grid& g, co
 }
 
 template <int D>
-__device__ __forceinline__ void tv_itemdf(const NgWeights& W, const Grid& g, const HermV& G, const HermVdf& Gd,
-                                          const HermVdf& Sd, const Mat<D>& Minv, int n, int m, int kb, int* status) {
+__device__ __forceinline__ void tv_itemdf(const NgWeights& W, const Grid& g, const HermV& G, const HermV& S,
+                                          const HermVdf& Gd, const HermVdf& Sd, const Mat<D>& Minv, int n, int m,
+                                          int kb, const cplx* tvq, int* status) {
     DMat<D> acc = dzero<D>();
     const int64_t rowS = tri(n);
     const int T1 = g.ntau + 1;
@@ -207,7 +208,7 @@ __device__ __forceinline__ void tv_itemdf(const NgWeights& W, const Grid& g, con
     });
     Mat<D> bdf = mzero<D>();
     for (int l = 1; l <= W.k; ++l) bdf = madd<D>(bdf, mscal<D>(W.a[l], gtv<D>(G, g, n - l, m, kb)));
-    Mat<D> rhs = q_tvdf<D>(W, g, Gd, Sd, n, m, kb);
+    Mat<D> rhs = tvq ? q_tv_fft<D>(W, g, G, S, n, m, kb, tvq) : q_tvdf<D>(W, g, Gd, Sd, n, m, kb);
     rhs = msub<D>(rhs, mscal<D>(1.0 / g.h, bdf));
     rhs = msub<D>(rhs, mscal<D>(g.h, mmuli<D>(dval<D>(acc))));
     Mat<D> y = mmul<D>(Minv, rhs);
@@ -254,9 +255,9 @@ __device__ __forceinline__ void les_itemdf(const NgWeights& W, const Grid& g, co
 }
 
 template <int D>
-__global__ void __launch_bounds__(128) k_step_bulkdf(Grid g, int n, HermV G, HermVdf Gd, HermVdf Sd,
+__global__ void __launch_bounds__(128, D == 1 ? 6 : 1) k_step_bulkdf(Grid g, int n, HermV G, HermV S, HermVdf Gd, HermVdf Sd,
                                                      const cplx* minv_ws, int nb_les, int nb_tv, int nb_ret,
-                                                     int* status) {
+                                                     const cplx* tvq, int* status) {
     const NgWeights& W = c_W[g.k - 1];
     int blk = blockIdx.x;
     int task;
@@ -273,7 +274,7 @@ __global__ void __launch_bounds__(128) k_step_bulkdf(Grid g, int n, HermV G, Her
     if (col >= ncol) return;
     const Mat<D> Minv = ld_minv<D>(minv_ws, kb);
     if (task == 0) les_itemdf<D>(W, g, G, Gd, Sd, Minv, n, (int)col + 1, kb, status);
-    else if (task == 1) tv_itemdf<D>(W, g, G, Gd, Sd, Minv, n, (int)col, kb, status);
+    else if (task == 1) tv_itemdf<D>(W, g, G, S, Gd, Sd, Minv, n, (int)col, kb, tvq, status);
     else ret_itemdf<D>(W, g, G, Gd, Sd, Minv, n, (int)col, kb, status);
 }
 

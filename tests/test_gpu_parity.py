@@ -122,16 +122,17 @@ def _oracle_problem_set(d, nb, N, T, beta, h, k, seed):
     return W, Gs, Ss, epss
 
 
-@pytest.mark.parametrize("schedule", ["mixed", "serial"])
+@pytest.mark.parametrize("schedule,tvsrc", [("mixed", "auto"), ("mixed", "direct"), ("serial", "auto")])
 @pytest.mark.parametrize("d", [1, 2])
-def test_timestep_from_oracle_history(ng, d, schedule):
+def test_timestep_from_oracle_history(ng, d, schedule, tvsrc):
     """ng_dyson_timestep on the oracle's history reproduces the oracle's step in the same
     schedule for n in {k+1, 2k, 2k+1, 2k+2, N} (all branches of the mixed schedule), with
-    per-problem Sigma."""
+    per-problem Sigma, with the left-mixing source by FFT (auto) and by the direct sums."""
     k, N, T, beta, h, nb = 5, 26, 18, 2.5, 0.06, 3
     W, Gs, Ss, epss = _oracle_problem_set(d, nb, N, T, beta, h, k, seed=11 + d)
     g = ng.Grid(nt=N, ntau=T, nf=d, nbatch=nb, korder=k, h=h, beta=beta)
     ctx = ng.Context(k)
+    ctx.set_tv_source(ng.NG_TVSRC_DIRECT if tvsrc == "direct" else ng.NG_TVSRC_AUTO)
     G, S, eps = ng.Herm(g), ng.Herm(g), ng.Func(g)
     oracle_to_herm(Ss, S, g)
     funcs_to_device(epss, eps)
@@ -150,6 +151,57 @@ def test_timestep_from_oracle_history(ng, d, schedule):
                             ("tv", got.tv[n], ref.tv[n])):
                 e[c] = np.abs(x - y).max() / np.abs(y).max()
             assert max(e.values()) < TOL, (n, kb, e)
+
+
+def _random_history(rng, N, T, d, scale=0.3):
+    X = OHerm(N, T, d)
+    c = lambda *sh: scale * (rng.normal(0, 1, sh) + 1j * rng.normal(0, 1, sh))
+    X.mat[...] = c(T + 1, d, d)
+    X.tv[...] = c(N + 1, T + 1, d, d)
+    low = np.tril(np.ones((N + 1, N + 1), bool))
+    X.ret[low] = c(int(low.sum()), d, d)
+    X.les[low.T] = c(int(low.sum()), d, d)
+    return X
+
+
+@pytest.mark.parametrize("d,T", [(1, 500), (1, 1023), (2, 500)])
+def test_fft_source_at_large_ntau(ng, d, T):
+    """The FFT pre-pass at transform lengths 1024 and 2048 (one step from a seeded random
+    history, two problems with their own Sigma): both source evaluations against the oracle,
+    and against each other at rounding level."""
+    k, N, beta, h, nb = 5, 20, 4.0, 0.05, 2
+    rng = np.random.default_rng(500 + d + T)
+    W = Weights(k)
+    Gs = [_random_history(rng, N, T, d) for _ in range(nb)]
+    Ss = [_random_history(rng, N, T, d, 0.05) for _ in range(nb)]
+    epss = []
+    for _ in range(nb):
+        e = OFunc(N, d)
+        e.val[:] = wl.random_hermitian(rng, d)
+        epss.append(e)
+    g = ng.Grid(nt=N, ntau=T, nf=d, nbatch=nb, korder=k, h=h, beta=beta)
+    ctx = ng.Context(k)
+    S, eps = ng.Herm(g), ng.Func(g)
+    oracle_to_herm(Ss, S, g)
+    funcs_to_device(epss, eps)
+    out = {}
+    for mode in (ng.NG_TVSRC_AUTO, ng.NG_TVSRC_DIRECT):
+        ctx.set_tv_source(mode)
+        for n in (k + 1, 2 * k + 2, N):
+            G = ng.Herm(g)
+            oracle_to_herm(Gs, G, g, nmax=n - 1)
+            ctx.dyson_timestep(g, n, G, S, eps)
+            _status_ok(ctx, ng)
+            out[mode, n] = [herm_to_oracle(G, g, kb).tv[n].copy() for kb in range(nb)]
+            for kb in range(nb):
+                ref = Gs[kb].copy()
+                dyson.dyson_timestep(n, ref, Ss[kb], epss[kb], 0.0, beta, h, W)
+                x, y = out[mode, n][kb], ref.tv[n]
+                assert np.abs(x - y).max() / np.abs(y).max() < TOL, (mode, n, kb)
+    for n in (k + 1, 2 * k + 2, N):
+        for kb in range(nb):
+            a, b = out[ng.NG_TVSRC_AUTO, n][kb], out[ng.NG_TVSRC_DIRECT, n][kb]
+            assert np.abs(a - b).max() / np.abs(b).max() < 1e-13
 
 
 def test_serial_schedule_propagation(ng):
