@@ -401,7 +401,8 @@ ng_status ng_profile_read(ng_ctx *ctx, double *out);
  * sustained FP64 FMA-pipe rate (DFMA, 8 independent chains per thread, 8 blocks of 256 threads
  * per SM) and out[1] = the FP64 tensor rate (DMMA, mma.sync m8n8k4 f64, 4 independent
  * accumulators per warp), both in TFLOP/s (2 flop per multiply-add), out[2] = the SM count.
- * Synchronises `stream`; takes about half a second.  `out` must hold 3 doubles. */
+ * Synchronises `stream`; takes about a second (a warm-up, then the best of three timed launches
+ * of each kernel).  `out` must hold 3 doubles. */
 ng_status ng_fp64_probe(double *out, void *stream);
 
 /* ---- driver --------------------------------------------------------------------------- */
