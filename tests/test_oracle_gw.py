@@ -1,0 +1,184 @@
+"""Pins of the oracle's GW self-energy (oracle/gw.py) by facts independent of its code:
+
+* a free single level (and diagonal levels): P is constant on every component, P^R = 0, so the
+  susceptibility equation has the closed form chi^M = c / (1 - c U(0^-) beta), c = -f(1 - f),
+  chi^< = chi^> = chi^tv = i chi^M, chi^R = 0, and Sigma(t,t') = -U(t) U(t') chi^M G(t,t') on
+  every component, also for a time-dependent U(t);
+* the contour boundary conditions C^tv(0, tau) = i C^M(-tau) and C^<(0,0) = C^tv(0,0) for P and
+  Sigma of a non-diagonal cluster (they tie the Matsubara rule of each bubble to its real-time
+  rules);
+* the expansion in U: Sigma_GW - Sigma_2B = O(U^3), with the U^3 term i G U (P * U * P) U
+  computed by the convolution oracle (pins the sign of the kernel K = -P U of the chi equation);
+* planted errors (the printed sign of the Bubble1 Matsubara rule, a sign of K) fail these pins.
+"""
+import numpy as np
+import pytest
+
+from oracle import bubble, conv, gw
+from oracle.contour import Func, Herm
+from oracle.freegf import fermi, green_from_H
+from oracle.weights import Weights
+
+K = 5
+
+
+def _ufunc(N, u):
+    U = Func(N, 1)
+    for n in range(-1, N + 1):
+        U.set(n, np.array([[u(n)]], complex))
+    return U
+
+
+def _run_gw(G, U, beta, h, W):
+    N, T, d = G.nt, G.ntau, G.d
+    chain = gw.GW(N, T, d, beta, h, W)
+    S = Herm(N, T, d)
+    chain.mat(G, U, S)
+    chain.start(G, U, S)
+    for n in range(W.k + 1, N + 1):
+        chain.step(n, G, U, S)
+    return chain, S
+
+
+def _low(N):
+    return np.tril(np.ones((N + 1, N + 1), bool))
+
+
+@pytest.mark.parametrize("levels", [[0.4], [0.4, -0.7]])
+def test_free_levels_closed_form(levels):
+    N, T, beta, h, U0 = 16, 20, 2.0, 0.05, 0.8
+    W = Weights(K)
+    G = green_from_H(N, T, np.diag(levels), 0.0, beta, h)
+    u = lambda n: U0 if n < 0 else U0 * (1.0 + 0.3 * np.sin(0.7 * n * h))
+    chain, S = _run_gw(G, _ufunc(N, u), beta, h, W)
+    d = len(levels)
+    low = _low(N)
+    for a in range(d):
+        f = fermi(levels[a], beta)
+        c = -f * (1.0 - f)
+        chim = c / (1.0 - c * U0 * beta)
+        chi = chain.chi
+        assert np.abs(chi.mat[:, a, a] - chim).max() < 1e-13
+        assert np.abs(chi.tv[:, :, a, a] - 1j * chim).max() < 1e-13
+        assert np.abs(chi.les[low.T][:, a, a] - 1j * chim).max() < 1e-13
+        assert np.abs(chi.ret[low][:, a, a]).max() < 1e-13
+        us = np.array([u(n) for n in range(N + 1)])
+        assert np.abs(S.mat[:, a, a] + U0 ** 2 * chim * G.mat[:, a, a]).max() < 1e-13
+        for n in range(N + 1):
+            for j in range(n + 1):
+                w = -us[n] * us[j] * chim
+                assert abs(S.ret[n, j, a, a] - w * G.ret[n, j, a, a]) < 1e-13
+                assert abs(S.les[j, n, a, a] - w * G.les[j, n, a, a]) < 1e-13
+            assert np.abs(S.tv[n, :, a, a] + us[n] * U0 * chim * G.tv[n, :, a, a]).max() < 1e-13
+    if d > 1:
+        off = ~np.eye(d, dtype=bool)
+        for X in (chain.chi, S):
+            assert np.abs(X.mat[:, off]).max() < 1e-14
+            assert np.abs(X.tv[:, :, off]).max() < 1e-14
+
+
+def _cluster_G(N, T, beta, h, seed=3):
+    rng = np.random.default_rng(seed)
+    a = rng.normal(0, 1, (2, 2)) + 1j * rng.normal(0, 1, (2, 2))
+    return green_from_H(N, T, 0.5 * (a + a.conj().T), 0.1, beta, h)
+
+
+def test_boundary_conditions_of_P_and_sigma():
+    N, T, beta, h = 12, 24, 1.5, 0.05
+    W = Weights(K)
+    G = _cluster_G(N, T, beta, h)
+    chain, S = _run_gw(G, _ufunc(N, lambda n: 0.6), beta, h, W)
+    P = chain.P
+    for X, xi in ((P, +1), (S, -1), (chain.chi, +1)):
+        # C^tv(0, tau_m) = i C^M(-tau_m) = i xi C^M(beta - tau_m)
+        assert np.abs(X.tv[0] - 1j * xi * X.mat[::-1]).max() < 1e-13 * max(1.0, np.abs(X.mat).max())
+    # C^<(0,0) = C^tv(0,0): exact for P; for chi (so for Sigma) only up to the quadrature error
+    # of the Matsubara solve, whose chi^M(beta) is hermitian to that accuracy
+    assert np.abs(P.les[0, 0] - P.tv[0, 0]).max() < 1e-15
+    assert np.abs(S.les[0, 0] - S.tv[0, 0]).max() < 1e-8
+    # the equal-time bosonic P is anti-hermitian on the lesser component: P^<(t,t)^dagger = -P^<(t,t)
+    for n in range(N + 1):
+        assert np.abs(P.les[n, n] + P.les[n, n].conj().T).max() < 1e-14
+
+
+def _sigma_2b_all(G, U):
+    S = Herm(G.nt, G.ntau, G.d)
+    for n in range(-1, G.nt + 1):
+        bubble.sigma_2b(n, G, U, S)
+    return S
+
+
+def _pp(P, beta, h, W):
+    C = Herm(P.nt, P.ntau, P.d, sig=+1)
+    for n in range(-1, P.nt + 1):
+        conv.convolution_timestep(n, C, P, P, None, P, P, W, beta, h)
+    return C
+
+
+def _flat(X):
+    N = X.nt
+    low = _low(N)
+    return np.concatenate([X.mat.ravel(), X.ret[low].ravel(), X.les[low.T].ravel(), X.tv.ravel()])
+
+
+def _expansion_errors(N, T, beta, h, U0s):
+    W = Weights(K)
+    G = _cluster_G(N, T, beta, h)
+    e2, e3, size3 = [], [], []
+    PP = None
+    for U0 in U0s:
+        U = _ufunc(N, lambda n: U0)
+        chain, S = _run_gw(G, U, beta, h, W)
+        if PP is None:
+            PP = _pp(chain.P, beta, h, W)
+        s2 = _sigma_2b_all(G, U)
+        dW3 = Herm(N, T, G.d, sig=+1)
+        for c in ("mat", "ret", "les", "tv"):
+            setattr(dW3, c, U0 ** 3 * getattr(PP, c))
+        s3 = Herm(N, T, G.d)
+        for n in range(-1, N + 1):
+            gw.bubble2(n, G, dW3, s3)
+        d2 = _flat(S) - _flat(s2)
+        e2.append(np.abs(d2).max())
+        e3.append(np.abs(d2 - _flat(s3)).max())
+        size3.append(np.abs(_flat(s3)).max())
+    return np.array(e2), np.array(e3), np.array(size3)
+
+
+def test_expansion_in_U_matches_second_born_and_third_order():
+    e2, e3, size3 = _expansion_errors(12, 24, 1.5, 0.05, (0.2, 0.1))
+    # Sigma_GW - Sigma_2B is the third-order term up to O(U^4)
+    assert 6.5 < e2[0] / e2[1] < 9.5, e2
+    assert 13.0 < e3[0] / e3[1] < 19.0, e3
+    assert np.all(e3 < 0.25 * size3), (e3, size3)
+
+
+def test_planted_bubble1_matsubara_sign_fails_closed_form(monkeypatch):
+    orig = gw.bubble1
+
+    def printed_sign(n, A, B, C):
+        orig(n, A, B, C)
+        if n == -1:
+            C.mat *= -1.0
+
+    monkeypatch.setattr(gw, "bubble1", printed_sign)
+    with pytest.raises(AssertionError):
+        test_free_levels_closed_form([0.4])
+
+
+def test_planted_kernel_sign_fails_expansion(monkeypatch):
+    orig = gw.GW._kernel
+
+    def flipped(self, n, G, U):
+        orig(self, n, G, U)
+        for X in (self.K, self.Kcc):
+            if n == -1:
+                X.mat *= -1.0
+            else:
+                X.ret[n, :n + 1] *= -1.0
+                X.les[:n + 1, n] *= -1.0
+                X.tv[n] *= -1.0
+
+    monkeypatch.setattr(gw.GW, "_kernel", flipped)
+    with pytest.raises(AssertionError):
+        test_expansion_in_U_matches_second_born_and_third_order()
