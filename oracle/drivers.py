@@ -12,12 +12,17 @@
     3. time stepping n = k+1..N: extrapolate_timestep(n-1), then exactly ``corrector``
        iterations of {G_loc(n), eps^MF_n, Sigma_2B(n), dyson_timestep(n)}.
   A problem with N_k = 1 and d = 2 is the Hubbard dimer in real space.
+* run_gw: the same loop with the GW self-energy of Sec. "Self-energy approximation: GW"
+  (oracle/gw.py) in place of the second-Born one: each Sigma evaluation first builds P, K and
+  K^ddagger on its slices, then solves the susceptibility (vie2_mat in the Matsubara loop,
+  vie2_start over slices 0..k in the bootstrapping, vie2_timestep(n) in each corrector pass),
+  then forms dW and Sigma.
   The second-Born dynamics has no closed form: its parity with the CUDA path is pinned
   only by invariants and by the pinned building blocks (parity partially unpinned).
 """
 import numpy as np
 
-from . import bubble, dyson, extrap
+from . import bubble, dyson, extrap, gw
 from .contour import Func, Herm
 
 
@@ -27,6 +32,24 @@ def solve_fixed_sigma(G, S, eps, mu, beta, h, W, schedule="mixed", nmax=None):
     for n in range(W.k + 1, (G.nt if nmax is None else nmax) + 1):
         dyson.dyson_timestep(n, G, S, eps, mu, beta, h, W, schedule)
     return G
+
+
+class Sigma2B:
+    """Second-Born self-energy slices (Eq. sigma_hubb_2b) for the driver: Matsubara, start-up
+    slices 0..k, one time step."""
+
+    def __init__(self, k):
+        self.k = k
+
+    def mat(self, Gloc, U, S):
+        bubble.sigma_2b(-1, Gloc, U, S)
+
+    def start(self, Gloc, U, S):
+        for n in range(self.k + 1):
+            bubble.sigma_2b(n, Gloc, U, S)
+
+    def step(self, n, Gloc, U, S):
+        bubble.sigma_2b(n, Gloc, U, S)
 
 
 class TwoBState:
@@ -46,11 +69,13 @@ def _update_mf(n, st, eps0, U, nbar):
 
 def run_2b(eps0, U, nt, ntau, beta, h, W, mu=0.0, nbar=0.5, corrector=3, schedule="mixed",
            mats_tol=1e-12, mats_maxiter=200, boot_tol=1e-12, boot_maxiter=200, nmax=None,
-           state=None):
-    """Self-consistent second-Born for the problems with bare Hamiltonians eps0[k] (Funcs)."""
+           state=None, sigma=None):
+    """Self-consistent second-Born (or, with sigma = gw.GW(...), GW) for the problems with bare
+    Hamiltonians eps0[k] (Funcs)."""
     nk = len(eps0)
     d = eps0[0].d
     st = state or TwoBState(nk, nt, ntau, d)
+    sig = sigma or Sigma2B(W.k)
     # ---- Matsubara -------------------------------------------------------------------
     for kk in range(nk):  # initial guess: free G^M of the bare Hamiltonian
         st.epsmf[kk].set(-1, eps0[kk](-1))
@@ -59,7 +84,7 @@ def run_2b(eps0, U, nt, ntau, beta, h, W, mu=0.0, nbar=0.5, corrector=3, schedul
     for it_m in range(mats_maxiter):
         bubble.kreduce(-1, st.G, st.Gloc)
         _update_mf(-1, st, eps0, U, nbar)
-        bubble.sigma_2b(-1, st.Gloc, U, st.S)
+        sig.mat(st.Gloc, U, st.S)
         err = 0.0
         for kk in range(nk):
             old = st.G[kk].mat.copy()
@@ -72,7 +97,7 @@ def run_2b(eps0, U, nt, ntau, beta, h, W, mu=0.0, nbar=0.5, corrector=3, schedul
     st.log["mats_err"] = err
     bubble.kreduce(-1, st.G, st.Gloc)
     _update_mf(-1, st, eps0, U, nbar)
-    bubble.sigma_2b(-1, st.Gloc, U, st.S)
+    sig.mat(st.Gloc, U, st.S)
     # ---- bootstrapping ---------------------------------------------------------------
     k = W.k
     for n in range(k + 1):  # initial guess for slices 0..k: the equilibrium Matsubara state
@@ -85,7 +110,7 @@ def run_2b(eps0, U, nt, ntau, beta, h, W, mu=0.0, nbar=0.5, corrector=3, schedul
         for n in range(k + 1):
             bubble.kreduce(n, st.G, st.Gloc)
             _update_mf(n, st, eps0, U, nbar)
-            bubble.sigma_2b(n, st.Gloc, U, st.S)
+        sig.start(st.Gloc, U, st.S)
         err = 0.0
         for kk in range(nk):
             old = st.G[kk].copy()
@@ -103,8 +128,16 @@ def run_2b(eps0, U, nt, ntau, beta, h, W, mu=0.0, nbar=0.5, corrector=3, schedul
         for _ in range(corrector):
             bubble.kreduce(n, st.G, st.Gloc)
             _update_mf(n, st, eps0, U, nbar)
-            bubble.sigma_2b(n, st.Gloc, U, st.S)
+            sig.step(n, st.Gloc, U, st.S)
             for kk in range(nk):
                 dyson.dyson_timestep(n, st.G[kk], st.S, st.epsmf[kk], mu, beta, h, W, schedule)
     bubble.kreduce(-1, st.G, st.Gloc)
     return st
+
+
+def run_gw(eps0, U, nt, ntau, beta, h, W, **kw):
+    """Self-consistent GW (Eq. SigmaGW, Eq. dyson_chi) for the problems eps0[k]; returns the
+    driver state and the GW chain (P, K, K^ddagger, chi, dW of the last evaluation)."""
+    chain = gw.GW(nt, ntau, eps0[0].d, beta, h, W)
+    st = run_2b(eps0, U, nt, ntau, beta, h, W, sigma=chain, **kw)
+    return st, chain

@@ -182,3 +182,36 @@ def test_planted_kernel_sign_fails_expansion(monkeypatch):
     monkeypatch.setattr(gw.GW, "_kernel", flipped)
     with pytest.raises(AssertionError):
         test_expansion_in_U_matches_second_born_and_third_order()
+
+
+def _quench_U(N, u_after, u_before):
+    U = Func(N, 1)
+    U.val[:] = u_after
+    U.set(-1, np.array([[u_before]], complex))
+    return U
+
+
+@pytest.mark.slow
+def test_dimer_quench_conservation_gw():
+    """Self-consistent GW Hubbard dimer after the quench U: 1 -> 2 (GW is a conserving
+    approximation): the Galitskii-Migdal energy (Eq. Total_ener) and the particle number stay
+    constant for t > 0 up to the discretisation, and the energy drift falls under halving of h."""
+    from oracle import drivers, observables
+    drifts, ndrift = [], []
+    for N, h in ((40, 0.1), (80, 0.05)):
+        W = Weights(K)
+        e0 = Func(N, 2)
+        e0.val[:] = np.array([[0.0, -1.0], [-1.0, 0.0]])
+        U = _quench_U(N, 2.0, 1.0)
+        st, chain = drivers.run_gw([e0], U, N, 30, 5.0, h, W, corrector=3)
+        G, S = st.G[0], st.S
+        E, Nn = [], []
+        for n in range(N + 1):
+            rho = observables.density_matrix(n, G)
+            E.append(0.5 * np.real(np.trace(rho @ (e0(n) + st.epsmf[0](n))))
+                     + observables.correlation_energy(n, G, S, W, 5.0, h))
+            Nn.append(np.real(np.trace(rho)))
+        drifts.append(np.ptp(E[1:]))
+        ndrift.append(np.ptp(Nn))
+    assert drifts[1] < drifts[0] / 8 and drifts[1] < 1e-3, drifts
+    assert ndrift[1] < 1e-4, ndrift
