@@ -76,19 +76,26 @@ def run_2b(eps0, U, nt, ntau, beta, h, W, mu=0.0, nbar=0.5, corrector=3, schedul
     d = eps0[0].d
     st = state or TwoBState(nk, nt, ntau, d)
     sig = sigma or Sigma2B(W.k)
+    # a momentum-resolved self-energy (k-space GW) acts on all G_k and gives one Sigma_k per
+    # problem; the local ones act on Gloc and give the shared Sigma
+    if getattr(sig, "kspace", False):
+        st.Sk = [Herm(nt, ntau, d) for _ in range(nk)]
+        src, dst, S_of = st.G, st.Sk, (lambda kk: st.Sk[kk])
+    else:
+        src, dst, S_of = st.Gloc, st.S, (lambda kk: st.S)
     # ---- Matsubara -------------------------------------------------------------------
     for kk in range(nk):  # initial guess: free G^M of the bare Hamiltonian
         st.epsmf[kk].set(-1, eps0[kk](-1))
-        dyson.dyson_mat(st.G[kk], st.S, st.epsmf[kk], mu, beta, W)
+        dyson.dyson_mat(st.G[kk], S_of(kk), st.epsmf[kk], mu, beta, W)
     it_m = 0
     for it_m in range(mats_maxiter):
         bubble.kreduce(-1, st.G, st.Gloc)
         _update_mf(-1, st, eps0, U, nbar)
-        sig.mat(st.Gloc, U, st.S)
+        sig.mat(src, U, dst)
         err = 0.0
         for kk in range(nk):
             old = st.G[kk].mat.copy()
-            dyson.dyson_mat(st.G[kk], st.S, st.epsmf[kk], mu, beta, W)
+            dyson.dyson_mat(st.G[kk], S_of(kk), st.epsmf[kk], mu, beta, W)
             err += float(np.abs(st.G[kk].mat - old).sum())
         # a summed distance cannot fall below round-off (about 1e-15 per element)
         if err < max(mats_tol, 1e-15 * nk * (ntau + 1) * d * d):
@@ -97,24 +104,24 @@ def run_2b(eps0, U, nt, ntau, beta, h, W, mu=0.0, nbar=0.5, corrector=3, schedul
     st.log["mats_err"] = err
     bubble.kreduce(-1, st.G, st.Gloc)
     _update_mf(-1, st, eps0, U, nbar)
-    sig.mat(st.Gloc, U, st.S)
+    sig.mat(src, U, dst)
     # ---- bootstrapping ---------------------------------------------------------------
     k = W.k
     for n in range(k + 1):  # initial guess for slices 0..k: the equilibrium Matsubara state
         for kk in range(nk):
             st.epsmf[kk].set(n, st.epsmf[kk](-1) - eps0[kk](-1) + eps0[kk](n))
     for kk in range(nk):
-        dyson.dyson_start(st.G[kk], st.S, st.epsmf[kk], mu, beta, h, W)
+        dyson.dyson_start(st.G[kk], S_of(kk), st.epsmf[kk], mu, beta, h, W)
     it_b = 0
     for it_b in range(boot_maxiter):
         for n in range(k + 1):
             bubble.kreduce(n, st.G, st.Gloc)
             _update_mf(n, st, eps0, U, nbar)
-        sig.start(st.Gloc, U, st.S)
+        sig.start(src, U, dst)
         err = 0.0
         for kk in range(nk):
             old = st.G[kk].copy()
-            dyson.dyson_start(st.G[kk], st.S, st.epsmf[kk], mu, beta, h, W)
+            dyson.dyson_start(st.G[kk], S_of(kk), st.epsmf[kk], mu, beta, h, W)
             err += sum(extrap.distance_norm2(n, st.G[kk], old) for n in range(k + 1))
         nel_boot = nk * d * d * ((k + 1) * (k + 2) + (k + 1) * (ntau + 1))
         if err < max(boot_tol, 1e-15 * nel_boot) and it_b > 2:
@@ -128,9 +135,9 @@ def run_2b(eps0, U, nt, ntau, beta, h, W, mu=0.0, nbar=0.5, corrector=3, schedul
         for _ in range(corrector):
             bubble.kreduce(n, st.G, st.Gloc)
             _update_mf(n, st, eps0, U, nbar)
-            sig.step(n, st.Gloc, U, st.S)
+            sig.step(n, src, U, dst)
             for kk in range(nk):
-                dyson.dyson_timestep(n, st.G[kk], st.S, st.epsmf[kk], mu, beta, h, W, schedule)
+                dyson.dyson_timestep(n, st.G[kk], S_of(kk), st.epsmf[kk], mu, beta, h, W, schedule)
     bubble.kreduce(-1, st.G, st.Gloc)
     return st
 
@@ -139,5 +146,13 @@ def run_gw(eps0, U, nt, ntau, beta, h, W, **kw):
     """Self-consistent GW (Eq. SigmaGW, Eq. dyson_chi) for the problems eps0[k]; returns the
     driver state and the GW chain (P, K, K^ddagger, chi, dW of the last evaluation)."""
     chain = gw.GW(nt, ntau, eps0[0].d, beta, h, W)
+    st = run_2b(eps0, U, nt, ntau, beta, h, W, sigma=chain, **kw)
+    return st, chain
+
+
+def run_gw_kspace(eps0, U, nt, ntau, beta, h, W, add, neg, **kw):
+    """Self-consistent k-space GW (Eqs. Sigmak, Pol) for the one-band problems eps0[k] on the
+    momentum group given by the tables add, neg; Sigma_k per k-point (st.Sk)."""
+    chain = gw.GWk(nt, ntau, len(eps0), beta, h, W, add, neg)
     st = run_2b(eps0, U, nt, ntau, beta, h, W, sigma=chain, **kw)
     return st, chain

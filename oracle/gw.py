@@ -21,6 +21,8 @@ rules carry the opposite sign; composed as Sigma = -U^2 Bubble2[G, Bubble1[G, G]
 second-Born Sigma^M(tau) = -U^2 G^M(tau)^2 G^M(-tau) of oracle/bubble.py, whose sign the KMS
 relation fixes.
 """
+import numpy as np
+
 from . import vie2
 from .contour import Herm
 
@@ -113,3 +115,108 @@ class GW:
         self._kernel(n, G, U)
         vie2.vie2_timestep(n, self.chi, self.K, self.Kcc, self.P, self.beta, self.h, self.W)
         self._sigma(n, G, U, S)
+
+
+def _slice_axpy(n, dst, src, s):
+    """dst += s * src on slice n (n = -1: Matsubara)."""
+    if n == -1:
+        dst.mat += s * src.mat
+        return
+    dst.ret[n, :n + 1] += s * src.ret[n, :n + 1]
+    dst.les[:n + 1, n] += s * src.les[:n + 1, n]
+    dst.tv[n] += s * src.tv[n]
+
+
+def _slice_zero(n, X):
+    _slice_axpy(n, X, X, -1.0)
+
+
+class GWk:
+    """GW of a translation-invariant one-band lattice with a local interaction U(t)
+    (Sec. "GW for the translationally invariant Hubbard model"), momenta k = 0..N_k-1 of a cyclic
+    group with the addition table add[k, q] = index of k + q and neg[q] = index of -q:
+        Pi_k(t,t')   = -(i/N_k) sum_q G_{k+q}(t,t') G_q(t',t)          (Eq. Pol)
+        chi_k        = Pi_k + Pi_k * U * chi_k,  (1 + K_k) * chi_k = Pi_k, K_k = -Pi_k U(t'),
+                       K_k^ddagger = -U(t) Pi_k                        (the local form of Eq. dyson_chi)
+        dW_k(t,t')   = U(t) chi_k(t,t') U(t')
+        Sigma_k      = (i/N_k) sum_q G_{k-q}(t,t') dW_q(t,t')          (Eq. Sigmak)
+    Each product is a Bubble1 / Bubble2 of two momentum components (Eqs. def_bubble1,
+    def_bubble2), so Pi_k = -(1/N_k) sum_q Bubble1[G_{k+q}, G_q] and
+    Sigma_k = (1/N_k) sum_q Bubble2[G_{k-q}, dW_q].  The driver runs it with kspace = True: the
+    Dyson equation of G_k takes Sigma_k."""
+
+    kspace = True
+
+    def __init__(self, nt, ntau, nk, beta, h, W, add, neg):
+        self.beta, self.h, self.W, self.nk = beta, h, W, nk
+        self.add, self.neg = np.asarray(add), np.asarray(neg)
+        mk = lambda: [Herm(nt, ntau, 1, sig=+1) for _ in range(nk)]
+        self.P, self.K, self.Kcc, self.chi, self.dW = mk(), mk(), mk(), mk(), mk()
+        self._tmpb = Herm(nt, ntau, 1, sig=+1)
+        self._tmpf = Herm(nt, ntau, 1)
+
+    def _kernel(self, n, Gk, U):
+        u = lambda t: U(t)[0, 0]
+        N = self.nk
+        for k in range(N):
+            P = self.P[k]
+            _slice_zero(n, P)
+            for q in range(N):
+                bubble1(n, Gk[self.add[k, q]], Gk[q], self._tmpb)
+                _slice_axpy(n, P, self._tmpb, -1.0 / N)
+            K, Kcc = self.K[k], self.Kcc[k]
+            if n == -1:
+                K.mat[...] = -P.mat * u(-1)
+                Kcc.mat[...] = -u(-1) * P.mat
+                continue
+            for j in range(n + 1):
+                K.ret[n, j] = -P.ret[n, j] * u(j)
+                Kcc.ret[n, j] = -u(n) * P.ret[n, j]
+                K.les[j, n] = -P.les[j, n] * u(n)
+                Kcc.les[j, n] = -u(j) * P.les[j, n]
+            K.tv[n] = -P.tv[n] * u(-1)
+            Kcc.tv[n] = -u(n) * P.tv[n]
+
+    def _sigma(self, n, Gk, U, Sk):
+        u = lambda t: U(t)[0, 0]
+        N = self.nk
+        for q in range(N):
+            chi, dW = self.chi[q], self.dW[q]
+            if n == -1:
+                dW.mat[...] = u(-1) * chi.mat * u(-1)
+                continue
+            for j in range(n + 1):
+                dW.ret[n, j] = u(n) * chi.ret[n, j] * u(j)
+                dW.les[j, n] = u(j) * chi.les[j, n] * u(n)
+            dW.tv[n] = u(n) * chi.tv[n] * u(-1)
+        for k in range(N):
+            _slice_zero(n, Sk[k])
+            for q in range(N):
+                bubble2(n, Gk[self.add[k, self.neg[q]]], self.dW[q], self._tmpf)
+                _slice_axpy(n, Sk[k], self._tmpf, 1.0 / N)
+
+    def mat(self, Gk, U, Sk):
+        self._kernel(-1, Gk, U)
+        for k in range(self.nk):
+            vie2.vie2_mat(self.chi[k], self.K[k], self.P[k], self.beta, self.W)
+        self._sigma(-1, Gk, U, Sk)
+
+    def start(self, Gk, U, Sk):
+        for n in range(self.W.k + 1):
+            self._kernel(n, Gk, U)
+        for k in range(self.nk):
+            vie2.vie2_start(self.chi[k], self.K[k], self.Kcc[k], self.P[k], self.beta, self.h, self.W)
+        for n in range(self.W.k + 1):
+            self._sigma(n, Gk, U, Sk)
+
+    def step(self, n, Gk, U, Sk):
+        self._kernel(n, Gk, U)
+        for k in range(self.nk):
+            vie2.vie2_timestep(n, self.chi[k], self.K[k], self.Kcc[k], self.P[k], self.beta, self.h, self.W)
+        self._sigma(n, Gk, U, Sk)
+
+
+def ring_tables(nk):
+    """Addition and negation tables of the momenta k_m = 2 pi m / N_k of a ring of N_k sites."""
+    m = np.arange(nk)
+    return (m[:, None] + m[None, :]) % nk, (-m) % nk

@@ -215,3 +215,119 @@ def test_dimer_quench_conservation_gw():
         ndrift.append(np.ptp(Nn))
     assert drifts[1] < drifts[0] / 8 and drifts[1] < 1e-3, drifts
     assert ndrift[1] < 1e-4, ndrift
+
+
+# ---- k-space GW (Eqs. Sigmak, Pol) against the real-space GW of the same ring ----------------
+def _ring_k(nk):
+    return 2 * np.pi * np.arange(nk) / nk
+
+
+def _to_real_space(Gk, N, T, sig=-1):
+    """G_ij = (1/N_k) sum_k exp(i k (r_i - r_j)) G_k on a ring of N_k sites (d = N_k)."""
+    nk = len(Gk)
+    ks = _ring_k(nk)
+    r = np.arange(nk)
+    ph = np.exp(1j * ks[None, None, :] * (r[:, None, None] - r[None, :, None])) / nk   # [i, j, k]
+    X = Herm(N, T, nk, sig=sig)
+    for c in ("mat", "ret", "les", "tv"):
+        stack = np.stack([getattr(g, c)[..., 0, 0] for g in Gk], axis=-1)         # [..., k]
+        setattr(X, c, np.einsum("...k,ijk->...ij", stack, ph))
+    return X
+
+
+def _to_momentum(X, nk, comp):
+    """X_q = sum_r exp(-i q r) X(r), X(r) = X_{r,0} of a translation-invariant real-space herm."""
+    ks = _ring_k(nk)
+    a = getattr(X, comp)[..., :, 0]                                                 # [..., r]
+    ph = np.exp(-1j * ks[:, None] * np.arange(nk)[None, :])                         # [q, r]
+    return np.einsum("...r,qr->...q", a, ph)
+
+
+def _kspace_fixed_G(nk, N, T, beta, h, A0):
+    ks = _ring_k(nk)
+    return [green_from_H(N, T, np.array([[-2.0 * np.cos(k - A0)]]), 0.1, beta, h) for k in ks]
+
+
+def _run_kspace_chain(Gk, U, beta, h, W):
+    N, T, nk = Gk[0].nt, Gk[0].ntau, len(Gk)
+    add, neg = gw.ring_tables(nk)
+    chain = gw.GWk(N, T, nk, beta, h, W, add, neg)
+    Sk = [Herm(N, T, 1) for _ in range(nk)]
+    chain.mat(Gk, U, Sk)
+    chain.start(Gk, U, Sk)
+    for n in range(W.k + 1, N + 1):
+        chain.step(n, Gk, U, Sk)
+    return chain, Sk
+
+
+def test_kspace_gw_equals_real_space_gw_on_a_ring():
+    """For fixed G_k of a shifted dispersion (no k -> -k symmetry), the momentum sums of the
+    k-space chain reproduce, after the lattice Fourier transform, the real-space GW chain of
+    the ring (P, chi and Sigma as d x d functions of the site indices)."""
+    nk, N, T, beta, h = 4, 12, 16, 2.0, 0.05
+    W = Weights(K)
+    Gk = _kspace_fixed_G(nk, N, T, beta, h, A0=0.4)
+    U = _ufunc(N, lambda n: 0.7 if n < 0 else 0.7 + 0.2 * np.sin(0.5 * n * h))
+    chain_k, Sk = _run_kspace_chain(Gk, U, beta, h, W)
+    Greal = _to_real_space(Gk, N, T)
+    chain_r, Sreal = _run_gw(Greal, U, beta, h, W)
+    low = _low(N)
+    for name, xk, xr in (("P", chain_k.P, chain_r.P), ("chi", chain_k.chi, chain_r.chi), ("Sigma", Sk, Sreal)):
+        for c in ("mat", "ret", "les", "tv"):
+            got = np.stack([getattr(x, c)[..., 0, 0] for x in xk], axis=-1)
+            ref = _to_momentum(xr, nk, c)
+            if c == "ret":
+                got, ref = got[low], ref[low]
+            if c == "les":
+                got, ref = got[low.T], ref[low.T]
+            err = np.abs(got - ref).max() / np.abs(ref).max()
+            assert err < 1e-12, (name, c, err)
+
+
+def test_kspace_gw_planted_momentum_sign_fails(monkeypatch):
+    orig = gw.ring_tables
+
+    def k_minus_q(nk):
+        add, neg = orig(nk)
+        return add[:, neg], neg          # Pi_k from G_{k-q} G_q instead of G_{k+q} G_q
+
+    monkeypatch.setattr(gw, "ring_tables", k_minus_q)
+    with pytest.raises(AssertionError):
+        test_kspace_gw_equals_real_space_gw_on_a_ring()
+
+
+@pytest.mark.slow
+def test_kspace_gw_self_consistent_equals_real_space_ring():
+    """Self-consistent GW of a 4-site ring with a Peierls pulse: the k-space driver (nk = 4,
+    one band, Sigma_k) and the real-space driver (one problem, d = 4 sites) give the same local
+    Green's function on every stored element."""
+    from oracle import drivers
+    nk, N, T, beta, h = 4, 16, 16, 3.0, 0.05
+    W = Weights(K)
+    ks = _ring_k(nk)
+    A = np.array([0.0] + [0.6 * np.sin(0.8 * n * h) for n in range(N + 1)])   # A(0^-) = 0
+    eps_k = -2.0 * np.cos(ks[None, :] - A[:, None])                           # [nt+2, k]
+    e0k = []
+    for kk in range(nk):
+        f = Func(N, 1)
+        f.val[:, 0, 0] = eps_k[:, kk]
+        e0k.append(f)
+    r = np.arange(nk)
+    ph = np.exp(1j * ks[None, None, :] * (r[:, None, None] - r[None, :, None])) / nk
+    e0r = Func(N, nk)
+    e0r.val[...] = np.einsum("tk,ijk->tij", eps_k, ph)
+    U = _ufunc(N, lambda n: 1.0 if n < 0 else 1.5)
+    stk, _ = drivers.run_gw_kspace(e0k, U, N, T, beta, h, W, *gw.ring_tables(nk), corrector=3)
+    str_, _ = drivers.run_gw([e0r], U, N, T, beta, h, W, corrector=3)
+    # st.Gloc holds the k-average taken before the last corrector's Dyson solve: average anew
+    Gl, Gr = Herm(N, T, 1), str_.G[0]
+    for c in ("mat", "ret", "les", "tv"):
+        setattr(Gl, c, sum(getattr(g, c) for g in stk.G) / nk)
+    low = _low(N)
+    for c in ("mat", "ret", "les", "tv"):
+        a, b = getattr(Gl, c)[..., 0, 0], getattr(Gr, c)[..., 0, 0]
+        if c == "ret":
+            a, b = a[low], b[low]
+        if c == "les":
+            a, b = a[low.T], b[low.T]
+        assert np.abs(a - b).max() < 1e-10 * max(1.0, np.abs(b).max()), (c, np.abs(a - b).max())
