@@ -11,7 +11,8 @@
  * Conventions shared by every entry point
  * ---------------------------------------
  *  - C linkage; every call returns ng_status and never throws, aborts or exits.
- *  - Statistics: fermions only (grid.sig = -1).  Orders korder = 1..5.
+ *  - Statistics: grid.sig = -1 (fermions); the vie2 and convolution calls also take bosonic
+ *    functions (grid.sig = +1, every operand of the call bosonic).  Orders korder = 1..5.
  *  - All contour data are caller-owned DEVICE buffers of complex128 stored as interleaved
  *    (re, im) double pairs.  The library never frees caller memory.
  *  - A contour function (struct ng_herm) holds the minimal component set of the paper's
@@ -235,6 +236,37 @@ ng_status ng_set_tv_source(ng_ctx *ctx, int mode);
 /* Forget the FP32 copies kept for NG_F32C time steps (they are rebuilt on the next call). */
 ng_status ng_precision_reset(ng_ctx *ctx);
 
+/* ---- Dyson equation in integral form (Table tab:vie2) --------------------------------- */
+
+/* (1 + F) * G = Q (Sec. "vie2: Dyson equation in integral form", Eq. vie2), solved with the
+ * k-th order rules of Sec. "Implementation: vie2" (Volterra integral equations of the second
+ * kind, Eqs. MBCVSAMx01_start, MBCVSAMx01_t and the conjugate Eq. MBCVSAMx01_cc)t).  F is a
+ * given kernel, Fcc = F^ddagger its hermitian partner (the values of F outside the stored
+ * triangles; pass F itself when F is hermitian symmetric), Q a hermitian source; G is hermitian
+ * when F * Q = Q * F^ddagger (Eq. ,masbX,.), e.g. F = -G0 * Sigma, Fcc = -Sigma * G0, Q = G0 for
+ * the Dyson series.  G: ldk = nbatch; F, Fcc, Q: ldk 1 or nbatch.  nf = 1, 2 (NG_EUNSUPPORTED
+ * otherwise).  grid.sig = +1 solves for bosonic functions (e.g. the susceptibility of Eq.
+ * dyson_chi).  Preconditions follow Table tab:vie2. */
+
+/* Matsubara slice: the k-th order discretised G^M + [F * G]^M = Q^M (Eqs. cm1, cm2), solved
+ * exactly by a dense LU per problem.  Reads F.mat, Q.mat; writes G.mat.  Workspace as
+ * ng_dyson_mat. */
+ng_status ng_vie2_mat(ng_ctx *ctx, const ng_grid *grid, ng_herm G, ng_herm F, ng_herm Q, void *stream);
+
+/* Start-up slices 0..k: retarded column systems, left-mixing and lesser VIE start-up (initial
+ * values Eqs. vie2_ini_r/_tv/_les).  Reads G.mat and F, Fcc, Q on slices -1..k. */
+ng_status ng_vie2_start(ng_ctx *ctx, const ng_grid *grid, ng_herm G, ng_herm F, ng_herm Fcc, ng_herm Q,
+                        void *stream);
+
+/* Time step tstp > k: G^R(n,n) = Q^R(n,n) and single steps for every retarded element m < n;
+ * one step per tau_m of the left-mixing row (source Q^tv - (C^tv_2 + C^tv_3)[F, 1, G^M]); the
+ * lesser column by the conjugate equation G * (1 + F^ddagger) = Q (implementation (B): kernel
+ * [F^R(n,l)]^dagger, source Q^< - (C^<_1 + C^<_3)[G, 1, F^ddagger]) for m = 1..n-1, G^<(0,n)
+ * from Eq. vie2_ini_les, then m = n.  Reads slices < tstp of G, slices <= tstp of F, Fcc, Q.
+ * schedule: NG_MIXED only (NG_SERIAL returns NG_EUNSUPPORTED). */
+ng_status ng_vie2_timestep(ng_ctx *ctx, const ng_grid *grid, int tstp, ng_herm G, ng_herm F, ng_herm Fcc,
+                           ng_herm Q, int schedule, void *stream);
+
 /* ---- convolution (Table tab:convolution) ---------------------------------------------- */
 
 /* Time slice tstp of the contour convolution C = A * f * B (Sec. "Numerical details:
@@ -448,6 +480,35 @@ ng_status ng_run_2b_host(ng_ctx *ctx, const ng_grid *grid, ng_herm G, ng_herm Gl
 ng_status ng_run_2b_sharded(ng_ctx *ctx, const ng_grid *grid, ng_herm G, ng_herm Gloc, ng_herm Sigma,
                             ng_func eps0, ng_func eps_mf, ng_func U, const ng_run_params *p, const ng_shard *shard,
                             int *iters_out, void *stream);
+
+/* ---- GW self-energy (Sec. "Self-energy approximation: GW") ------------------------------ */
+
+/* P, K and K^ddagger on slice tstp (-1 = Matsubara) from the local fermionic Gloc, elementwise
+ * in the orbital indices: P_ab(t,t') = -i G_ab(t,t') G_ba(t',t) (minus the product of Eq.
+ * def_bubble1), K = -P U(t'), K^ddagger = -U(t) P, the kernel pair of (1 + K) * chi = P
+ * (Eq. dyson_chi with a local interaction U(t), real; U.val[n+1] holds U_n).  The Matsubara
+ * component follows C^M(tau) = -i C(-i tau, 0) (Eq. matsconv): P^M_ab(tau) = G^M_ab(tau)
+ * G^M_ba(-tau).  grid describes Gloc (sig = -1); P, K, Kcc are bosonic herms of the same shape;
+ * all ldk = 1.  Reads slice tstp of Gloc (the whole Matsubara/left-mixing row), writes slice
+ * tstp of P, K, Kcc. */
+ng_status ng_gw_polarization_timestep(ng_ctx *ctx, const ng_grid *grid, int tstp, ng_herm P, ng_herm K,
+                                      ng_herm Kcc, ng_herm Gloc, ng_func U, void *stream);
+
+/* Sigma on slice tstp from Gloc and the susceptibility chi (Eq. SigmaGW):
+ * dW_ab(t,t') = U(t) chi_ab(t,t') U(t'), Sigma_ab = i G_ab(t,t') dW_ab(t,t') (Eq. def_bubble2;
+ * Matsubara Sigma^M = -G^M(tau) dW^M(tau)).  All ldk = 1. */
+ng_status ng_gw_sigma_timestep(ng_ctx *ctx, const ng_grid *grid, int tstp, ng_herm Sigma, ng_herm Gloc,
+                               ng_herm Chi, ng_func U, void *stream);
+
+/* Self-consistent GW run: ng_run_2b with the GW self-energy of the local Gloc in place of the
+ * second-Born one.  Each evaluation of Sigma forms P, K, K^ddagger on its slices, solves the
+ * susceptibility equation (ng_vie2_mat in the Matsubara loop, ng_vie2_start for slices 0..k
+ * in the bootstrapping, ng_vie2_timestep(n) in every corrector pass), then dW and Sigma.
+ * Chi: caller-owned bosonic herm (ldk = 1, whole contour) receiving chi; P, K, K^ddagger are
+ * kept in the context, so a run continued with do_setup = 0 must follow a GW run on the same
+ * context and grid.  nf = 1, 2.  Otherwise as ng_run_2b. */
+ng_status ng_run_gw(ng_ctx *ctx, const ng_grid *grid, ng_herm G, ng_herm Gloc, ng_herm Sigma, ng_herm Chi,
+                    ng_func eps0, ng_func eps_mf, ng_func U, const ng_run_params *p, int *iters_out, void *stream);
 
 /* Fixed-Sigma solve: dyson_mat, dyson_start, then dyson_timestep for n = k+1..n_to
  * (Sec. "Test of accuracy and scaling analysis", three-step procedure). */

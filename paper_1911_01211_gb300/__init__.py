@@ -100,6 +100,11 @@ SIGNATURES = {
     "ng_distance_timestep": (ctypes.c_int, [_P, _G, ctypes.c_int, ng_herm, ng_herm, _P, _P]),
     "ng_run_2b": (ctypes.c_int, [_P, _G, ng_herm, ng_herm, ng_herm, ng_func, ng_func, ng_func,
                                  ctypes.POINTER(ng_run_params), ctypes.POINTER(ctypes.c_int), _P]),
+    "ng_run_gw": (ctypes.c_int, [_P, _G, ng_herm, ng_herm, ng_herm, ng_herm, ng_func, ng_func, ng_func,
+                                 ctypes.POINTER(ng_run_params), ctypes.POINTER(ctypes.c_int), _P]),
+    "ng_gw_polarization_timestep": (ctypes.c_int, [_P, _G, ctypes.c_int, ng_herm, ng_herm, ng_herm, ng_herm,
+                                                   ng_func, _P]),
+    "ng_gw_sigma_timestep": (ctypes.c_int, [_P, _G, ctypes.c_int, ng_herm, ng_herm, ng_herm, ng_func, _P]),
     "ng_solve_fixed": (ctypes.c_int, [_P, _G, ng_herm, ng_herm, ng_func, ctypes.c_int, _P]),
     "ng_precision_reset": (ctypes.c_int, [_P]),
     "ng_herm_sandwich": (ctypes.c_int, [_P, _G, ng_herm, _G, ng_herm, ctypes.POINTER(ctypes.c_double), _P]),
@@ -109,6 +114,9 @@ SIGNATURES = {
     "ng_batch_setup": (ctypes.c_int, [_P, _P, _P]),
     "ng_batch_step": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, _P]),
     "ng_batch_solve": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int), _P]),
+    "ng_vie2_mat": (ctypes.c_int, [_P, _G, ng_herm, ng_herm, ng_herm, _P]),
+    "ng_vie2_start": (ctypes.c_int, [_P, _G, ng_herm, ng_herm, ng_herm, ng_herm, _P]),
+    "ng_vie2_timestep": (ctypes.c_int, [_P, _G, ctypes.c_int, ng_herm, ng_herm, ng_herm, ng_herm, ctypes.c_int, _P]),
     "ng_convolution_timestep": (ctypes.c_int, [_P, _G, ctypes.c_int, ng_herm, ng_herm, ng_herm, ng_func, ng_herm,
                                                ng_herm, _P]),
     "ng_observables": (ctypes.c_int, [_P, _G, ctypes.c_int, ng_herm, ng_herm, ng_func, ng_func, _P, _P]),
@@ -363,6 +371,17 @@ class Context:
         self._chk(self.lib.ng_dyson_timestep(self.h, ctypes.byref(grid.c()), tstp, G.c(), S.c(), eps.c(),
                                              precision, schedule, _stream(stream)))
 
+    def vie2_mat(self, grid, G, F, Q, stream=None):
+        self._chk(self.lib.ng_vie2_mat(self.h, ctypes.byref(grid.c()), G.c(), F.c(), Q.c(), _stream(stream)))
+
+    def vie2_start(self, grid, G, F, Fcc, Q, stream=None):
+        self._chk(self.lib.ng_vie2_start(self.h, ctypes.byref(grid.c()), G.c(), F.c(), Fcc.c(), Q.c(),
+                                         _stream(stream)))
+
+    def vie2_timestep(self, grid, tstp, G, F, Fcc, Q, schedule=NG_MIXED, stream=None):
+        self._chk(self.lib.ng_vie2_timestep(self.h, ctypes.byref(grid.c()), tstp, G.c(), F.c(), Fcc.c(), Q.c(),
+                                            schedule, _stream(stream)))
+
     def convolution_timestep(self, grid, tstp, C, A, Acc, f, B, Bcc, stream=None):
         """Slice tstp (-1: Matsubara) of C = A * f * B; f = None is the identity."""
         fc = f.c() if f is not None else ng_func(None, 1)
@@ -416,6 +435,28 @@ class Context:
         if not (allow_noconv and st == NG_ENOCONV):
             self._chk(st)
         return list(iters)
+
+    def run_gw(self, grid, G, Gloc, S, Chi, eps0, eps_mf, U, corrector=3, mats_tol=1e-12, mats_maxiter=200,
+               boot_tol=1e-12, boot_maxiter=200, nbar=0.5, n_from=None, n_to=None, do_setup=True,
+               stream=None, allow_noconv=False, precision=NG_FP64):
+        """ng_run_gw: Chi is a bosonic Herm (ldk = 1) on the grid of G receiving chi."""
+        p = ng_run_params(corrector, mats_tol, mats_maxiter, boot_tol, boot_maxiter, nbar,
+                          grid.korder + 1 if n_from is None else n_from,
+                          grid.nt if n_to is None else n_to, 1 if do_setup else 0, precision)
+        iters = (ctypes.c_int * 2)()
+        st = self.lib.ng_run_gw(self.h, ctypes.byref(grid.c()), G.c(), Gloc.c(), S.c(), Chi.c(), eps0.c(),
+                                eps_mf.c(), U.c(), ctypes.byref(p), iters, _stream(stream))
+        if not (allow_noconv and st == NG_ENOCONV):
+            self._chk(st)
+        return list(iters)
+
+    def gw_polarization_timestep(self, grid, tstp, P, K, Kcc, Gloc, U, stream=None):
+        self._chk(self.lib.ng_gw_polarization_timestep(self.h, ctypes.byref(grid.c()), tstp, P.c(), K.c(), Kcc.c(),
+                                                       Gloc.c(), U.c(), _stream(stream)))
+
+    def gw_sigma_timestep(self, grid, tstp, S, Gloc, Chi, U, stream=None):
+        self._chk(self.lib.ng_gw_sigma_timestep(self.h, ctypes.byref(grid.c()), tstp, S.c(), Gloc.c(), Chi.c(),
+                                                U.c(), _stream(stream)))
 
     def run_2b_host(self, grid, G, Gloc, S, eps0, eps_mf, U, eps0_host, U_host, gdiag_host, corrector=3,
                     mats_tol=1e-12, mats_maxiter=200, boot_tol=1e-12, boot_maxiter=200, nbar=0.5, n_from=None,

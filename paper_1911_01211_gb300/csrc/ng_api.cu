@@ -14,6 +14,8 @@
 #include "ng_stepdf.cuh"
 #include "ng_conv_launch.h"
 #include "ng_tvfft.h"
+#include "ng_gw.cuh"
+#include "ng_vie2_launch.h"
 #include "ng_adjoint_types.h"
 #include <cmath>
 
@@ -54,6 +56,10 @@ struct ng_ctx {
     size_t ws_st_bytes = 0;
     void* ws_prev = nullptr;         // previous iterate for the driver's convergence checks
     size_t ws_prev_bytes = 0;
+    void* ws_gw = nullptr;           // GW driver: bosonic P, K, K^ddagger on the whole contour
+    size_t ws_gw_bytes = 0;
+    void* ws_gwmat = nullptr;        // GW driver: Matsubara workspace of the chi solve (ws_mat
+    size_t ws_gwmat_bytes = 0;       // keeps the LU factors of G^M between iterations)
     // per-launch timing of the time-step kernels (ng_profile_enable / ng_profile_read)
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -90,15 +96,15 @@ namespace {
 bool g_weights_loaded[64] = {false};
 
 // Integration weights of every order into constant memory of device `dev` (current): this
-// file's c_W and the own copies of the adjoint and convolution translation units, together,
-// once per device.
+// file's c_W and the own copies of the adjoint, convolution and vie2 translation units,
+// together, once per device.
 ng_status load_weights_once(int dev) {
     if (dev < 0 || dev >= 64) return NG_EUNSUPPORTED;
     if (g_weights_loaded[dev]) return NG_OK;
     NgWeights all[NG_KMAX];
     for (int k = 1; k <= NG_KMAX; ++k) ng_make_weights(k, &all[k - 1]);
     if (cudaMemcpyToSymbol(c_W, all, sizeof(all)) != cudaSuccess || adj_load_weights(all) != cudaSuccess ||
-        conv_load_weights(all) != cudaSuccess) {
+        conv_load_weights(all) != cudaSuccess || vie2_load_weights(all) != cudaSuccess) {
         cudaGetLastError();
         return NG_ECUDA;
     }
@@ -144,11 +150,13 @@ ng_status ensure(ng_ctx* c, void** p, size_t* have, size_t need) {
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
-ng_status check_grid(ng_ctx* c, const ng_grid* g, Grid* out) {
+// boson_ok: the call also takes bosonic functions (sig = +1; vie2 and convolution)
+ng_status check_grid(ng_ctx* c, const ng_grid* g, Grid* out, bool boson_ok = false) {
     if (!c) return NG_EINVAL;
     if (!g) return fail(c, NG_EINVAL, "grid is NULL");
     if (g->korder != c->k) return fail(c, NG_EINVAL, "grid korder %d differs from the context order %d", g->korder, c->k);
-    if (g->sig != -1) return fail(c, NG_EINVAL, "only fermions (sig = -1) are supported");
+    if (g->sig != -1 && !(boson_ok && g->sig == 1))
+        return fail(c, NG_EINVAL, boson_ok ? "sig must be -1 (fermions) or +1 (bosons)" : "only fermions (sig = -1) are supported");
     if (g->nt < 2 * c->k + 2) return fail(c, NG_EINVAL, "nt = %d must be >= 2k+2 = %d", g->nt, 2 * c->k + 2);
     if (g->ntau < 2 * c->k + 2) return fail(c, NG_EINVAL, "ntau = %d must be >= 2k+2 = %d", g->ntau, 2 * c->k + 2);
     if (g->nbatch < 1) return fail(c, NG_EINVAL, "nbatch must be >= 1");
@@ -518,6 +526,49 @@ ng_status launch_start(ng_ctx* c, const Grid& g, const HermV& G, const HermV& S,
     return check_launch(c, "k_start_les");
 }
 
+// Matsubara slice of the integral form (Eq. vie2_langreth_m): the discretised equation
+// G^M + [F * G]^M = Q^M is the linear system of the integro-differential Matsubara solve with
+// K = -F^M and right-hand side Q^M, solved by the same dense LU per problem.
+template <int D>
+__global__ void k_v2_mat_fill(Grid g, HermV F, HermV Q, cplx* ws_g, cplx* ws_K) {
+    const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (item >= (int64_t)(g.ntau + 1) * g.nb) return;
+    const int kb = (int)(item % g.nb), m = (int)(item / g.nb);
+    const Mat<D> q = gmat<D>(Q, m, kb), f = gmat<D>(F, m, kb);
+    const int64_t o = ((int64_t)kb * (g.ntau + 1) + m) * D * D;
+    for (int a = 0; a < D; ++a)
+        for (int b = 0; b < D; ++b) {
+            ws_g[o + a * D + b] = q.v[a][b];
+            ws_K[o + a * D + b] = cneg(f.v[a][b]);
+        }
+}
+
+template <int D>
+ng_status launch_vie2_mat(ng_ctx* c, const Grid& g, const HermV& G, const HermV& F, const HermV& Q, cudaStream_t s,
+                          void** ws, size_t* ws_bytes) {
+    const int T = g.ntau, N = (T + 1) * D, ld = N + D;
+    const size_t b_g = sizeof(cplx) * (size_t)g.nb * (T + 1) * D * D;
+    const size_t b_A = sizeof(cplx) * (size_t)g.nb * N * ld;
+    const size_t b_piv = sizeof(int) * (size_t)g.nb * N + 256;
+    ng_status st = NG_OK;
+    if ((st = ensure(c, ws, ws_bytes, 3 * b_g + b_A + b_piv))) return st;
+    cplx* ws_g = (cplx*)*ws;
+    cplx* ws_K = ws_g + b_g / sizeof(cplx);
+    cplx* ws_A = ws_K + 2 * (b_g / sizeof(cplx));
+    int* ws_piv = (int*)(ws_A + b_A / sizeof(cplx));
+    const int64_t items = (int64_t)(T + 1) * g.nb;
+    k_v2_mat_fill<D><<<nblocks(items, 128), 128, 0, s>>>(g, F, Q, ws_g, ws_K);
+    if ((st = check_launch(c, "k_v2_mat_fill"))) return st;
+    k_mat_assemble<D><<<nblocks((int64_t)(T + 1) * (T + 2) * g.nb, 256), 256, 0, s>>>(g, ws_g, ws_K, ws_A);
+    if ((st = check_launch(c, "k_mat_assemble"))) return st;
+    const size_t smem = sizeof(cplx) * (size_t)(ld + N) + NG_LU_THREADS * (sizeof(double) + sizeof(int));
+    CUDA_TRY(c, cudaFuncSetAttribute(k_lu_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_lu_solve<<<g.nb, NG_LU_THREADS, smem, s>>>(N, D, ws_A, ws_piv, c->d_status);
+    if ((st = check_launch(c, "k_lu_solve"))) return st;
+    k_mat_store<D><<<nblocks(items, 128), 128, 0, s>>>(g, ws_A, G, c->d_status);
+    return check_launch(c, "k_mat_store");
+}
+
 template <int D>
 ng_status launch_free(ng_ctx* c, const Grid& g, const HermV& G, const cplx* eps_dev, double scale, cudaStream_t s) {
     const int64_t nel = (g.ntau + 1) + 2 * tri(g.nt + 1) + (int64_t)(g.nt + 1) * (g.ntau + 1);
@@ -600,6 +651,18 @@ ng_status do_sigma(ng_ctx* c, const Grid& g, int tstp, const HermV& S, const Her
     const int cnt = tstp < 0 ? g.ntau + 1 : 2 * (tstp + 1) + g.ntau + 1;
     k_sigma2b<<<nblocks((int64_t)cnt * g.nf * g.nf, 128), 128, 0, s>>>(g, tstp, S, L, U);
     return check_launch(c, "k_sigma2b");
+}
+ng_status do_gw_pol(ng_ctx* c, const Grid& g, int tstp, const HermV& P, const HermV& K, const HermV& Kcc, const HermV& L,
+                    const FuncV& U, cudaStream_t s) {
+    const int cnt = tstp < 0 ? g.ntau + 1 : 2 * (tstp + 1) + g.ntau + 1;
+    k_gw_pol<<<nblocks((int64_t)cnt * g.nf * g.nf, 128), 128, 0, s>>>(g, tstp, P, K, Kcc, L, U);
+    return check_launch(c, "k_gw_pol");
+}
+ng_status do_gw_sigma(ng_ctx* c, const Grid& g, int tstp, const HermV& S, const HermV& L, const HermV& X,
+                      const FuncV& U, cudaStream_t s) {
+    const int cnt = tstp < 0 ? g.ntau + 1 : 2 * (tstp + 1) + g.ntau + 1;
+    k_gw_sigma<<<nblocks((int64_t)cnt * g.nf * g.nf, 128), 128, 0, s>>>(g, tstp, S, L, X, U);
+    return check_launch(c, "k_gw_sigma");
 }
 ng_status do_hartree(ng_ctx* c, const Grid& g, int tstp, const FuncV& mf, const FuncV& e0, const HermV& L, const FuncV& U,
                      double nbar, cudaStream_t s) {
@@ -829,6 +892,8 @@ void ng_destroy(ng_ctx* c) {
     cudaFree(c->ws_mat);
     cudaFree(c->ws_st);
     cudaFree(c->ws_prev);
+    cudaFree(c->ws_gw);
+    cudaFree(c->ws_gwmat);
     cudaFree(c->shG.buf);
     cudaFree(c->shS.buf);
     cudaFree(c->dfG.buf);
@@ -967,12 +1032,63 @@ ng_status ng_dyson_timestep(ng_ctx* c, const ng_grid* grid, int tstp, ng_herm G,
     return do_timestep(c, g, tstp, Gv, Sv, ev, (cudaStream_t)stream, precision);
 }
 
+// argument checks shared by the vie2 entry points
+static ng_status vie2_args(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm F, ng_herm Fcc, ng_herm Q, bool rt,
+                           Grid* g, HermV* Gv, HermV* Fv, HermV* Fccv, HermV* Qv) {
+    ng_status st;
+    if ((st = check_grid(c, grid, g, true))) return st;
+    if (g->nf > 2) return fail(c, NG_EUNSUPPORTED, "the vie2 solver supports nf <= 2");
+    if ((st = check_herm(c, *g, G, "G", rt, Gv, g->nb))) return st;
+    if ((st = check_herm(c, *g, F, "F", rt, Fv, 0))) return st;
+    if ((st = check_herm(c, *g, Fcc, "Fcc", rt, Fccv, 0))) return st;
+    return check_herm(c, *g, Q, "Q", rt, Qv, 0);
+}
+
+ng_status ng_vie2_mat(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm F, ng_herm Q, void* stream) {
+    Grid g;
+    HermV Gv, Fv, Fccv, Qv;
+    ng_status st;
+    if ((st = vie2_args(c, grid, G, F, F, Q, false, &g, &Gv, &Fv, &Fccv, &Qv))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    return g.nf == 1 ? launch_vie2_mat<1>(c, g, Gv, Fv, Qv, s, &c->ws_mat, &c->ws_mat_bytes)
+                     : launch_vie2_mat<2>(c, g, Gv, Fv, Qv, s, &c->ws_mat, &c->ws_mat_bytes);
+}
+
+ng_status ng_vie2_start(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm F, ng_herm Fcc, ng_herm Q, void* stream) {
+    Grid g;
+    HermV Gv, Fv, Fccv, Qv;
+    ng_status st;
+    if ((st = vie2_args(c, grid, G, F, Fcc, Q, true, &g, &Gv, &Fv, &Fccv, &Qv))) return st;
+    if ((st = ensure(c, &c->ws_st, &c->ws_st_bytes, start_ws_bytes(g)))) return st;
+    if (vie2_start_launch(g, Gv, Fv, Fccv, Qv, (cplx*)c->ws_st, c->d_status, (cudaStream_t)stream) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, NG_ECUDA, "launch of the vie2 start-up kernels failed");
+    }
+    return NG_OK;
+}
+
+ng_status ng_vie2_timestep(ng_ctx* c, const ng_grid* grid, int tstp, ng_herm G, ng_herm F, ng_herm Fcc, ng_herm Q,
+                           int schedule, void* stream) {
+    Grid g;
+    HermV Gv, Fv, Fccv, Qv;
+    ng_status st;
+    if ((st = vie2_args(c, grid, G, F, Fcc, Q, true, &g, &Gv, &Fv, &Fccv, &Qv))) return st;
+    if (tstp <= g.k || tstp > g.nt) return fail(c, NG_EINVAL, "tstp = %d must be in k+1..nt = %d..%d", tstp, g.k + 1, g.nt);
+    if (schedule == NG_SERIAL) return fail(c, NG_EUNSUPPORTED, "the vie2 time step runs the mixed schedule only");
+    if (schedule != NG_MIXED) return fail(c, NG_EINVAL, "unknown schedule %d", schedule);
+    if (vie2_step_launch(g, tstp, Gv, Fv, Fccv, Qv, c->d_status, (cudaStream_t)stream) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, NG_ECUDA, "launch of the vie2 time-step kernels failed");
+    }
+    return NG_OK;
+}
+
 ng_status ng_convolution_timestep(ng_ctx* c, const ng_grid* grid, int tstp, ng_herm C, ng_herm A, ng_herm Acc,
                                   ng_func f, ng_herm B, ng_herm Bcc, void* stream) {
     Grid g;
     HermV Cv, Av, Accv, Bv, Bccv;
     ng_status st;
-    if ((st = check_grid(c, grid, &g))) return st;
+    if ((st = check_grid(c, grid, &g, true))) return st;
     if (tstp < -1 || tstp > g.nt) return fail(c, NG_EINVAL, "tstp = %d must be in -1..nt = %d", tstp, g.nt);
     const bool rt = tstp >= 0;
     if ((st = check_herm(c, g, C, "C", rt, &Cv, 0))) return st;
@@ -1180,11 +1296,18 @@ struct HostIO {
     cplx* gdiag;        // [nt+1][nf][nf]: Gloc^<(t_n, t_n)
 };
 
-// the second-Born driver; sh = NULL: all k-points on this GPU, else this rank's share;
-// io = NULL: inputs and outputs stay on the device
+// GW state of the driver: the bosonic grid (sig = +1, one problem), P, K, K^ddagger (context
+// workspace) and chi (the caller's), all with ldk = 1
+struct GwRt {
+    Grid gb;
+    HermV P, K, Kcc, X;
+};
+
+// the self-consistent driver, second-Born (gw = NULL) or GW; sh = NULL: all k-points on this
+// GPU, else this rank's share; io = NULL: inputs and outputs stay on the device
 static ng_status run_2b_impl(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm Gloc, ng_herm S, ng_func eps0,
                              ng_func epsmf, ng_func U, const ng_run_params* p, const ng_shard* sh, const HostIO* io,
-                             int* iters_out, void* stream) {
+                             int* iters_out, void* stream, const GwRt* gw = nullptr) {
     Grid g;
     HermV Gv, Lv, Sv;
     FuncV e0, mf, uv;
@@ -1231,6 +1354,37 @@ static ng_status run_2b_impl(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm 
         return NG_OK;
     };
     const int k = g.k, dd = g.nf * g.nf, T = g.ntau;
+    // Sigma slices from..to from Gloc: from = to = -1 the Matsubara slice, 0..k the start-up
+    // slices, n > k one time step.  GW: P, K and K^ddagger on those slices, then the chi
+    // equation (vie2 Matsubara, start-up or time step), then dW and Sigma.
+    auto sigma_slices = [&](int from, int to) -> ng_status {
+        ng_status r;
+        if (!gw) {
+            for (int n = from; n <= to; ++n)
+                if ((r = do_sigma(c, g, n, Sv, Lv, uv, s))) return r;
+            return NG_OK;
+        }
+        for (int n = from; n <= to; ++n)
+            if ((r = do_gw_pol(c, g, n, gw->P, gw->K, gw->Kcc, Lv, uv, s))) return r;
+        cudaError_t e = cudaSuccess;
+        if (from < 0) {
+            r = g.nf == 1 ? launch_vie2_mat<1>(c, gw->gb, gw->X, gw->K, gw->P, s, &c->ws_gwmat, &c->ws_gwmat_bytes)
+                          : launch_vie2_mat<2>(c, gw->gb, gw->X, gw->K, gw->P, s, &c->ws_gwmat, &c->ws_gwmat_bytes);
+            if (r) return r;
+        } else if (from == 0) {
+            e = vie2_start_launch(gw->gb, gw->X, gw->K, gw->Kcc, gw->P, (cplx*)c->ws_st, c->d_status, s);
+        } else {
+            for (int n = from; n <= to && e == cudaSuccess; ++n)
+                e = vie2_step_launch(gw->gb, n, gw->X, gw->K, gw->Kcc, gw->P, c->d_status, s);
+        }
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, NG_ECUDA, "launch of the chi solve failed: %s", cudaGetErrorString(e));
+        }
+        for (int n = from; n <= to; ++n)
+            if ((r = do_gw_sigma(c, g, n, Sv, Lv, gw->X, uv, s))) return r;
+        return NG_OK;
+    };
     // host I/O: eps0 slices (index n+1) and the whole U in, Gloc^<(t_n, t_n) out
     const size_t eps_slice = sizeof(cplx) * dd * (size_t)eps0.ldk;
     auto eps_in = [&](int from, int to) -> ng_status {   // slices from..to (index from+1..to+1)
@@ -1275,7 +1429,7 @@ static ng_status run_2b_impl(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm 
         for (mats_it = 0; mats_it < p->mats_maxiter; ++mats_it) {
             if ((st = do_kreduce_rt(c, g, -1, Lv, Gv, s, rtp))) return st;
             if ((st = do_hartree(c, g, -1, mf, e0, Lv, uv, p->nbar, s))) return st;
-            if ((st = do_sigma(c, g, -1, Sv, Lv, uv, s))) return st;
+            if ((st = sigma_slices(-1, -1))) return st;
             CUDA_TRY(c, cudaMemcpyAsync(Pv.mat.p, Gv.mat.p, per * el_mat, cudaMemcpyDeviceToDevice, s));
             // after two fresh solves the operator changes little between iterations: refine the
             // current iterate with the kept LU factors, refactor only if that stalls
@@ -1291,7 +1445,7 @@ static ng_status run_2b_impl(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm 
         ++mats_it;
         if ((st = do_kreduce_rt(c, g, -1, Lv, Gv, s, rtp))) return st;
         if ((st = do_hartree(c, g, -1, mf, e0, Lv, uv, p->nbar, s))) return st;
-        if ((st = do_sigma(c, g, -1, Sv, Lv, uv, s))) return st;
+        if ((st = sigma_slices(-1, -1))) return st;
         // ---- bootstrapping ----
         for (int n = 0; n <= k; ++n) {
             k_mf_init<<<nblocks((int64_t)dd * epsmf.ldk, 128), 128, 0, s>>>(g, n, mf, e0);
@@ -1302,8 +1456,8 @@ static ng_status run_2b_impl(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm 
             for (int n = 0; n <= k; ++n) {
                 if ((st = do_kreduce_rt(c, g, n, Lv, Gv, s, rtp))) return st;
                 if ((st = do_hartree(c, g, n, mf, e0, Lv, uv, p->nbar, s))) return st;
-                if ((st = do_sigma(c, g, n, Sv, Lv, uv, s))) return st;
             }
+            if ((st = sigma_slices(0, k))) return st;
             CUDA_TRY(c, cudaMemcpyAsync(Pv.ret.p, Gv.ret.p, per * el_tri, cudaMemcpyDeviceToDevice, s));
             CUDA_TRY(c, cudaMemcpyAsync(Pv.les.p, Gv.les.p, per * el_tri, cudaMemcpyDeviceToDevice, s));
             CUDA_TRY(c, cudaMemcpyAsync(Pv.tv.p, Gv.tv.p, per * el_tv, cudaMemcpyDeviceToDevice, s));
@@ -1325,7 +1479,7 @@ static ng_status run_2b_impl(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm 
         for (int it = 0; it < p->corrector; ++it) {
             if ((st = do_kreduce_rt(c, g, n, Lv, Gv, s, rtp))) return st;
             if ((st = do_hartree(c, g, n, mf, e0, Lv, uv, p->nbar, s))) return st;
-            if ((st = do_sigma(c, g, n, Sv, Lv, uv, s))) return st;
+            if ((st = sigma_slices(n, n))) return st;
             if ((st = do_timestep(c, g, n, Gv, Sv, mf, s, p->precision))) return st;
         }
         if ((st = gdiag_out(n, n))) return st;
@@ -1359,6 +1513,75 @@ ng_status ng_run_2b_sharded(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm G
     if (!c) return NG_EINVAL;
     if (!shard) return fail(c, NG_EINVAL, "shard is NULL");
     return run_2b_impl(c, grid, G, Gloc, S, eps0, epsmf, U, p, shard, nullptr, iters_out, stream);
+}
+
+ng_status ng_run_gw(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm Gloc, ng_herm S, ng_herm Chi, ng_func eps0,
+                    ng_func epsmf, ng_func U, const ng_run_params* p, int* iters_out, void* stream) {
+    Grid g;
+    ng_status st;
+    if ((st = check_grid(c, grid, &g))) return st;
+    if (g.nf > 2) return fail(c, NG_EUNSUPPORTED, "the GW driver supports nf <= 2");
+    if (Chi.ldk != 1) return fail(c, NG_EINVAL, "Chi must have ldk = 1");
+    GwRt gw;
+    gw.gb = g;
+    gw.gb.sig = 1;
+    gw.gb.nb = 1;
+    if ((st = check_herm(c, gw.gb, Chi, "Chi", true, &gw.X, 1))) return st;
+    // P, K, K^ddagger: whole-contour bosonic functions in the packed layout, ldk = 1
+    const int dd = g.nf * g.nf;
+    const int64_t n_mat = g.ntau + 1, n_tri = tri(g.nt + 1), n_tv = (int64_t)(g.nt + 1) * (g.ntau + 1);
+    const int64_t per = (n_mat + 2 * n_tri + n_tv) * dd;
+    if ((st = ensure(c, &c->ws_gw, &c->ws_gw_bytes, sizeof(cplx) * 3 * (size_t)per))) return st;
+    auto view = [&](cplx* b) {
+        HermV v;
+        v.mat = Comp{b, 1, dd};
+        v.ret = Comp{b + n_mat * dd, 1, dd};
+        v.les = Comp{v.ret.p + n_tri * dd, 1, dd};
+        v.tv = Comp{v.les.p + n_tri * dd, 1, dd};
+        return v;
+    };
+    cplx* base = (cplx*)c->ws_gw;
+    gw.P = view(base);
+    gw.K = view(base + per);
+    gw.Kcc = view(base + 2 * per);
+    if ((st = ensure(c, &c->ws_st, &c->ws_st_bytes, std::max(start_ws_bytes(g), start_ws_bytes(gw.gb))))) return st;
+    return run_2b_impl(c, grid, G, Gloc, S, eps0, epsmf, U, p, nullptr, nullptr, iters_out, stream, &gw);
+}
+
+ng_status ng_gw_polarization_timestep(ng_ctx* c, const ng_grid* grid, int tstp, ng_herm P, ng_herm K, ng_herm Kcc,
+                                      ng_herm Gloc, ng_func U, void* stream) {
+    Grid g;
+    HermV Pv, Kv, Kccv, L;
+    FuncV uv;
+    ng_status st;
+    if ((st = check_grid(c, grid, &g))) return st;
+    if (tstp < -1 || tstp > g.nt) return fail(c, NG_EINVAL, "tstp = %d out of range", tstp);
+    if (P.ldk != 1 || K.ldk != 1 || Kcc.ldk != 1 || Gloc.ldk != 1)
+        return fail(c, NG_EINVAL, "P, K, Kcc and Gloc must have ldk = 1");
+    if ((st = check_herm(c, g, P, "P", tstp >= 0, &Pv, 1))) return st;
+    if ((st = check_herm(c, g, K, "K", tstp >= 0, &Kv, 1))) return st;
+    if ((st = check_herm(c, g, Kcc, "Kcc", tstp >= 0, &Kccv, 1))) return st;
+    if ((st = check_herm(c, g, Gloc, "Gloc", tstp >= 0, &L, 1))) return st;
+    if ((st = check_func(c, g, U, "U", &uv))) return st;
+    if (U.ldk != 1) return fail(c, NG_EINVAL, "U.ldk must be 1");
+    return do_gw_pol(c, g, tstp, Pv, Kv, Kccv, L, uv, (cudaStream_t)stream);
+}
+
+ng_status ng_gw_sigma_timestep(ng_ctx* c, const ng_grid* grid, int tstp, ng_herm S, ng_herm Gloc, ng_herm Chi,
+                               ng_func U, void* stream) {
+    Grid g;
+    HermV Sv, L, Xv;
+    FuncV uv;
+    ng_status st;
+    if ((st = check_grid(c, grid, &g))) return st;
+    if (tstp < -1 || tstp > g.nt) return fail(c, NG_EINVAL, "tstp = %d out of range", tstp);
+    if (S.ldk != 1 || Gloc.ldk != 1 || Chi.ldk != 1) return fail(c, NG_EINVAL, "Sigma, Gloc and Chi must have ldk = 1");
+    if ((st = check_herm(c, g, S, "Sigma", tstp >= 0, &Sv, 1))) return st;
+    if ((st = check_herm(c, g, Gloc, "Gloc", tstp >= 0, &L, 1))) return st;
+    if ((st = check_herm(c, g, Chi, "Chi", tstp >= 0, &Xv, 1))) return st;
+    if ((st = check_func(c, g, U, "U", &uv))) return st;
+    if (U.ldk != 1) return fail(c, NG_EINVAL, "U.ldk must be 1");
+    return do_gw_sigma(c, g, tstp, Sv, L, Xv, uv, (cudaStream_t)stream);
 }
 
 }  // extern "C"
