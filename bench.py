@@ -16,8 +16,10 @@ the W warm-up steps), so a short window measures the most expensive steps.
 Lines printed: one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on the
 host cores for the same metric (a bounded sample of k-point steps of the same workload).
 Other workloads: --workload uneven (64 independent clusters, the batch path; --compare-plain
-adds the same problems solved one after another) and --workload adjoint (gradient of the final
-kinetic energy on the 16 x 16 square lattice, with finite-difference checks).
+adds the same problems solved one after another), --workload adjoint (gradient of the final
+kinetic energy on the 16 x 16 square lattice, with finite-difference checks), --workload dimer
+(the Hubbard dimer quench and its energy drift) and --workload gw (the k-space GW chain,
+nk = 128, nt = 2500).
 """
 import argparse
 import json
@@ -68,10 +70,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-oracle-check", action="store_true",
                     help="skip the oracle's time step n = nt on four k-points (headline-size parity)")
-    ap.add_argument("--workload", choices=["chain", "uneven", "adjoint", "dimer"], default="chain",
+    ap.add_argument("--workload", choices=["chain", "uneven", "adjoint", "dimer", "gw"], default="chain",
                     help="chain: the headline chain_kspace run; uneven: the 64-cluster uneven batch; "
                          "adjoint: gradient of E_kin(t_N) on the 16x16 square lattice; dimer: the Hubbard "
-                         "dimer quench at nt = 1000 and its energy drift")
+                         "dimer quench at nt = 1000 and its energy drift; gw: the k-space GW chain "
+                         "(nk = 128, nt = 2500)")
+    ap.add_argument("--gw-nk", type=int, default=128, help="gw: momenta (development override)")
+    ap.add_argument("--gw-nt", type=int, default=2500, help="gw: nt (development override)")
     ap.add_argument("--fd-slices", type=int, default=20, help="adjoint: time slices checked by central differences")
     ap.add_argument("--fd-deltas", default="1e-4,1e-5,1e-6",
                     help="adjoint: central-difference steps (comma separated); the fourth-order stencil is added")
@@ -593,6 +598,74 @@ def run_dimer(a):
     print(json.dumps(line), flush=True)
 
 
+def run_gw(a):
+    """k-space GW of the 1D Hubbard chain (the paper's GW example: nk = 128 momenta, U = 2,
+    nt = 2500; here ntau = 400, beta = 10, h = 0.02, k = 5, 3 corrector passes, the Peierls pulse
+    of chain_kspace): ng_run_gw_kspace with Sigma_k from the momentum sums (lattice FFTs), chi_k by
+    the batched bosonic vie2.  Setup and W warm-up steps are a first call; the timed window is the
+    remaining steps, CUDA events around one call, with the Dyson bulk kernel and the whole GW
+    evaluation timed per launch by the library's profile record."""
+    import numpy as np
+    import torch
+    import paper_1911_01211_gb300 as ng
+    from paper_1911_01211_gb300 import workloads as wl
+    w = wl.chain_kspace(nk=a.gw_nk, nt=a.gw_nt, ntau=400, beta=10.0, h=0.02, U=2.0)
+    g = ng.Grid(nt=w.nt, ntau=w.ntau, nf=1, nbatch=w.nbatch, korder=w.korder, h=w.h, beta=w.beta)
+    ctx = ng.Context(w.korder)
+    G, S, X = ng.Herm(g), ng.Herm(g), ng.Herm(g)
+    L = ng.Herm(g, ldk=1)
+    e0 = ng.Func(g, values=torch.from_numpy(w.eps0))
+    mf = ng.Func(g)
+    U = ng.Func(g, scalar=True)
+    U.val[:, 0, 0, 0] = torch.from_numpy(w.U.astype(complex))
+    W = max(3, a.warmup)
+    n_w = w.korder + W
+    t0 = time.perf_counter()
+    its = ctx.run_gw_kspace(g, G, L, S, X, e0, mf, U, corrector=w.corrector, n_to=n_w)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    n_to = w.nt if a.steps <= 0 else min(w.nt, n_w + a.steps)
+    K = n_to - n_w
+    clocks = ClockSampler(0)
+    clocks.start()
+    ctx.profile_enable(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    ctx.run_gw_kspace(g, G, L, S, X, e0, mf, U, corrector=w.corrector, n_from=n_w + 1, n_to=n_to, do_setup=False)
+    ev1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    ms = ev0.elapsed_time(ev1)
+    st = ctx.status_sync()
+    obs = torch.zeros(5, dtype=torch.float64, device="cuda")
+    E, N = [], []
+    for n in range(0, n_to + 1, max(1, n_to // 100)):
+        ctx.observables(g, n, G, S, e0, mf, obs)
+        v = obs.cpu().numpy()
+        N.append(v[0])
+        E.append(v[4])
+    peak = fp64_peak_tflops(clk.get("sm_mhz") or 2070.0)
+    bulk_tf = prof["bulk_flops"] / (prof["bulk_ms"] * 1e-3) / 1e12 if prof["bulk_ms"] > 0 else None
+    line = {"metric": "k-point timesteps/s (k-space GW chain)", "value": w.nbatch * K / (ms / 1e3),
+            "unit": "k-point timesteps/s", "n_gpus": 1, "steps": K, "warmup": W, "ms_per_step": ms / K,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"chain_kspace GW nk={w.nbatch} nt={w.nt} ntau={w.ntau} h={w.h} beta={w.beta} "
+                                   f"U=2 k={w.korder} corrector={w.corrector} (k-space GW, Eqs. Sigmak/Pol, Peierls "
+                                   f"pulse)", "timed": f"steps {n_w + 1}..{n_to} (setup and {W} warm-up steps untimed)"},
+            "roofline": {"bound": "alu", "achieved": bulk_tf, "peak": peak, "unit": "TFLOP/s",
+                         "frac": bulk_tf / peak if bulk_tf else None, "traffic": None, "kernel": "k_step_bulk<1>",
+                         "share_of_timed": prof["bulk_ms"] / ms},
+            "gw_chain_share_of_timed": prof["gw_ms"] / ms, "gw_chain_ms_per_eval": prof["gw_ms"] / max(prof["gw_evals"], 1),
+            "setup": {"s": t_setup, "iterations": its},
+            "E_tot_drift_after_pulse": float(np.ptp(E[len(E) // 2:])), "N_drift": float(np.ptp(N)),
+            "clocks": clk, "device_status": {"status": st[0], "flags": st[1]}}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def run_uneven(a):
     """Uneven batch of independent embedded clusters (nf in {1,2,4,8}, nt in [500,3000],
     ntau = 300, beta in [5,30], h = 0.02, 4-site baths): the whole batch solve (Matsubara and
@@ -795,5 +868,7 @@ if __name__ == "__main__":
         run_adjoint(args)
     elif args.workload == "dimer":
         run_dimer(args)
+    elif args.workload == "gw":
+        run_gw(args)
     else:
         run_ours(args)

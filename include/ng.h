@@ -61,7 +61,8 @@ typedef enum {
     NG_EUNSUPPORTED = 7,  /* valid but not implemented here (e.g. NG_F32C with nf > 2)    */
     NG_ESCRATCH = 8,      /* the problem needs more than the fixed static scratch of the  */
                           /* allocation-free entry point (nothing launched)              */
-    NG_ECOMM = 9          /* the caller's rank-exchange callback reported a failure       */
+    NG_ECOMM = 9,         /* the caller's rank-exchange callback reported a failure       */
+    NG_ESINGULAR = 10     /* a per-step or Matsubara matrix was singular (device status)  */
 } ng_status;
 
 /* device status word bits (ng_status_sync) */
@@ -146,7 +147,9 @@ void ng_destroy(ng_ctx *ctx);
 const char *ng_last_error(const ng_ctx *ctx);
 
 /* Synchronise `stream`, read and clear the device status word (NG_FLAG_* bits) into
- * *device_flags.  Returns NG_ENONFINITE if NG_FLAG_NONFINITE was set, NG_OK otherwise. */
+ * *device_flags.  Returns NG_ENONFINITE if NG_FLAG_NONFINITE was set, else NG_ESINGULAR if
+ * NG_FLAG_SINGULAR was set (a pivot of a per-step, start-up or Matsubara solve was zero; the
+ * affected values are not finite or not meaningful), NG_OK otherwise. */
 ng_status ng_status_sync(ng_ctx *ctx, void *stream, int *device_flags);
 
 /* Host copy of the FP64 integration weights for the context's order k, for inspection:
@@ -426,7 +429,9 @@ ng_status ng_profile_enable(ng_ctx *ctx, int enable);
  * complex multiply-adds per d x d block product; with the FFT source, its quadrature
  * corrections in place of the O(ntau^2) sums), out[3] = total boundary-kernel time in ms,
  * out[4] = number of boundary launches, out[5] = total time of the FFT source pre-pass in ms,
- * out[6] = its launches.  `out` must hold 7 doubles. */
+ * out[6] = its launches, out[7] = total time of the GW self-energy evaluations of ng_run_gw /
+ * ng_run_gw_kspace in ms (bubbles, lattice transforms and the chi solve), out[8] = their
+ * number.  `out` must hold 9 doubles. */
 ng_status ng_profile_read(ng_ctx *ctx, double *out);
 
 /* FP64 throughput of the current device, for the roofline of the FP64 kernels: out[0] = the
@@ -509,6 +514,29 @@ ng_status ng_gw_sigma_timestep(ng_ctx *ctx, const ng_grid *grid, int tstp, ng_he
  * context and grid.  nf = 1, 2.  Otherwise as ng_run_2b. */
 ng_status ng_run_gw(ng_ctx *ctx, const ng_grid *grid, ng_herm G, ng_herm Gloc, ng_herm Sigma, ng_herm Chi,
                     ng_func eps0, ng_func eps_mf, ng_func U, const ng_run_params *p, int *iters_out, void *stream);
+
+/* k-space GW of a translation-invariant one-band lattice (Sec. "GW for the translationally
+ * invariant Hubbard model"): the nbatch problems are the momenta k_m = 2 pi m / nbatch of a ring
+ * (m = 0..nbatch-1, the problem index), U(t) local:
+ *     Pi_k(t,t')  = -(i/N_k) sum_q G_{k+q}(t,t') G_q(t',t)          (Eq. Pol)
+ *     chi_k       = Pi_k + Pi_k * U * chi_k,  K_k = -Pi_k U(t'), K_k^ddagger = -U(t) Pi_k
+ *     Sigma_k     = (i/N_k) sum_q G_{k-q}(t,t') U(t) chi_q(t,t') U(t')   (Eq. Sigmak)
+ * The momentum sums are evaluated in real space: per slice element, G(r) = (1/N_k) sum_k
+ * e^{ikr} G_k, the bubbles of r and -r, and X_k = sum_r e^{-ikr} X(r) back, by FP64 FFTs along
+ * the k index (radix 2 for nbatch a power of two, the direct sum otherwise); the same sums as
+ * the momentum convolutions up to rounding.  nf = 1, nbatch <= 4096.  G, Sigma, P, K, Kcc, Chi
+ * have ldk = nbatch (P, K, Kcc, Chi bosonic). */
+ng_status ng_gw_kspace_polarization_timestep(ng_ctx *ctx, const ng_grid *grid, int tstp, ng_herm P, ng_herm K,
+                                             ng_herm Kcc, ng_herm Gk, ng_func U, void *stream);
+ng_status ng_gw_kspace_sigma_timestep(ng_ctx *ctx, const ng_grid *grid, int tstp, ng_herm Sigma, ng_herm Gk,
+                                      ng_herm Chi, ng_func U, void *stream);
+
+/* Self-consistent k-space GW run: ng_run_gw with Sigma_k per momentum (Sigma.ldk = nbatch) in
+ * the Dyson equation of each G_k, chi_k solved by the batched vie2 (Chi.ldk = nbatch); the
+ * Hartree term from the local density as in ng_run_2b.  NG_FP64 only. */
+ng_status ng_run_gw_kspace(ng_ctx *ctx, const ng_grid *grid, ng_herm G, ng_herm Gloc, ng_herm Sigma, ng_herm Chi,
+                           ng_func eps0, ng_func eps_mf, ng_func U, const ng_run_params *p, int *iters_out,
+                           void *stream);
 
 /* Fixed-Sigma solve: dyson_mat, dyson_start, then dyson_timestep for n = k+1..n_to
  * (Sec. "Test of accuracy and scaling analysis", three-step procedure). */

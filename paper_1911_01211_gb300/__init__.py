@@ -22,12 +22,12 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libng.so")
 
 (NG_OK, NG_EINVAL, NG_ENOMEM, NG_ECUDA, NG_ENOCONV, NG_ETIMEOUT, NG_ENONFINITE, NG_EUNSUPPORTED, NG_ESCRATCH,
- NG_ECOMM) = range(10)
+ NG_ECOMM, NG_ESINGULAR) = range(11)
 NG_FP64, NG_F32C, NG_DF64 = 0, 1, 2
 NG_MIXED, NG_SERIAL = 0, 1
 NG_TVSRC_AUTO, NG_TVSRC_DIRECT = 0, 1
 _STATUS_NAMES = ["NG_OK", "NG_EINVAL", "NG_ENOMEM", "NG_ECUDA", "NG_ENOCONV", "NG_ETIMEOUT",
-                 "NG_ENONFINITE", "NG_EUNSUPPORTED", "NG_ESCRATCH", "NG_ECOMM"]
+                 "NG_ENONFINITE", "NG_EUNSUPPORTED", "NG_ESCRATCH", "NG_ECOMM", "NG_ESINGULAR"]
 
 
 class NgError(RuntimeError):
@@ -105,6 +105,11 @@ SIGNATURES = {
     "ng_gw_polarization_timestep": (ctypes.c_int, [_P, _G, ctypes.c_int, ng_herm, ng_herm, ng_herm, ng_herm,
                                                    ng_func, _P]),
     "ng_gw_sigma_timestep": (ctypes.c_int, [_P, _G, ctypes.c_int, ng_herm, ng_herm, ng_herm, ng_func, _P]),
+    "ng_run_gw_kspace": (ctypes.c_int, [_P, _G, ng_herm, ng_herm, ng_herm, ng_herm, ng_func, ng_func, ng_func,
+                                        ctypes.POINTER(ng_run_params), ctypes.POINTER(ctypes.c_int), _P]),
+    "ng_gw_kspace_polarization_timestep": (ctypes.c_int, [_P, _G, ctypes.c_int, ng_herm, ng_herm, ng_herm,
+                                                          ng_herm, ng_func, _P]),
+    "ng_gw_kspace_sigma_timestep": (ctypes.c_int, [_P, _G, ctypes.c_int, ng_herm, ng_herm, ng_herm, ng_func, _P]),
     "ng_solve_fixed": (ctypes.c_int, [_P, _G, ng_herm, ng_herm, ng_func, ctypes.c_int, _P]),
     "ng_precision_reset": (ctypes.c_int, [_P]),
     "ng_herm_sandwich": (ctypes.c_int, [_P, _G, ng_herm, _G, ng_herm, ctypes.POINTER(ctypes.c_double), _P]),
@@ -338,11 +343,12 @@ class Context:
         self._chk(self.lib.ng_profile_enable(self.h, 1 if on else 0))
 
     def profile_read(self):
-        """{bulk_ms, bulk_launches, bulk_flops, boundary_ms, boundary_launches, tvfft_ms, tvfft_launches}"""
-        out = (ctypes.c_double * 7)()
+        """{bulk_ms, bulk_launches, bulk_flops, boundary_ms, boundary_launches, tvfft_ms, tvfft_launches,
+        gw_ms, gw_evals}"""
+        out = (ctypes.c_double * 9)()
         self._chk(self.lib.ng_profile_read(self.h, out))
         return dict(zip(("bulk_ms", "bulk_launches", "bulk_flops", "boundary_ms", "boundary_launches", "tvfft_ms",
-                         "tvfft_launches"), list(out)))
+                         "tvfft_launches", "gw_ms", "gw_evals"), list(out)))
 
     def set_tv_source(self, mode):
         """NG_TVSRC_AUTO (FFT where supported) or NG_TVSRC_DIRECT."""
@@ -449,6 +455,28 @@ class Context:
         if not (allow_noconv and st == NG_ENOCONV):
             self._chk(st)
         return list(iters)
+
+    def run_gw_kspace(self, grid, G, Gloc, S, Chi, eps0, eps_mf, U, corrector=3, mats_tol=1e-12, mats_maxiter=200,
+                      boot_tol=1e-12, boot_maxiter=200, nbar=0.5, n_from=None, n_to=None, do_setup=True,
+                      stream=None, allow_noconv=False):
+        """ng_run_gw_kspace: S and Chi have ldk = nbatch (momenta k_m = 2 pi m / nbatch)."""
+        p = ng_run_params(corrector, mats_tol, mats_maxiter, boot_tol, boot_maxiter, nbar,
+                          grid.korder + 1 if n_from is None else n_from,
+                          grid.nt if n_to is None else n_to, 1 if do_setup else 0, NG_FP64)
+        iters = (ctypes.c_int * 2)()
+        st = self.lib.ng_run_gw_kspace(self.h, ctypes.byref(grid.c()), G.c(), Gloc.c(), S.c(), Chi.c(), eps0.c(),
+                                       eps_mf.c(), U.c(), ctypes.byref(p), iters, _stream(stream))
+        if not (allow_noconv and st == NG_ENOCONV):
+            self._chk(st)
+        return list(iters)
+
+    def gw_kspace_polarization_timestep(self, grid, tstp, P, K, Kcc, Gk, U, stream=None):
+        self._chk(self.lib.ng_gw_kspace_polarization_timestep(self.h, ctypes.byref(grid.c()), tstp, P.c(), K.c(),
+                                                              Kcc.c(), Gk.c(), U.c(), _stream(stream)))
+
+    def gw_kspace_sigma_timestep(self, grid, tstp, S, Gk, Chi, U, stream=None):
+        self._chk(self.lib.ng_gw_kspace_sigma_timestep(self.h, ctypes.byref(grid.c()), tstp, S.c(), Gk.c(), Chi.c(),
+                                                       U.c(), _stream(stream)))
 
     def gw_polarization_timestep(self, grid, tstp, P, K, Kcc, Gloc, U, stream=None):
         self._chk(self.lib.ng_gw_polarization_timestep(self.h, ctypes.byref(grid.c()), tstp, P.c(), K.c(), Kcc.c(),

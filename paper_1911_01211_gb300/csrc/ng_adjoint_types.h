@@ -36,11 +36,14 @@ struct AdjStep {
     cplx* crhs;                 // [n+1][nb]   lesser (B) rows
     cplx* cMn;                  // [nb]        cotangent of M_n
     cplx* retA;                 // [(k+1)^2][nb] cotangents of Sigma~^R(n-l, n-j) of the ret (A) block
-    cplx* part;                 // [NG_ADJ_NPART][len] partial sums of shared cotangents
+    cplx* part;                 // [NG_ADJ_NPART][NG_ADJ_SPLIT][len] partial sums of shared cotangents
     int64_t plen;               // stride of part
 };
 
 #define NG_ADJ_NPART 8
+// the history kernels split each row over NG_ADJ_SPLIT blocks (grid y); part holds one block
+// sum per split, [NG_ADJ_NPART][NG_ADJ_SPLIT][plen]
+#define NG_ADJ_SPLIT 4
 enum { P_TVROW = 0, P_TVCOL, P_RROW, P_RCOL, P_LCOL, P_LROW, P_QTV };
 
 struct AdjBoot {

@@ -58,6 +58,8 @@ struct ng_ctx {
     size_t ws_prev_bytes = 0;
     void* ws_gw = nullptr;           // GW driver: bosonic P, K, K^ddagger on the whole contour
     size_t ws_gw_bytes = 0;
+    void* ws_gwk = nullptr;          // k-space GW: compact real-space slice buffers
+    size_t ws_gwk_bytes = 0;
     void* ws_gwmat = nullptr;        // GW driver: Matsubara workspace of the chi solve (ws_mat
     size_t ws_gwmat_bytes = 0;       // keeps the LU factors of G^M between iterations)
     // per-launch timing of the time-step kernels (ng_profile_enable / ng_profile_read)
@@ -65,7 +67,7 @@ struct ng_ctx {
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
     double prof_flops = 0.0;
-    std::vector<int> ev_kind;        // 0 bulk, 1 boundary, 2 FFT source pre-pass, per event pair
+    std::vector<int> ev_kind;        // 0 bulk, 1 boundary, 2 FFT source pre-pass, 3 GW chain, per event pair
     Shadow shG, shS;                 // FP32 copies of G and Sigma for NG_F32C
     ShadowDF dfG, dfS;               // double-float copies of G and Sigma for NG_DF64
     void* ws_obs = nullptr;          // per-problem observables before the batch sum
@@ -652,17 +654,38 @@ ng_status do_sigma(ng_ctx* c, const Grid& g, int tstp, const HermV& S, const Her
     k_sigma2b<<<nblocks((int64_t)cnt * g.nf * g.nf, 128), 128, 0, s>>>(g, tstp, S, L, U);
     return check_launch(c, "k_sigma2b");
 }
-ng_status do_gw_pol(ng_ctx* c, const Grid& g, int tstp, const HermV& P, const HermV& K, const HermV& Kcc, const HermV& L,
-                    const FuncV& U, cudaStream_t s) {
+// GW launches on slice tstp: local (L = 1, whole-contour views) or on the ring of L momenta
+// (views of compact real-space slice buffers and the k-space stores)
+inline SliceView whole(const HermV& h) { return SliceView{h, nullptr}; }
+inline SliceView compact(cplx* buf) { return SliceView{HermV{}, buf}; }
+ng_status do_gw_pol(ng_ctx* c, const Grid& g, int tstp, int L, const SliceView& P, const SliceView& K,
+                    const SliceView& Kcc, const SliceView& G, const FuncV& U, cudaStream_t s) {
     const int cnt = tstp < 0 ? g.ntau + 1 : 2 * (tstp + 1) + g.ntau + 1;
-    k_gw_pol<<<nblocks((int64_t)cnt * g.nf * g.nf, 128), 128, 0, s>>>(g, tstp, P, K, Kcc, L, U);
+    k_gw_pol<<<nblocks((int64_t)cnt * g.nf * g.nf * L, 128), 128, 0, s>>>(g, tstp, L, P, K, Kcc, G, U);
     return check_launch(c, "k_gw_pol");
 }
-ng_status do_gw_sigma(ng_ctx* c, const Grid& g, int tstp, const HermV& S, const HermV& L, const HermV& X,
-                      const FuncV& U, cudaStream_t s) {
+ng_status do_gw_sigma(ng_ctx* c, const Grid& g, int tstp, int L, const SliceView& S, const SliceView& G,
+                      const SliceView& X, const FuncV& U, cudaStream_t s) {
     const int cnt = tstp < 0 ? g.ntau + 1 : 2 * (tstp + 1) + g.ntau + 1;
-    k_gw_sigma<<<nblocks((int64_t)cnt * g.nf * g.nf, 128), 128, 0, s>>>(g, tstp, S, L, X, U);
+    k_gw_sigma<<<nblocks((int64_t)cnt * g.nf * g.nf * L, 128), 128, 0, s>>>(g, tstp, L, S, G, X, U);
     return check_launch(c, "k_gw_sigma");
+}
+// lattice Fourier transform of every element of slice tstp along its L momenta / sites
+ng_status do_kfft(ng_ctx* c, const Grid& g, int tstp, int L, const SliceView& in, const SliceView& out, int sign,
+                  double scale, cudaStream_t s) {
+    int log2L = -1;
+    if ((L & (L - 1)) == 0) {
+        log2L = 0;
+        while ((1 << log2L) < L) ++log2L;
+    }
+    const int vpb = std::max(1, 1024 / L);
+    const size_t smem = sizeof(cplx) * (size_t)vpb * L;
+    if (smem > 48 * 1024)
+        CUDA_TRY(c, cudaFuncSetAttribute(k_kfft_slice, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int cnt = tstp < 0 ? g.ntau + 1 : 2 * (tstp + 1) + g.ntau + 1;
+    const int64_t nvec = (int64_t)cnt * g.nf * g.nf;
+    k_kfft_slice<<<(unsigned)((nvec + vpb - 1) / vpb), 256, smem, s>>>(g, tstp, L, log2L, vpb, in, out, sign, scale);
+    return check_launch(c, "k_kfft_slice");
 }
 ng_status do_hartree(ng_ctx* c, const Grid& g, int tstp, const FuncV& mf, const FuncV& e0, const HermV& L, const FuncV& U,
                      double nbar, cudaStream_t s) {
@@ -894,6 +917,7 @@ void ng_destroy(ng_ctx* c) {
     cudaFree(c->ws_prev);
     cudaFree(c->ws_gw);
     cudaFree(c->ws_gwmat);
+    cudaFree(c->ws_gwk);
     cudaFree(c->shG.buf);
     cudaFree(c->shS.buf);
     cudaFree(c->dfG.buf);
@@ -918,6 +942,7 @@ ng_status ng_status_sync(ng_ctx* c, void* stream, int* flags) {
     CUDA_TRY(c, cudaMemset(c->d_status, 0, sizeof(int)));
     if (flags) *flags = f;
     if (f & NGF_NONFINITE) return fail(c, NG_ENONFINITE, "device reported non-finite values (flags %d)", f);
+    if (f & NGF_SINGULAR) return fail(c, NG_ESINGULAR, "device reported a singular matrix (flags %d)", f);
     return NG_OK;
 }
 
@@ -941,14 +966,15 @@ ng_status ng_profile_enable(ng_ctx* c, int enable) {
 
 ng_status ng_profile_read(ng_ctx* c, double* out) {
     if (!c || !out) return NG_EINVAL;
-    for (int i = 0; i < 7; ++i) out[i] = 0.0;
+    for (int i = 0; i < 9; ++i) out[i] = 0.0;
     if (c->ev_used) CUDA_TRY(c, cudaEventSynchronize(c->ev_pool[c->ev_used - 1]));
+    static const int slot[4] = {0, 3, 5, 7};   // bulk, boundary, FFT source, GW chain
     for (size_t p = 0; p < c->ev_kind.size(); ++p) {
         float ms = 0.f;
         CUDA_TRY(c, cudaEventElapsedTime(&ms, c->ev_pool[2 * p], c->ev_pool[2 * p + 1]));
         const int kind = c->ev_kind[p];
-        out[kind == 0 ? 0 : (kind == 1 ? 3 : 5)] += ms;
-        out[kind == 0 ? 1 : (kind == 1 ? 4 : 6)] += 1;
+        out[slot[kind]] += ms;
+        out[slot[kind] + 1] += 1;
     }
     out[2] = c->prof_flops;
     return NG_OK;
@@ -1301,6 +1327,9 @@ struct HostIO {
 struct GwRt {
     Grid gb;
     HermV P, K, Kcc, X;
+    int L = 1;                   // 1: GW of the local Gloc; nk: k-space GW on the ring of nk momenta
+    cplx* slice_buf = nullptr;   // L > 1: compact real-space slices of G, P, K, K^ddagger, chi, Sigma
+    int64_t slice_stride = 0;    // complex values per slice buffer
 };
 
 // the self-consistent driver, second-Born (gw = NULL) or GW; sh = NULL: all k-points on this
@@ -1315,9 +1344,11 @@ static ng_status run_2b_impl(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm 
     if ((st = check_grid(c, grid, &g))) return st;
     if (!p) return fail(c, NG_EINVAL, "params is NULL");
     if ((st = check_herm(c, g, G, "G", true, &Gv, g.nb))) return st;
-    if (Gloc.ldk != 1 || S.ldk != 1) return fail(c, NG_EINVAL, "Gloc and Sigma must have ldk = 1");
+    // Sigma: shared (ldk = 1), or one per k-point for the k-space GW
+    const int s_ldk = (gw && gw->L > 1) ? g.nb : 1;
+    if (Gloc.ldk != 1 || S.ldk != s_ldk) return fail(c, NG_EINVAL, "Gloc must have ldk = 1 and Sigma ldk = %d", s_ldk);
     if ((st = check_herm(c, g, Gloc, "Gloc", true, &Lv, 1))) return st;
-    if ((st = check_herm(c, g, S, "Sigma", true, &Sv, 1))) return st;
+    if ((st = check_herm(c, g, S, "Sigma", true, &Sv, s_ldk))) return st;
     if ((st = check_func(c, g, eps0, "eps0", &e0))) return st;
     if ((st = check_func(c, g, epsmf, "eps_mf", &mf))) return st;
     if ((st = check_func(c, g, U, "U", &uv))) return st;
@@ -1364,8 +1395,27 @@ static ng_status run_2b_impl(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm 
                 if ((r = do_sigma(c, g, n, Sv, Lv, uv, s))) return r;
             return NG_OK;
         }
-        for (int n = from; n <= to; ++n)
-            if ((r = do_gw_pol(c, g, n, gw->P, gw->K, gw->Kcc, Lv, uv, s))) return r;
+        // one event pair around the whole GW evaluation (bubbles, transforms, chi solve)
+        const long pe = prof_pair(c, 3);
+        if (pe >= 0) CUDA_TRY(c, cudaEventRecord(c->ev_pool[pe], s));
+        const int L = gw->L;
+        // k-space: G(r) = (1/L) sum_k e^{ikr} G_k, the bubbles in real space (conjugation
+        // r -> -r), X_k = sum_r e^{-ikr} X(r) back (Eqs. Pol, Sigmak)
+        cplx* B = gw->slice_buf;
+        const int64_t bs = gw->slice_stride;
+        const SliceView vG = compact(B), vP = compact(B + bs), vK = compact(B + 2 * bs), vKcc = compact(B + 3 * bs),
+                        vX = compact(B + 4 * bs), vS = compact(B + 5 * bs);
+        for (int n = from; n <= to; ++n) {
+            if (L == 1) {
+                if ((r = do_gw_pol(c, g, n, 1, whole(gw->P), whole(gw->K), whole(gw->Kcc), whole(Lv), uv, s))) return r;
+                continue;
+            }
+            if ((r = do_kfft(c, g, n, L, whole(Gv), vG, +1, 1.0 / L, s))) return r;
+            if ((r = do_gw_pol(c, g, n, L, vP, vK, vKcc, vG, uv, s))) return r;
+            if ((r = do_kfft(c, g, n, L, vP, whole(gw->P), -1, 1.0, s))) return r;
+            if ((r = do_kfft(c, g, n, L, vK, whole(gw->K), -1, 1.0, s))) return r;
+            if ((r = do_kfft(c, g, n, L, vKcc, whole(gw->Kcc), -1, 1.0, s))) return r;
+        }
         cudaError_t e = cudaSuccess;
         if (from < 0) {
             r = g.nf == 1 ? launch_vie2_mat<1>(c, gw->gb, gw->X, gw->K, gw->P, s, &c->ws_gwmat, &c->ws_gwmat_bytes)
@@ -1381,8 +1431,17 @@ static ng_status run_2b_impl(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm 
             cudaGetLastError();
             return fail(c, NG_ECUDA, "launch of the chi solve failed: %s", cudaGetErrorString(e));
         }
-        for (int n = from; n <= to; ++n)
-            if ((r = do_gw_sigma(c, g, n, Sv, Lv, gw->X, uv, s))) return r;
+        for (int n = from; n <= to; ++n) {
+            if (L == 1) {
+                if ((r = do_gw_sigma(c, g, n, 1, whole(Sv), whole(Lv), whole(gw->X), uv, s))) return r;
+                continue;
+            }
+            if ((r = do_kfft(c, g, n, L, whole(Gv), vG, +1, 1.0 / L, s))) return r;
+            if ((r = do_kfft(c, g, n, L, whole(gw->X), vX, +1, 1.0 / L, s))) return r;
+            if ((r = do_gw_sigma(c, g, n, L, vS, vG, vX, uv, s))) return r;
+            if ((r = do_kfft(c, g, n, L, vS, whole(Sv), -1, 1.0, s))) return r;
+        }
+        if (pe >= 0) CUDA_TRY(c, cudaEventRecord(c->ev_pool[pe + 1], s));
         return NG_OK;
     };
     // host I/O: eps0 slices (index n+1) and the whole U in, Gloc^<(t_n, t_n) out
@@ -1420,7 +1479,7 @@ static ng_status run_2b_impl(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm 
         // ---- Matsubara loop ----
         if ((st = eps_in(-1, k))) return st;
         CUDA_TRY(c, cudaMemcpyAsync(epsmf.val, eps0.val, fslice, cudaMemcpyDeviceToDevice, s));
-        CUDA_TRY(c, cudaMemsetAsync(S.mat, 0, sizeof(cplx) * dd * el_mat, s));
+        CUDA_TRY(c, cudaMemsetAsync(S.mat, 0, sizeof(cplx) * dd * el_mat * (size_t)S.ldk, s));
         if ((st = do_mat(c, g, Gv, Sv, mf, s))) return st;
         double err = 0.0;
         // stopping floors: a summed distance cannot fall below round-off, about 1e-15 per element
@@ -1515,37 +1574,135 @@ ng_status ng_run_2b_sharded(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm G
     return run_2b_impl(c, grid, G, Gloc, S, eps0, epsmf, U, p, shard, nullptr, iters_out, stream);
 }
 
+// the six compact real-space slice buffers of the k-space chain (G, P, K, K^ddagger, chi, Sigma)
+static ng_status gwk_slice_buffers(ng_ctx* c, const Grid& g, GwRt* gw) {
+    const int L = g.nb, dd = g.nf * g.nf;
+    const int64_t slice = (2 * (int64_t)(g.nt + 1) + g.ntau + 1) * dd * L;
+    ng_status st;
+    if ((st = ensure(c, &c->ws_gwk, &c->ws_gwk_bytes, sizeof(cplx) * 6 * (size_t)slice))) return st;
+    gw->L = L;
+    gw->slice_buf = (cplx*)c->ws_gwk;
+    gw->slice_stride = slice;
+    return NG_OK;
+}
+
+// GW state for ng_run_gw (kspace = false: one local problem) and ng_run_gw_kspace (the ring of
+// nbatch momenta): bosonic grid, P, K, K^ddagger in the context, chi from the caller and, for
+// the ring, the compact real-space slice buffers
+static ng_status gw_prepare(ng_ctx* c, const Grid& g, ng_herm Chi, bool kspace, GwRt* gw) {
+    ng_status st;
+    if (g.nf > 2) return fail(c, NG_EUNSUPPORTED, "the GW driver supports nf <= 2");
+    if (kspace && g.nf != 1) return fail(c, NG_EUNSUPPORTED, "the k-space GW is one-band (nf = 1)");
+    if (kspace && g.nb > 4096) return fail(c, NG_EUNSUPPORTED, "the k-space GW supports at most 4096 momenta");
+    const int L = kspace ? g.nb : 1;
+    if (Chi.ldk != L) return fail(c, NG_EINVAL, "Chi must have ldk = %d", L);
+    gw->gb = g;
+    gw->gb.sig = 1;
+    gw->gb.nb = L;
+    gw->L = L;
+    if ((st = check_herm(c, gw->gb, Chi, "Chi", true, &gw->X, L))) return st;
+    // P, K, K^ddagger: whole-contour bosonic functions in the packed layout, ldk = L
+    const int dd = g.nf * g.nf;
+    const int64_t n_mat = g.ntau + 1, n_tri = tri(g.nt + 1), n_tv = (int64_t)(g.nt + 1) * (g.ntau + 1);
+    const int64_t per = (n_mat + 2 * n_tri + n_tv) * dd * L;
+    if ((st = ensure(c, &c->ws_gw, &c->ws_gw_bytes, sizeof(cplx) * 3 * (size_t)per))) return st;
+    auto view = [&](cplx* b) {
+        HermV v;
+        v.mat = Comp{b, L, dd};
+        v.ret = Comp{b + n_mat * dd * L, L, dd};
+        v.les = Comp{v.ret.p + n_tri * dd * L, L, dd};
+        v.tv = Comp{v.les.p + n_tri * dd * L, L, dd};
+        return v;
+    };
+    cplx* base = (cplx*)c->ws_gw;
+    gw->P = view(base);
+    gw->K = view(base + per);
+    gw->Kcc = view(base + 2 * per);
+    if (kspace && (st = gwk_slice_buffers(c, g, gw))) return st;
+    return ensure(c, &c->ws_st, &c->ws_st_bytes, std::max(start_ws_bytes(g), start_ws_bytes(gw->gb)));
+}
+
 ng_status ng_run_gw(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm Gloc, ng_herm S, ng_herm Chi, ng_func eps0,
                     ng_func epsmf, ng_func U, const ng_run_params* p, int* iters_out, void* stream) {
     Grid g;
     ng_status st;
-    if ((st = check_grid(c, grid, &g))) return st;
-    if (g.nf > 2) return fail(c, NG_EUNSUPPORTED, "the GW driver supports nf <= 2");
-    if (Chi.ldk != 1) return fail(c, NG_EINVAL, "Chi must have ldk = 1");
     GwRt gw;
-    gw.gb = g;
-    gw.gb.sig = 1;
-    gw.gb.nb = 1;
-    if ((st = check_herm(c, gw.gb, Chi, "Chi", true, &gw.X, 1))) return st;
-    // P, K, K^ddagger: whole-contour bosonic functions in the packed layout, ldk = 1
-    const int dd = g.nf * g.nf;
-    const int64_t n_mat = g.ntau + 1, n_tri = tri(g.nt + 1), n_tv = (int64_t)(g.nt + 1) * (g.ntau + 1);
-    const int64_t per = (n_mat + 2 * n_tri + n_tv) * dd;
-    if ((st = ensure(c, &c->ws_gw, &c->ws_gw_bytes, sizeof(cplx) * 3 * (size_t)per))) return st;
-    auto view = [&](cplx* b) {
-        HermV v;
-        v.mat = Comp{b, 1, dd};
-        v.ret = Comp{b + n_mat * dd, 1, dd};
-        v.les = Comp{v.ret.p + n_tri * dd, 1, dd};
-        v.tv = Comp{v.les.p + n_tri * dd, 1, dd};
-        return v;
-    };
-    cplx* base = (cplx*)c->ws_gw;
-    gw.P = view(base);
-    gw.K = view(base + per);
-    gw.Kcc = view(base + 2 * per);
-    if ((st = ensure(c, &c->ws_st, &c->ws_st_bytes, std::max(start_ws_bytes(g), start_ws_bytes(gw.gb))))) return st;
+    if ((st = check_grid(c, grid, &g))) return st;
+    if ((st = gw_prepare(c, g, Chi, false, &gw))) return st;
     return run_2b_impl(c, grid, G, Gloc, S, eps0, epsmf, U, p, nullptr, nullptr, iters_out, stream, &gw);
+}
+
+ng_status ng_run_gw_kspace(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm Gloc, ng_herm Sigma, ng_herm Chi,
+                           ng_func eps0, ng_func epsmf, ng_func U, const ng_run_params* p, int* iters_out,
+                           void* stream) {
+    Grid g;
+    ng_status st;
+    GwRt gw;
+    if ((st = check_grid(c, grid, &g))) return st;
+    if ((st = gw_prepare(c, g, Chi, true, &gw))) return st;
+    if (p && p->precision != NG_FP64) return fail(c, NG_EUNSUPPORTED, "the k-space GW driver runs in NG_FP64");
+    return run_2b_impl(c, grid, G, Gloc, Sigma, eps0, epsmf, U, p, nullptr, nullptr, iters_out, stream, &gw);
+}
+
+// one slice of the k-space chain (tests and callers composing their own loop)
+static ng_status gwk_slice_args(ng_ctx* c, const ng_grid* grid, int tstp, ng_herm Gk, ng_func U, Grid* g, GwRt* gw,
+                                HermV* Gv, FuncV* uv) {
+    ng_status st;
+    if ((st = check_grid(c, grid, g))) return st;
+    if (tstp < -1 || tstp > g->nt) return fail(c, NG_EINVAL, "tstp = %d out of range", tstp);
+    if (g->nf != 1) return fail(c, NG_EUNSUPPORTED, "the k-space GW is one-band (nf = 1)");
+    if (g->nb > 4096) return fail(c, NG_EUNSUPPORTED, "the k-space GW supports at most 4096 momenta");
+    gw->gb = *g;
+    gw->gb.sig = 1;
+    if ((st = gwk_slice_buffers(c, *g, gw))) return st;
+    if ((st = check_herm(c, *g, Gk, "G", tstp >= 0, Gv, g->nb))) return st;
+    if ((st = check_func(c, *g, U, "U", uv))) return st;
+    if (U.ldk != 1) return fail(c, NG_EINVAL, "U.ldk must be 1");
+    return NG_OK;
+}
+
+ng_status ng_gw_kspace_polarization_timestep(ng_ctx* c, const ng_grid* grid, int tstp, ng_herm P, ng_herm K,
+                                             ng_herm Kcc, ng_herm Gk, ng_func U, void* stream) {
+    Grid g;
+    GwRt gw;
+    HermV Gv, Pv, Kv, Kccv;
+    FuncV uv;
+    ng_status st;
+    if ((st = gwk_slice_args(c, grid, tstp, Gk, U, &g, &gw, &Gv, &uv))) return st;
+    if ((st = check_herm(c, gw.gb, P, "P", tstp >= 0, &Pv, g.nb))) return st;
+    if ((st = check_herm(c, gw.gb, K, "K", tstp >= 0, &Kv, g.nb))) return st;
+    if ((st = check_herm(c, gw.gb, Kcc, "Kcc", tstp >= 0, &Kccv, g.nb))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int L = g.nb;
+    const int64_t bs = gw.slice_stride;
+    cplx* B = gw.slice_buf;
+    if ((st = do_kfft(c, g, tstp, L, whole(Gv), compact(B), +1, 1.0 / L, s))) return st;
+    if ((st = do_gw_pol(c, g, tstp, L, compact(B + bs), compact(B + 2 * bs), compact(B + 3 * bs), compact(B), uv, s)))
+        return st;
+    if ((st = do_kfft(c, g, tstp, L, compact(B + bs), whole(Pv), -1, 1.0, s))) return st;
+    if ((st = do_kfft(c, g, tstp, L, compact(B + 2 * bs), whole(Kv), -1, 1.0, s))) return st;
+    return do_kfft(c, g, tstp, L, compact(B + 3 * bs), whole(Kccv), -1, 1.0, s);
+}
+
+ng_status ng_gw_kspace_sigma_timestep(ng_ctx* c, const ng_grid* grid, int tstp, ng_herm Sigma, ng_herm Gk,
+                                      ng_herm Chi, ng_func U, void* stream) {
+    Grid g;
+    GwRt gw;
+    HermV Gv, Sv;
+    FuncV uv;
+    ng_status st;
+    HermV Xv;
+    if ((st = gwk_slice_args(c, grid, tstp, Gk, U, &g, &gw, &Gv, &uv))) return st;
+    if ((st = check_herm(c, g, Sigma, "Sigma", tstp >= 0, &Sv, g.nb))) return st;
+    if ((st = check_herm(c, gw.gb, Chi, "Chi", tstp >= 0, &Xv, g.nb))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int L = g.nb;
+    const int64_t bs = gw.slice_stride;
+    cplx* B = gw.slice_buf;
+    if ((st = do_kfft(c, g, tstp, L, whole(Gv), compact(B), +1, 1.0 / L, s))) return st;
+    if ((st = do_kfft(c, g, tstp, L, whole(Xv), compact(B + 4 * bs), +1, 1.0 / L, s))) return st;
+    if ((st = do_gw_sigma(c, g, tstp, L, compact(B + 5 * bs), compact(B), compact(B + 4 * bs), uv, s))) return st;
+    return do_kfft(c, g, tstp, L, compact(B + 5 * bs), whole(Sv), -1, 1.0, s);
 }
 
 ng_status ng_gw_polarization_timestep(ng_ctx* c, const ng_grid* grid, int tstp, ng_herm P, ng_herm K, ng_herm Kcc,
@@ -1564,7 +1721,7 @@ ng_status ng_gw_polarization_timestep(ng_ctx* c, const ng_grid* grid, int tstp, 
     if ((st = check_herm(c, g, Gloc, "Gloc", tstp >= 0, &L, 1))) return st;
     if ((st = check_func(c, g, U, "U", &uv))) return st;
     if (U.ldk != 1) return fail(c, NG_EINVAL, "U.ldk must be 1");
-    return do_gw_pol(c, g, tstp, Pv, Kv, Kccv, L, uv, (cudaStream_t)stream);
+    return do_gw_pol(c, g, tstp, 1, whole(Pv), whole(Kv), whole(Kccv), whole(L), uv, (cudaStream_t)stream);
 }
 
 ng_status ng_gw_sigma_timestep(ng_ctx* c, const ng_grid* grid, int tstp, ng_herm S, ng_herm Gloc, ng_herm Chi,
@@ -1581,7 +1738,7 @@ ng_status ng_gw_sigma_timestep(ng_ctx* c, const ng_grid* grid, int tstp, ng_herm
     if ((st = check_herm(c, g, Chi, "Chi", tstp >= 0, &Xv, 1))) return st;
     if ((st = check_func(c, g, U, "U", &uv))) return st;
     if (U.ldk != 1) return fail(c, NG_EINVAL, "U.ldk must be 1");
-    return do_gw_sigma(c, g, tstp, Sv, L, Xv, uv, (cudaStream_t)stream);
+    return do_gw_sigma(c, g, tstp, 1, whole(Sv), whole(L), whole(Xv), uv, (cudaStream_t)stream);
 }
 
 }  // extern "C"
@@ -1955,7 +2112,7 @@ size_t adj_layout(const Grid& g, int seg, int corr, AdjLayout* A, char* base) {
     A->crhs = take((int64_t)(g.nt + 1) * nb);
     A->cMn = take(nb);
     A->retA = take(K1 * K1 * nb);
-    A->part = take((int64_t)NG_ADJ_NPART * A->L);
+    A->part = take((int64_t)NG_ADJ_NPART * NG_ADJ_SPLIT * A->L);
     A->cLoc = take(A->L);
     A->cmf = take((int64_t)(g.nt + 2) * nb);
     A->ce0 = (double*)take(((int64_t)(g.nt + 2) * nb + 1) / 2);

@@ -5,7 +5,10 @@
   exercised) at 1e-14 relative;
 * the bosonic convolution P * P (grid.sig = +1) at 1e-12;
 * the self-consistent ng_run_gw for the Hubbard dimer after an interaction quench and for a
-  k-space chain (local GW), G, Sigma and chi compared on every stored element at 1e-10.
+  k-space chain (local GW), G, Sigma and chi compared on every stored element at 1e-10;
+* the k-space GW (Eqs. Sigmak, Pol): the FFT-based slice calls against the oracle's momentum
+  sums (nk = 4 radix-2, nk = 6 direct transform) at 1e-13, and ng_run_gw_kspace against
+  drivers.run_gw_kspace at 1e-10.
 """
 import numpy as np
 import pytest
@@ -134,7 +137,7 @@ def test_run_gw_hubbard_dimer(ng):
     _check(herm_to_oracle(X, g, 0), chain.chi)
 
 
-def test_run_gw_kspace_chain(ng):
+def test_run_gw_local_on_kspace_chain(ng):
     """A k-space chain (nk = 4, nf = 1) with the local GW self-energy of Gloc."""
     w = wl.chain_kspace(nk=4, nt=24, ntau=20, beta=4.0, h=0.05)
     g, G, S, X, st, chain, iters = _run_gw_both(ng, w)
@@ -142,3 +145,71 @@ def test_run_gw_kspace_chain(ng):
         _check(herm_to_oracle(G, g, kb), st.G[kb])
     _check(herm_to_oracle(S, g, 0), st.S)
     _check(herm_to_oracle(X, g, 0), chain.chi)
+
+
+# ---- k-space GW (Eqs. Sigmak, Pol): FFTs along k on the GPU, momentum sums in the oracle ----
+@pytest.mark.parametrize("nk", [4, 6])
+def test_gw_kspace_slices_match_oracle(ng, nk):
+    """ng_gw_kspace_polarization_timestep / _sigma_timestep (radix-2 FFT for nk = 4, the direct
+    transform for nk = 6) against the oracle's momentum sums from seeded random G_k and chi_k."""
+    N, T, beta, h, k = 12, 14, 2.0, 0.05, 5
+    rng = np.random.default_rng(1900 + nk)
+    Gk = [_random_herm(rng, N, T, 1, 1.0) for _ in range(nk)]
+    Xk = [_random_herm(rng, N, T, 1, 0.7) for _ in range(nk)]
+    for x in Xk:
+        x.sig = +1
+    u = 0.9 + 0.2 * rng.random(N + 2)
+    Uo = OFunc(N, 1)
+    Uo.val[:, 0, 0] = u
+    g = ng.Grid(nt=N, ntau=T, nf=1, nbatch=nk, korder=k, h=h, beta=beta)
+    G, X, P, K, Kcc, S = (ng.Herm(g) for _ in range(6))
+    oracle_to_herm(Gk, G, g)
+    oracle_to_herm(Xk, X, g)
+    U = ng.Func(g, scalar=True)
+    U.val[:, 0, 0, 0] = torch.from_numpy(u.astype(complex))
+    ctx = ng.Context(k)
+    chain = gw.GWk(N, T, nk, beta, h, Weights(k), *gw.ring_tables(nk))
+    chain.chi = Xk
+    Sk = [OHerm(N, T, 1) for _ in range(nk)]
+    for n in (-1, 0, 1, 6, N):
+        ctx.gw_kspace_polarization_timestep(g, n, P, K, Kcc, G, U)
+        ctx.gw_kspace_sigma_timestep(g, n, S, G, X, U)
+        torch.cuda.synchronize()
+        chain._kernel(n, Gk, Uo)
+        chain._sigma(n, Gk, Uo, Sk)
+        for name, dev, refs in (("P", P, chain.P), ("K", K, chain.K), ("Kcc", Kcc, chain.Kcc), ("Sigma", S, Sk)):
+            scale = max(np.abs(np.concatenate([np.ravel(y) for ref in refs for y in _slice(ref, n)])).max(), 1e-300)
+            for kb in range(nk):
+                got = herm_to_oracle(dev, g, kb)
+                for x, y in zip(_slice(got, n), _slice(refs[kb], n)):
+                    err = float(np.abs(x - y).max() / scale)
+                    assert err < 1e-13, (name, n, kb, err)
+    _status_ok(ctx, ng)
+    ctx.close()
+
+
+def test_run_gw_kspace_chain(ng):
+    """The self-consistent k-space GW of the chain_kspace workload (nk = 4, Peierls pulse)
+    against drivers.run_gw_kspace: G_k, Sigma_k and chi_k on every stored element."""
+    w = wl.chain_kspace(nk=4, nt=20, ntau=16, beta=4.0, h=0.05)
+    g = _grid(ng, w)
+    ctx = ng.Context(w.korder)
+    G, S, X = ng.Herm(g), ng.Herm(g), ng.Herm(g)
+    L = ng.Herm(g, ldk=1)
+    e0 = ng.Func(g, values=torch.from_numpy(w.eps0))
+    mf = ng.Func(g)
+    U = ng.Func(g, scalar=True)
+    U.val[:, 0, 0, 0] = torch.from_numpy(w.U.astype(complex))
+    ctx.run_gw_kspace(g, G, L, S, X, e0, mf, U, corrector=w.corrector)
+    _status_ok(ctx, ng)
+    ctx.close()
+    W = Weights(w.korder)
+    eps0 = [_ofunc(w.eps0, kb) for kb in range(w.nbatch)]
+    Uo = OFunc(w.nt, 1)
+    Uo.val[:, 0, 0] = w.U
+    st, chain = drivers.run_gw_kspace(eps0, Uo, w.nt, w.ntau, w.beta, w.h, W, *gw.ring_tables(w.nbatch),
+                                      corrector=w.corrector)
+    for kb in range(w.nbatch):
+        _check(herm_to_oracle(G, g, kb), st.G[kb])
+        _check(herm_to_oracle(S, g, kb), st.Sk[kb])
+        _check(herm_to_oracle(X, g, kb), chain.chi[kb])
