@@ -834,7 +834,7 @@ def run_adjoint(a):
     t_fd = time.perf_counter() - t_fd
     fd_report = {}
     gi = grad[idx] if idx else np.zeros(0)
-    for name, d, _, _ in stencils:
+    for name, d, _, _ in stencils if idx else []:
         fd = np.array([acc[(name, i)] for i in idx])
         per = [float(abs(x - y) / max(abs(y), 1e-300)) for x, y in zip(gi, fd)]
         fd_report[name] = {"delta": d, "max_rel_err_normwise": float(np.abs(gi - fd).max() / np.abs(fd).max()),

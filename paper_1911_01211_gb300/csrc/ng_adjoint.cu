@@ -19,15 +19,16 @@ cudaError_t adj_pass(const AdjStep& a, SliceV Glc, const cplx* U, SliceV cLoc, d
     const int width = std::max(n + 1, T + 1);
     k_adj_sigA<<<dim3(nblk((int64_t)a.nq * width * 32, 128), 4), 128, 0, s>>>(a, width);
     k_adj_bulk<<<nb, 128, 0, s>>>(a);
-    k_adj_tvrow<<<n, 256, 0, s>>>(a);
-    k_adj_rrow<<<n, 256, 0, s>>>(a);
+    const unsigned S = NG_ADJ_SPLIT;
+    k_adj_tvrow<<<dim3(n, S), 256, 0, s>>>(a);
+    k_adj_rrow<<<dim3(n, S), 256, 0, s>>>(a);
     if (!a.full) {
-        k_adj_tvcol<<<T + 1, 256, 0, s>>>(a);
-        k_adj_rcol<<<n - k, 256, 0, s>>>(a);
-        k_adj_lcol<<<n, 256, 0, s>>>(a);
-        if (n - k - 1 > 0) k_adj_lrow<<<n - k - 1, 256, 0, s>>>(a);
+        k_adj_tvcol<<<dim3(T + 1, S), 256, 0, s>>>(a);
+        k_adj_rcol<<<dim3(n - k, S), 256, 0, s>>>(a);
+        k_adj_lcol<<<dim3(n, S), 256, 0, s>>>(a);
+        if (n - k - 1 > 0) k_adj_lrow<<<dim3(n - k - 1, S), 256, 0, s>>>(a);
     }
-    k_adj_qtv<<<T + 1, 256, 0, s>>>(a);
+    k_adj_qtv<<<dim3(T + 1, S), 256, 0, s>>>(a);
     k_adj_cur<<<nblk(2 * (int64_t)(n + 1) + T + 1 + (int64_t)k * k, 128), 128, 0, s>>>(a);
     k_adj_sigma2b<<<nblk(std::max(n, T) + 1, 128), 128, 0, s>>>(a.g, n, Glc, a.cSw, a.cmfw, 1, FuncV{(cplx*)U, 1},
                                                                 cLoc);

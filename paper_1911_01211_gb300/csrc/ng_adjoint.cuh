@@ -318,6 +318,7 @@ __global__ void __launch_bounds__(256) k_adj_tvrow(AdjStep a) {
     const NgWeights& W = c_W[a.g.k - 1];
     const int k = W.k, n = a.n, nb = a.g.nb, T = a.g.ntau, j = blockIdx.x;
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int m0 = blockIdx.y * nw + wp, ms = nw * gridDim.y;   // this block's share of the row
     const double h = a.g.h, ht = a.g.htau, xi = (double)a.g.sig;
     __shared__ cplx red[32];
     const cplx coefA = cadd(cmuli(cscal(h * gw(W, n, j), cconj(a.Sc.ret[j]))),
@@ -325,11 +326,12 @@ __global__ void __launch_bounds__(256) k_adj_tvrow(AdjStep a) {
     const bool useB = !a.full && j >= 1 && j <= n - k - 1;
     const cplx* crj = a.crhs + (int64_t)j * nb;
     cplx acc = cz();
-    for (int m = wp; m <= T; m += nw) {
+    for (int m = m0; m <= T; m += ms) {
         // w_{T,m} Sigma^tv(n, T-m) (-xi htau), multiplying crhs_j
         const cplx sB = useB ? cscal(-xi * ht * gw(W, T, m), a.Sc.tv[T - m]) : cz();
         const int64_t base = ((int64_t)j * (T + 1) + m) * nb;
         const cplx* cTm = a.caccT + (int64_t)m * nb;
+#pragma unroll 4
         for (int kb = lane; kb < nb; kb += 32) {
             const cplx cT = cTm[kb];
             cplx v = cfma(coefA, cT, a.cGt[base + kb]);
@@ -339,7 +341,7 @@ __global__ void __launch_bounds__(256) k_adj_tvrow(AdjStep a) {
         }
     }
     acc = block_csum(acc, red);
-    if (threadIdx.x == 0) a.part[P_TVROW * a.plen + j] = cmuli(cscal(h * gw(W, n, j), acc));
+    if (threadIdx.x == 0) a.part[(P_TVROW * NG_ADJ_SPLIT + blockIdx.y) * a.plen + j] = cmuli(cscal(h * gw(W, n, j), acc));
 }
 
 // tv column m: cotangent of Sigma^tv(n, T-m) from the C^<_3 sources of the lesser (B) rows
@@ -347,16 +349,19 @@ __global__ void __launch_bounds__(256) k_adj_tvcol(AdjStep a) {
     const NgWeights& W = c_W[a.g.k - 1];
     const int k = W.k, n = a.n, nb = a.g.nb, T = a.g.ntau, m = blockIdx.x;
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int j0 = blockIdx.y * nw + wp, js = nw * gridDim.y;
     const double ht = a.g.htau, xi = (double)a.g.sig;
     __shared__ cplx red[32];
     cplx acc = cz();
-    for (int j = 1 + wp; j <= n - k - 1; j += nw) {
+    for (int j = 1 + j0; j <= n - k - 1; j += js) {
         const int64_t base = ((int64_t)j * (T + 1) + m) * nb;
         const cplx* crj = a.crhs + (int64_t)j * nb;
+#pragma unroll 4
         for (int kb = lane; kb < nb; kb += 32) acc = cfma(a.Gt[base + kb], cconj(crj[kb]), acc);
     }
     acc = block_csum(acc, red);
-    if (threadIdx.x == 0) a.part[P_TVCOL * a.plen + (T - m)] = cscal(-xi * ht * gw(W, T, m), acc);
+    if (threadIdx.x == 0)
+        a.part[(P_TVCOL * NG_ADJ_SPLIT + blockIdx.y) * a.plen + (T - m)] = cscal(-xi * ht * gw(W, T, m), acc);
 }
 
 // ret history row j < n: retarded (B) columns m <= n-k-1 (history term and BDF), and the
@@ -364,8 +369,10 @@ __global__ void __launch_bounds__(256) k_adj_tvcol(AdjStep a) {
 // modified retarded continuation).
 __global__ void __launch_bounds__(256) k_adj_rrow(AdjStep a) {
     const NgWeights& W = c_W[a.g.k - 1];
-    const int k = W.k, n = a.n, nb = a.g.nb, j = blockIdx.x;
+    // rows in decreasing length (row j holds j + 1 entries): the longest are scheduled first
+    const int k = W.k, n = a.n, nb = a.g.nb, j = gridDim.x - 1 - blockIdx.x;
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int m0 = blockIdx.y * nw + wp, ms = nw * gridDim.y;
     const double h = a.g.h;
     __shared__ cplx red[32];
     const cplx sRc = cconj(a.Sc.ret[j]);
@@ -373,7 +380,7 @@ __global__ void __launch_bounds__(256) k_adj_rrow(AdjStep a) {
     const bool rowB = !a.full && j >= 1 && j <= n - k - 1;
     const cplx* crj = a.crhs + (int64_t)j * nb;
     cplx acc = cz();
-    for (int m = wp; m <= j; m += nw) {
+    for (int m = m0; m <= j; m += ms) {
         const int64_t base = (tri(j) + m) * nb;
         const bool colB = (m <= n - k - 1);
         const double w = colB ? gw(W, n - m, j - m) : 0.0;
@@ -386,6 +393,7 @@ __global__ void __launch_bounds__(256) k_adj_rrow(AdjStep a) {
         const cplx* cRm = a.caccR + (int64_t)m * nb;
         const cplx* crm = a.crhs + (int64_t)m * nb;
         cplx t = cz();   // sum over the problems of conj(G^R(j,m)) caccR_m, weighted once below
+#pragma unroll 4
         for (int kb = lane; kb < nb; kb += 32) {
             cplx v = a.cGr[base + kb];
             if (colB) {
@@ -400,7 +408,7 @@ __global__ void __launch_bounds__(256) k_adj_rrow(AdjStep a) {
         acc = cadd(acc, cscal(w, t));
     }
     acc = block_csum(acc, red);
-    if (threadIdx.x == 0) a.part[P_RROW * a.plen + j] = cmuli(cscal(h, acc));
+    if (threadIdx.x == 0) a.part[(P_RROW * NG_ADJ_SPLIT + blockIdx.y) * a.plen + j] = cmuli(cscal(h, acc));
 }
 
 // ret column b: cotangent of Sigma^<(b,n) from the C^<_1 sources of the lesser (B) rows
@@ -408,11 +416,12 @@ __global__ void __launch_bounds__(256) k_adj_rcol(AdjStep a) {
     const NgWeights& W = c_W[a.g.k - 1];
     const int k = W.k, n = a.n, nb = a.g.nb, b = blockIdx.x;
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int a0 = blockIdx.y * nw + wp, as = nw * gridDim.y;
     const double h = a.g.h;
     __shared__ cplx red[32];
     cplx acc = cz();
     // rows ar >= max(1, b): R~(ar,b) = G^R(ar,b); rows 1 <= ar < b <= k: R~(ar,b) = -conj(G^R(b,ar))
-    for (int ar = 1 + wp; ar <= n - k - 1; ar += nw) {
+    for (int ar = 1 + a0; ar <= n - k - 1; ar += as) {
         const bool dir = ar >= b;
         if (!dir && b > k) continue;
         const double w = (dir && ar > k) ? gw(W, ar, b) : W.greg[ar][b];
@@ -421,22 +430,27 @@ __global__ void __launch_bounds__(256) k_adj_rcol(AdjStep a) {
         // cc1 = -i h crhs:  dir: w conj(G^R(ar,b)) cc1;  continued: -w G^R(b,ar) cc1
         // (-i h applied once after the block sum, w once per row)
         cplx t = cz();
-        if (dir)
+        if (dir) {
+#pragma unroll 4
             for (int kb = lane; kb < nb; kb += 32) t = cfma(cconj(a.Gr[base + kb]), cra[kb], t);
-        else
+        } else {
+#pragma unroll 4
             for (int kb = lane; kb < nb; kb += 32) t = cfma(a.Gr[base + kb], cra[kb], t);
+        }
         acc = cadd(acc, cscal(dir ? w : -w, t));
     }
     acc = block_csum(acc, red);
-    if (threadIdx.x == 0) a.part[P_RCOL * a.plen + b] = cmulmi(cscal(h, acc));
+    if (threadIdx.x == 0) a.part[(P_RCOL * NG_ADJ_SPLIT + blockIdx.y) * a.plen + b] = cmulmi(cscal(h, acc));
 }
 
 // les history column b < n: history term and BDF of the lesser (B) rows; partial of
 // Sigma^R(n,b) from rows m <= b
 __global__ void __launch_bounds__(256) k_adj_lcol(AdjStep a) {
     const NgWeights& W = c_W[a.g.k - 1];
-    const int k = W.k, n = a.n, nb = a.g.nb, b = blockIdx.x;
+    // columns in decreasing length (column b holds b + 1 entries): the longest first
+    const int k = W.k, n = a.n, nb = a.g.nb, b = gridDim.x - 1 - blockIdx.x;
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int a0 = blockIdx.y * nw + wp, as = nw * gridDim.y;
     const double h = a.g.h;
     __shared__ cplx red[32];
     const double wb = gw(W, n, b);
@@ -446,13 +460,14 @@ __global__ void __launch_bounds__(256) k_adj_lcol(AdjStep a) {
     const cplx c0 = cadd(cmulmi(cscal(h * wb, a.Sc.ret[b])), cr(bdf));
     const cplx* crb = a.crhs + (int64_t)b * nb;
     cplx acc = cz();
-    for (int ar = wp; ar <= b; ar += nw) {
+    for (int ar = a0; ar <= b; ar += as) {
         const int64_t base = (tri(b) + ar) * nb;
         const bool rowB = ar >= 1 && ar <= n - k - 1;
         const bool cnj = ar < b && colB;
         // row m = b, index l = ar < b:  -i h w_{n,ar} conj(Sigma^R(n,ar)) conj(crhs_b)
         const cplx c1 = cnj ? cmulmi(cscal(h * gw(W, n, ar), cconj(a.Sc.ret[ar]))) : cz();
         const cplx* cra = a.crhs + (int64_t)ar * nb;
+#pragma unroll 4
         for (int kb = lane; kb < nb; kb += 32) {
             cplx v = a.cGl[base + kb];
             if (rowB) {
@@ -465,7 +480,7 @@ __global__ void __launch_bounds__(256) k_adj_lcol(AdjStep a) {
         }
     }
     acc = block_csum(acc, red);
-    if (threadIdx.x == 0) a.part[P_LCOL * a.plen + b] = cmuli(cscal(h * wb, acc));
+    if (threadIdx.x == 0) a.part[(P_LCOL * NG_ADJ_SPLIT + blockIdx.y) * a.plen + b] = cmuli(cscal(h * wb, acc));
 }
 
 // les history row a: partial of Sigma^R(n,a) from the lesser (B) rows m > a
@@ -473,17 +488,20 @@ __global__ void __launch_bounds__(256) k_adj_lrow(AdjStep a) {
     const NgWeights& W = c_W[a.g.k - 1];
     const int k = W.k, n = a.n, nb = a.g.nb, ar = blockIdx.x;
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int m0 = blockIdx.y * nw + wp, ms = nw * gridDim.y;
     const double h = a.g.h;
     __shared__ cplx red[32];
     cplx acc = cz();
-    for (int m = max(ar + 1, 1) + wp; m <= n - k - 1; m += nw) {
+    for (int m = max(ar + 1, 1) + m0; m <= n - k - 1; m += ms) {
         const int64_t base = (tri(m) + ar) * nb;
         const cplx* crm = a.crhs + (int64_t)m * nb;
         // G^<(m, a) = -conj(G^<(a, m))
+#pragma unroll 4
         for (int kb = lane; kb < nb; kb += 32) acc = csub(acc, cconj(cmul(a.Gl[base + kb], crm[kb])));
     }
     acc = block_csum(acc, red);
-    if (threadIdx.x == 0) a.part[P_LROW * a.plen + ar] = cmuli(cscal(h * gw(W, n, ar), acc));
+    if (threadIdx.x == 0)
+        a.part[(P_LROW * NG_ADJ_SPLIT + blockIdx.y) * a.plen + ar] = cmuli(cscal(h * gw(W, n, ar), acc));
 }
 
 // Matsubara source of the tv row, q = -i htau (C2 + C3) (Eqs. ctv2, ctv3): cotangent of
@@ -492,10 +510,11 @@ __global__ void __launch_bounds__(256) k_adj_qtv(AdjStep a) {
     const NgWeights& W = c_W[a.g.k - 1];
     const int k = W.k, nb = a.g.nb, T = a.g.ntau, p = blockIdx.x;
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int m0 = blockIdx.y * nw + wp, ms = nw * gridDim.y;
     const double ht = a.g.htau, xi = (double)a.g.sig;
     __shared__ cplx red[32];
     cplx acc = cz();
-    for (int m = wp; m <= T; m += nw) {
+    for (int m = m0; m <= T; m += ms) {
         // C2 (with xi): m <= k: R[m][j][p] xi G^M(T-j), p <= k;  m > k: w_{m,m-p} xi G^M(T-m+p), p <= m
         // C3: m >= T-k: R[T-m][j][T-p] G^M(j), p >= T-k;  m < T-k: w_{T-m,p-m} G^M(p-m), p >= m
         const bool c2R = (m <= k) && (p <= k), c2G = (m > k) && (p <= m);
@@ -515,7 +534,7 @@ __global__ void __launch_bounds__(256) k_adj_qtv(AdjStep a) {
         }
     }
     acc = block_csum(acc, red);
-    if (threadIdx.x == 0) a.part[P_QTV * a.plen + p] = cmuli(cscal(ht, acc));
+    if (threadIdx.x == 0) a.part[(P_QTV * NG_ADJ_SPLIT + blockIdx.y) * a.plen + p] = cmuli(cscal(ht, acc));
 }
 
 // Current self-energy slice: add the partial sums, the M_n term and the retarded (A) block.
@@ -526,6 +545,12 @@ __global__ void k_adj_cur(AdjStep a) {
     const int k = W.k, n = a.n, nb = a.g.nb, T = a.g.ntau, K1 = k + 1;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const double h = a.g.h;
+    // the NG_ADJ_SPLIT block partials of a history sum, added in split order
+    auto part = [&](int which, int64_t idx) {
+        cplx v = cz();
+        for (int sp = 0; sp < NG_ADJ_SPLIT; ++sp) v = cadd(v, a.part[(which * NG_ADJ_SPLIT + sp) * a.plen + idx]);
+        return v;
+    };
     auto sumk = [&](int l, int j) {
         cplx s = cz();
         for (int kb = 0; kb < nb; ++kb) s = cadd(s, a.retA[(int64_t)(l * K1 + j) * nb + kb]);
@@ -535,9 +560,9 @@ __global__ void k_adj_cur(AdjStep a) {
         const int j = (int)i;
         cplx v = cz();
         if (j < n) {
-            v = cadd(a.part[P_TVROW * a.plen + j], a.part[P_RROW * a.plen + j]);
-            if (!a.full) v = cadd(v, a.part[P_LCOL * a.plen + j]);
-            if (!a.full && j <= n - k - 2) v = cadd(v, a.part[P_LROW * a.plen + j]);
+            v = cadd(part(P_TVROW, j), part(P_RROW, j));
+            if (!a.full) v = cadd(v, part(P_LCOL, j));
+            if (!a.full && j <= n - k - 2) v = cadd(v, part(P_LROW, j));
             if (j >= n - k) v = cadd(v, sumk(0, n - j));   // retarded (A) block, row n
         } else {
             cplx s = cz();
@@ -550,14 +575,14 @@ __global__ void k_adj_cur(AdjStep a) {
     int64_t r = i - (n + 1);
     if (r <= n) {
         const int b = (int)r;
-        if (!a.full && b <= n - k - 1) a.cSw.les[b] = cadd(a.cSw.les[b], a.part[P_RCOL * a.plen + b]);
+        if (!a.full && b <= n - k - 1) a.cSw.les[b] = cadd(a.cSw.les[b], part(P_RCOL, b));
         return;
     }
     r -= n + 1;
     if (r <= T) {
         const int p = (int)r;
-        cplx v = a.part[P_QTV * a.plen + p];
-        if (!a.full) v = cadd(v, a.part[P_TVCOL * a.plen + p]);
+        cplx v = part(P_QTV, p);
+        if (!a.full) v = cadd(v, part(P_TVCOL, p));
         a.cSw.tv[p] = cadd(a.cSw.tv[p], v);
         return;
     }
