@@ -44,6 +44,7 @@ struct Shadow {
 struct ng_ctx {
     int k = 0;
     int device = 0;
+    int sms = 1;                     // streaming multiprocessors of the device (grid sizing)
     NgWeights W;
     char err[512] = {0};
     int* d_status = nullptr;
@@ -261,8 +262,10 @@ ng_status launch_minv(ng_ctx* c, const Grid& g, int n, const HermV& S, const Fun
 
 // FFT pre-pass of the left-mixing source of step n (*tvq = nullptr when the direct sums are
 // used: NG_TVSRC_DIRECT, or nf / ntau outside what the transforms support)
+// prof: record the pre-pass as its own profile entry (not inside a GW evaluation, which is
+// timed as a whole)
 ng_status prep_tvfft(ng_ctx* c, const Grid& g, int n, const HermV& G, const HermV& S, cudaStream_t s,
-                     const cplx** tvq) {
+                     const cplx** tvq, bool prof = true) {
     *tvq = nullptr;
     if (c->tvsrc == NG_TVSRC_DIRECT || !tvfft_supported(g.nf, g.ntau)) return NG_OK;
     ng_status st;
@@ -274,7 +277,7 @@ ng_status prep_tvfft(ng_ctx* c, const Grid& g, int n, const HermV& G, const Herm
     }
     const size_t need = sizeof(cplx) * (size_t)(g.ntau + 1) * g.nf * g.nf * g.nb;
     if ((st = ensure(c, &c->ws_tvq, &c->ws_tvq_bytes, need))) return st;
-    long e = prof_pair(c, 2);
+    long e = prof ? prof_pair(c, 2) : -1;
     if (e >= 0) cudaEventRecord(c->ev_pool[e], s);
     if (tvfft_launch(g, n, S.tv, G.mat, (const cplx*)c->ws_tw, (cplx*)c->ws_tvq, s) != cudaSuccess) {
         cudaGetLastError();
@@ -678,13 +681,16 @@ ng_status do_kfft(ng_ctx* c, const Grid& g, int tstp, int L, const SliceView& in
         log2L = 0;
         while ((1 << log2L) < L) ++log2L;
     }
-    const int vpb = std::max(1, 1024 / L);
-    const size_t smem = sizeof(cplx) * (size_t)vpb * L;
-    if (smem > 48 * 1024)
-        CUDA_TRY(c, cudaFuncSetAttribute(k_kfft_slice, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int cnt = tstp < 0 ? g.ntau + 1 : 2 * (tstp + 1) + g.ntau + 1;
     const int64_t nvec = (int64_t)cnt * g.nf * g.nf;
-    k_kfft_slice<<<(unsigned)((nvec + vpb - 1) / vpb), 256, smem, s>>>(g, tstp, L, log2L, vpb, in, out, sign, scale);
+    // vectors per block: up to 1024 values, but at least two blocks per SM when the slice allows
+    const int64_t fill = std::max<int64_t>(1, nvec / (2 * (int64_t)c->sms));
+    const int vpb = (int)std::max<int64_t>(1, std::min<int64_t>(std::max(1, 1024 / L), fill));
+    const size_t smem = sizeof(cplx) * (size_t)(vpb + 1) * L;
+    if (smem > 48 * 1024)
+        CUDA_TRY(c, cudaFuncSetAttribute(k_kfft_slice, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int thr = std::min(256, std::max(64, vpb * L / 4 / 32 * 32));
+    k_kfft_slice<<<(unsigned)((nvec + vpb - 1) / vpb), thr, smem, s>>>(g, tstp, L, log2L, vpb, in, out, sign, scale);
     return check_launch(c, "k_kfft_slice");
 }
 ng_status do_hartree(ng_ctx* c, const Grid& g, int tstp, const FuncV& mf, const FuncV& e0, const HermV& L, const FuncV& U,
@@ -900,6 +906,10 @@ ng_status ng_create(int korder, int device, ng_ctx** out) {
         return NG_ENOMEM;
     }
     cudaMemset(c->d_status, 0, sizeof(int));
+    if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || c->sms < 1) {
+        cudaGetLastError();
+        c->sms = 1;
+    }
     *out = c;
     return NG_OK;
 }
@@ -1102,7 +1112,9 @@ ng_status ng_vie2_timestep(ng_ctx* c, const ng_grid* grid, int tstp, ng_herm G, 
     if (tstp <= g.k || tstp > g.nt) return fail(c, NG_EINVAL, "tstp = %d must be in k+1..nt = %d..%d", tstp, g.k + 1, g.nt);
     if (schedule == NG_SERIAL) return fail(c, NG_EUNSUPPORTED, "the vie2 time step runs the mixed schedule only");
     if (schedule != NG_MIXED) return fail(c, NG_EINVAL, "unknown schedule %d", schedule);
-    if (vie2_step_launch(g, tstp, Gv, Fv, Fccv, Qv, c->d_status, (cudaStream_t)stream) != cudaSuccess) {
+    const cplx* tvq = nullptr;
+    if ((st = prep_tvfft(c, g, tstp, Gv, Fv, (cudaStream_t)stream, &tvq))) return st;
+    if (vie2_step_launch(g, tstp, Gv, Fv, Fccv, Qv, tvq, c->d_status, (cudaStream_t)stream) != cudaSuccess) {
         cudaGetLastError();
         return fail(c, NG_ECUDA, "launch of the vie2 time-step kernels failed");
     }
@@ -1424,8 +1436,11 @@ static ng_status run_2b_impl(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm 
         } else if (from == 0) {
             e = vie2_start_launch(gw->gb, gw->X, gw->K, gw->Kcc, gw->P, (cplx*)c->ws_st, c->d_status, s);
         } else {
-            for (int n = from; n <= to && e == cudaSuccess; ++n)
-                e = vie2_step_launch(gw->gb, n, gw->X, gw->K, gw->Kcc, gw->P, c->d_status, s);
+            for (int n = from; n <= to && e == cudaSuccess; ++n) {
+                const cplx* tvq = nullptr;
+                if ((r = prep_tvfft(c, gw->gb, n, gw->X, gw->K, s, &tvq, false))) return r;
+                e = vie2_step_launch(gw->gb, n, gw->X, gw->K, gw->Kcc, gw->P, tvq, c->d_status, s);
+            }
         }
         if (e != cudaSuccess) {
             cudaGetLastError();

@@ -188,34 +188,41 @@ __global__ void k_gw_sigma(Grid g, int tstp, int L, SliceView S, SliceView G, Sl
 // Lattice Fourier transform along the innermost index of every element of slice tstp:
 //   out(q) = scale * sum_p exp(sign * 2 pi i p q / L) in(p),  p, q = 0..L-1,
 // radix-2 in shared memory for L a power of two (log2L >= 0), the direct sum otherwise
-// (log2L = -1).  vpb vectors per block, vpb * L complex values of dynamic shared memory; in and
-// out are views of slice tstp (whole-contour store or compact buffer).
+// (log2L = -1).  vpb vectors per block; dynamic shared memory holds the twiddle table
+// tw[j] = exp(sign 2 pi i j / L), j < L (computed once per block: FP64 sin/cos is costly on this
+// part, so no butterfly evaluates one), then the vpb * L values.  in and out are views of slice
+// tstp (whole-contour store or compact buffer).
 __global__ void k_kfft_slice(Grid g, int tstp, int L, int log2L, int vpb, SliceView in, SliceView out, int sign,
                              double scale) {
-    extern __shared__ cplx sm[];
+    extern __shared__ cplx sm_all[];
+    cplx* tw = sm_all;
+    cplx* sm = sm_all + L;
     const int dd = g.nf * g.nf;
     const int64_t nvec = (int64_t)slice_count(g, tstp) * dd;
     const int64_t v0 = (int64_t)blockIdx.x * vpb;
+    for (int j = threadIdx.x; j < L; j += blockDim.x) {
+        double sn, cs;
+        sincospi((double)sign * 2.0 * (double)j / (double)L, &sn, &cs);
+        tw[j] = make_double2(cs, sn);
+    }
     // load (bit-reversed for the radix-2 path)
     for (int t = threadIdx.x; t < vpb * L; t += blockDim.x) {
         const int lv = t / L, p = t % L;
         const int64_t v = v0 + lv;
         if (v >= nvec) continue;
         const cplx x = in.vec(g, tstp, (int)(v / dd), (int)(v % dd), L)[p];
-        const int dst = log2L >= 0 ? (int)(__brev((unsigned)p) >> (32 - max(log2L, 1))) * (log2L > 0) : p;
+        const int dst = log2L > 0 ? (int)(__brev((unsigned)p) >> (32 - log2L)) : (log2L == 0 ? 0 : p);
         sm[lv * L + dst] = x;
     }
     __syncthreads();
     if (log2L >= 0) {
-        for (int hs = 1; hs < L; hs <<= 1) {
+        for (int hs = 1, tstride = L / 2; hs < L; hs <<= 1, tstride >>= 1) {
             for (int t = threadIdx.x; t < vpb * (L / 2); t += blockDim.x) {
                 const int lv = t / (L / 2), bt = t % (L / 2);
                 const int j = bt % hs, blk = bt / hs;
                 const int i0 = lv * L + blk * 2 * hs + j, i1 = i0 + hs;
-                double sn, cs;
-                sincospi((double)sign * (double)j / (double)hs, &sn, &cs);
-                const cplx w = make_double2(cs, sn);
-                const cplx x0 = sm[i0], x1 = cmul(w, sm[i1]);
+                // exp(sign pi i j / hs) = tw[j L / (2 hs)]
+                const cplx x0 = sm[i0], x1 = cmul(tw[j * tstride], sm[i1]);
                 sm[i0] = cadd(x0, x1);
                 sm[i1] = csub(x0, x1);
             }
@@ -234,11 +241,7 @@ __global__ void k_kfft_slice(Grid g, int tstp, int L, int log2L, int vpb, SliceV
         const int64_t v = v0 + lv;
         if (v >= nvec) continue;
         cplx acc = make_double2(0.0, 0.0);
-        for (int p = 0; p < L; ++p) {
-            double sn, cs;
-            sincospi((double)sign * 2.0 * (double)((int64_t)p * q % L) / (double)L, &sn, &cs);
-            acc = cadd(acc, cmul(make_double2(cs, sn), sm[lv * L + p]));
-        }
+        for (int p = 0; p < L; ++p) acc = cadd(acc, cmul(tw[(int)((int64_t)p * q % L)], sm[lv * L + p]));
         out.vec(g, tstp, (int)(v / dd), (int)(v % dd), L)[q] = cscal(scale, acc);
     }
 }

@@ -18,12 +18,12 @@ cudaError_t start_d(const Grid& g, const HermV& G, const HermV& F, const HermV& 
 }
 
 template <int D>
-cudaError_t step_d(const Grid& g, int n, const HermV& G, const HermV& F, const HermV& Fcc, const HermV& Q, int* status,
-                   cudaStream_t s) {
+cudaError_t step_d(const Grid& g, int n, const HermV& G, const HermV& F, const HermV& Fcc, const HermV& Q,
+                   const cplx* tvq, int* status, cudaStream_t s) {
     const int thr = 128;
     const int b_les = (int)nblk((int64_t)g.nb * (n - 1), thr), b_tv = (int)nblk((int64_t)g.nb * (g.ntau + 1), thr);
     const int b_ret = (int)nblk((int64_t)g.nb * n, thr);
-    k_v2_bulk<D><<<b_les + b_tv + b_ret, thr, 0, s>>>(g, n, G, F, Fcc, Q, b_ret, b_tv, b_les, status);
+    k_v2_bulk<D><<<b_les + b_tv + b_ret, thr, 0, s>>>(g, n, G, F, Fcc, Q, b_ret, b_tv, b_les, tvq, status);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_v2_diag<D><<<g.nb, NG_BND_THREADS, 0, s>>>(g, n, G, F, Fcc, Q, status);
@@ -41,6 +41,6 @@ cudaError_t vie2_start_launch(const Grid& g, const HermV& G, const HermV& F, con
 }
 
 cudaError_t vie2_step_launch(const Grid& g, int n, const HermV& G, const HermV& F, const HermV& Fcc, const HermV& Q,
-                             int* status, cudaStream_t s) {
-    return g.nf == 1 ? step_d<1>(g, n, G, F, Fcc, Q, status, s) : step_d<2>(g, n, G, F, Fcc, Q, status, s);
+                             const cplx* tvq, int* status, cudaStream_t s) {
+    return g.nf == 1 ? step_d<1>(g, n, G, F, Fcc, Q, tvq, status, s) : step_d<2>(g, n, G, F, Fcc, Q, tvq, status, s);
 }

@@ -38,8 +38,10 @@ __device__ __forceinline__ Mat<D> v2_flesx(const HermV& F, const HermV& Fcc, int
 // integro-differential step returns -i times this sum for a kernel in place of Sigma.
 template <int D>
 __device__ __forceinline__ Mat<D> v2_ctv23(const NgWeights& W, const Grid& g, const HermV& G, const HermV& F, int n,
-                                           int m, int kb) {
-    return mmuli<D>(q_tv<D>(W, g, G, F, n, m, kb));
+                                           int m, int kb, const cplx* tvq) {
+    // tvq: the unit-weight correlation of the FFT pre-pass (the quadrature's corrections added
+    // here), else the direct sums
+    return mmuli<D>(tvq ? q_tv_fft<D>(W, g, G, F, n, m, kb, tvq) : q_tv<D>(W, g, G, F, n, m, kb));
 }
 
 // (C^<_2 + C^<_3)[F, 1, G](m, n) (Eqs. cles2, cles3): h sum_j w_{n,j} F^<(m,j) G^A(j,n) with
@@ -96,12 +98,12 @@ __device__ __forceinline__ void v2_ret_item(const NgWeights& W, const Grid& g, c
 // left-mixing G^tv(n, m)
 template <int D>
 __device__ __forceinline__ void v2_tv_item(const NgWeights& W, const Grid& g, const HermV& G, const HermV& F,
-                                           const HermV& Q, int n, int m, int kb, int* status) {
+                                           const HermV& Q, int n, int m, int kb, const cplx* tvq, int* status) {
     Mat<D> acc = mzero<D>();
     greg_for(W, n, n - 1, [&](int j, double w) {
         mfma<D>(acc, mscal<D>(w, ld<D>(F.ret, tri(n) + j, kb)), gtv<D>(G, g, j, m, kb));
     });
-    Mat<D> rhs = msub<D>(gtv<D>(Q, g, n, m, kb), v2_ctv23<D>(W, g, G, F, n, m, kb));
+    Mat<D> rhs = msub<D>(gtv<D>(Q, g, n, m, kb), v2_ctv23<D>(W, g, G, F, n, m, kb, tvq));
     rhs = msub<D>(rhs, mscal<D>(g.h, acc));
     int sing = 0;
     const Mat<D> y = mmul<D>(minv<D>(v2_one_plus<D>(g.h * gw(W, n, n), ld<D>(F.ret, tri(n) + n, kb)), &sing), rhs);
@@ -116,8 +118,9 @@ __device__ __forceinline__ void v2_tv_item(const NgWeights& W, const Grid& g, co
 //   c3   = sum_{j <= T} w_{T,j} G^tv(m,j) [F^tv(n, T-j)]^dagger   (C^<_3 = i xi h_tau c3)
 //   hist = sum_{l < n} w_{n,l} G^<(m,l) [F^R(n,l)]^dagger
 template <int D>
-__device__ void v2_les_parts(const NgWeights& W, const Grid& g, const HermV& G, const HermV& F, const HermV& Fcc,
-                             int n, int m, int kb, int j0, int js, Mat<D>& c1, Mat<D>& c3, Mat<D>& hist) {
+__device__ void v2_les_parts_strided(const NgWeights& W, const Grid& g, const HermV& G, const HermV& F,
+                                     const HermV& Fcc, int n, int m, int kb, int j0, int js, Mat<D>& c1, Mat<D>& c3,
+                                     Mat<D>& hist) {
     const int k = W.k, T = g.ntau;
     const int jm = m > k ? m : k;
     for (int j = j0; j <= jm; j += js)
@@ -128,6 +131,32 @@ __device__ void v2_les_parts(const NgWeights& W, const Grid& g, const HermV& G, 
         const Mat<D> gl = (l >= m) ? ld<D>(G.les, tri(l) + m, kb) : mscal<D>(-1.0, mdag<D>(ld<D>(G.les, tri(m) + l, kb)));
         mfma_db<D>(hist, mscal<D>(gw(W, n, l), gl), ld<D>(F.ret, tri(n) + l, kb));
     }
+}
+
+// The whole sums (one item per thread): the unit-weight middle of each Gregory quadrature runs
+// without a weight multiply (greg_for), so the FP64 work per term is the complex product alone.
+template <int D>
+__device__ void v2_les_parts(const NgWeights& W, const Grid& g, const HermV& G, const HermV& F, const HermV& Fcc,
+                             int n, int m, int kb, Mat<D>& c1, Mat<D>& c3, Mat<D>& hist) {
+    const int k = W.k, T = g.ntau;
+    if (m <= k) {
+        for (int j = 0; j <= k; ++j)
+            mfma<D>(c1, mscal<D>(W.greg[m][j], gretx<D>(G, m, j, kb)), ld<D>(Fcc.les, tri(n) + j, kb));
+    } else {
+        const int64_t rowG = tri(m), colF = tri(n);
+        greg_for(W, m, m, [&](int j, double w) {
+            mfma<D>(c1, mscal<D>(w, ld<D>(G.ret, rowG + j, kb)), ld<D>(Fcc.les, colF + j, kb));
+        });
+    }
+    const int64_t rowGt = (int64_t)m * (T + 1), rowFt = (int64_t)n * (T + 1);
+    greg_for(W, T, T, [&](int j, double w) {
+        mfma_db<D>(c3, mscal<D>(w, ld<D>(G.tv, rowGt + j, kb)), ld<D>(F.tv, rowFt + T - j, kb));
+    });
+    const int64_t rowF = tri(n), colM = tri(m);
+    greg_for(W, n, n - 1, [&](int l, double w) {
+        const Mat<D> gl = (l >= m) ? ld<D>(G.les, tri(l) + m, kb) : mscal<D>(-1.0, mdag<D>(ld<D>(G.les, colM + l, kb)));
+        mfma_db<D>(hist, mscal<D>(w, gl), ld<D>(F.ret, rowF + l, kb));
+    });
 }
 
 // G^<(m,n) = [Q^<(m,n) - h c1 - i xi h_tau c3 - h hist] [1 + h w_{n,n} F^R(n,n)]^-dagger
@@ -146,8 +175,9 @@ __device__ __forceinline__ Mat<D> v2_les_solve(const NgWeights& W, const Grid& g
 // Time step n: one launch over the retarded items (m = 0..n-1), the left-mixing items
 // (m = 0..ntau) and the lesser items (m = 1..n-1); (column, problem) items, problem fastest.
 template <int D>
-__global__ void __launch_bounds__(128) k_v2_bulk(Grid g, int n, HermV G, HermV F, HermV Fcc, HermV Q, int nb_ret,
-                                                 int nb_tv, int nb_les, int* status) {
+__global__ void __launch_bounds__(128, D == 1 ? 6 : 1)
+    k_v2_bulk(Grid g, int n, HermV G, HermV F, HermV Fcc, HermV Q, int nb_ret, int nb_tv, int nb_les, const cplx* tvq,
+              int* status) {
     const NgWeights& W = c_W[g.k - 1];
     int blk = blockIdx.x, task;
     if (blk < nb_les) task = 0;
@@ -159,13 +189,13 @@ __global__ void __launch_bounds__(128) k_v2_bulk(Grid g, int n, HermV G, HermV F
     const int ncol = task == 0 ? n - 1 : (task == 1 ? g.ntau + 1 : n);
     if (col >= ncol) return;
     if (task == 1) {
-        v2_tv_item<D>(W, g, G, F, Q, n, (int)col, kb, status);
+        v2_tv_item<D>(W, g, G, F, Q, n, (int)col, kb, tvq, status);
     } else if (task == 2) {
         v2_ret_item<D>(W, g, G, F, Q, n, (int)col, kb, status);
     } else {
         const int m = (int)col + 1;
         Mat<D> c1 = mzero<D>(), c3 = mzero<D>(), hist = mzero<D>();
-        v2_les_parts<D>(W, g, G, F, Fcc, n, m, kb, 0, 1, c1, c3, hist);
+        v2_les_parts<D>(W, g, G, F, Fcc, n, m, kb, c1, c3, hist);
         const Mat<D> y = v2_les_solve<D>(W, g, F, Q, n, m, kb, c1, c3, hist, status);
         if (!mfinite<D>(y)) atomicOr(status, NGF_NONFINITE);
         st<D>(G.les, tri(n) + m, kb, y);
@@ -187,7 +217,7 @@ __global__ void __launch_bounds__(NG_BND_THREADS) k_v2_diag(Grid g, int n, HermV
     }
     __syncthreads();
     Mat<D> c1 = mzero<D>(), c3 = mzero<D>(), hist = mzero<D>();
-    v2_les_parts<D>(W, g, G, F, Fcc, n, n, kb, t, blockDim.x, c1, c3, hist);
+    v2_les_parts_strided<D>(W, g, G, F, Fcc, n, n, kb, t, blockDim.x, c1, c3, hist);
     c1 = block_sum<D>(c1, red);
     c3 = block_sum<D>(c3, red);
     hist = block_sum<D>(hist, red);
@@ -294,7 +324,7 @@ __global__ void k_v2_start_tv(Grid g, HermV G, HermV F, HermV Q, const cplx* ws,
     const int k = W.k, N = k * D;
     const Mat<D> y0 = mcscal<D>(make_double2(0.0, (double)g.sig), gmat<D>(G, g.ntau - m, kb));
     Mat<D> q[NG_KMAX], y[NG_KMAX];
-    for (int n = 1; n <= k; ++n) q[n - 1] = msub<D>(gtv<D>(Q, g, n, m, kb), v2_ctv23<D>(W, g, G, F, n, m, kb));
+    for (int n = 1; n <= k; ++n) q[n - 1] = msub<D>(gtv<D>(Q, g, n, m, kb), v2_ctv23<D>(W, g, G, F, n, m, kb, nullptr));
     v2_start_apply<D>(ws + (int64_t)kb * (N * N + k * D * D), k, q, y0, y);
     st<D>(G.tv, m, kb, y0);
     for (int n = 1; n <= k; ++n) {

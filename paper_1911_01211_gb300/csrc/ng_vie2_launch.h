@@ -9,6 +9,8 @@ cudaError_t vie2_load_weights(const NgWeights* all);
 // start-up slices 0..k of G for nb problems (nf = 1, 2); ws: nb (k nf)^2 + nb k nf^2 complex
 cudaError_t vie2_start_launch(const Grid& g, const HermV& G, const HermV& F, const HermV& Fcc, const HermV& Q,
                               cplx* ws, int* status, cudaStream_t s);
-// time step n > k (conjugate schedule of the lesser column), nf = 1, 2
+// time step n > k (conjugate schedule of the lesser column), nf = 1, 2; tvq: the FFT
+// correlation of the left-mixing source of F and G^M at step n (the layout of tvfft_launch),
+// or NULL for the direct sums
 cudaError_t vie2_step_launch(const Grid& g, int n, const HermV& G, const HermV& F, const HermV& Fcc, const HermV& Q,
-                             int* status, cudaStream_t s);
+                             const cplx* tvq, int* status, cudaStream_t s);

@@ -84,10 +84,12 @@ def _random_herm(rng, N, T, d, scale):
     return X
 
 
+@pytest.mark.parametrize("tvsrc", ["fft", "direct"])
 @pytest.mark.parametrize("d", [1, 2])
-def test_vie2_steps_from_random_data(ng, d):
+def test_vie2_steps_from_random_data(ng, d, tvsrc):
     """Matsubara, start-up and the steps n = k+1, 2k+1, 2k+2, N from a random history, with F,
-    Fcc and Q drawn independently (single steps are linear in their inputs)."""
+    Fcc and Q drawn independently (single steps are linear in their inputs); the left-mixing
+    source from the FFT pre-pass with its corrections, or from the direct sums."""
     k, N, T, beta, h, nb = 5, 22, 18, 2.0, 0.06, 2
     rng = np.random.default_rng(900 + d)
     W = Weights(k)
@@ -101,6 +103,7 @@ def test_vie2_steps_from_random_data(ng, d):
     oracle_to_herm(Fcc, dFcc, g)
     oracle_to_herm(Q, dQ, g)
     ctx = ng.Context(k)
+    ctx.set_tv_source(ng.NG_TVSRC_AUTO if tvsrc == "fft" else ng.NG_TVSRC_DIRECT)
     # Matsubara and start-up
     G = ng.Herm(g)
     ctx.vie2_mat(g, G, dF, dQ)
