@@ -447,7 +447,8 @@ def run_ours(a):
                       "tv": G.tv[nt * (w.ntau + 1):(nt + 1) * (w.ntau + 1)]}
         ref = {c: x.clone() for c, x in sl().items()}
         bytes_per_elem = {"f32c": 8, "df64": 16}
-        for name, prec, kern in (("f32c", ng.NG_F32C, "k_step_bulk32<1>"), ("df64", ng.NG_DF64, "k_step_bulkdf<1>")):
+        k32 = "k_step_bulk32p (two k-points per thread)" if w.nbatch % 2 == 0 else "k_step_bulk32<1>"
+        for name, prec, kern in (("f32c", ng.NG_F32C, k32), ("df64", ng.NG_DF64, "k_step_bulkdf<1>")):
             rm = propagate(prec, False)
             stm, flagsm = ctx.status_sync()
             submit_check(name)

@@ -341,13 +341,38 @@ __device__ __forceinline__ Mat<1> kpval(const KP& k, int i) {
     return r;
 }
 
+// Tuning of the two-problems-per-thread kernel: blocks per SM it is compiled for, and how far
+// the unit-weight middle of each Gregory sum is unrolled (more loads in flight per thread)
+#ifndef NG_F32P_MINB
+#define NG_F32P_MINB 8
+#endif
+#ifndef NG_F32P_UNROLL
+#define NG_F32P_UNROLL 4
+#endif
+
+// greg_for with the unit-weight middle unrolled U times
+template <int U, class F>
+__device__ __forceinline__ void greg_for_u(const NgWeights& W, int L, int lmax, F&& f) {
+    const int k = W.k;
+    if (L <= 2 * k + 1) {
+        for (int l = 0; l <= lmax; ++l) f(l, W.greg[L][l]);
+        return;
+    }
+    const int e1 = min(k, lmax);
+    for (int l = 0; l <= e1; ++l) f(l, W.omega[l]);
+    const int e2 = min(L - k - 1, lmax);
+#pragma unroll U
+    for (int l = k + 1; l <= e2; ++l) f(l, 1.0);
+    for (int l = L - k; l <= lmax; ++l) f(l, W.omega[L - l]);
+}
+
 __device__ __forceinline__ void ret_item32p(const NgWeights& W, const Grid& g, const HermV& G, const HermV32& G32,
                                             const HermV32& S32, const cplx* minv_ws, int n, int m, int kb,
                                             int* status) {
     const int L = n - m;
     KP acc = kpzero();
     const int64_t rowS = tri(n);
-    greg_for(W, L, L - 1, [&](int l, double w) {
+    greg_for_u<NG_F32P_UNROLL>(W, L, L - 1, [&](int l, double w) {
         kpfma(acc, pscal((float)w, ldp(S32.ret, rowS + m + l, kb)), ldp(G32.ret, tri(m + l) + m, kb));
     });
     for (int i = 0; i < 2; ++i) {
@@ -366,7 +391,7 @@ __device__ __forceinline__ void tv_item32p(const NgWeights& W, const Grid& g, co
     KP acc = kpzero();
     const int64_t rowS = tri(n);
     const int T1 = g.ntau + 1;
-    greg_for(W, n, n - 1, [&](int j, double w) {
+    greg_for_u<NG_F32P_UNROLL>(W, n, n - 1, [&](int j, double w) {
         kpfma(acc, pscal((float)w, ldp(S32.ret, rowS + j, kb)), ldp(G32.tv, (int64_t)j * T1 + m, kb));
     });
     for (int i = 0; i < 2; ++i) {
@@ -394,18 +419,18 @@ __device__ __forceinline__ void les_item32p(const NgWeights& W, const Grid& g, c
         }
     } else {
         const int64_t rowG = tri(m);
-        greg_for(W, m, m, [&](int j, double w) {
+        greg_for_u<NG_F32P_UNROLL>(W, m, m, [&](int j, double w) {
             kpfma(c1, pscal((float)w, ldp(G32.ret, rowG + j, kb)), ldp(S32.les, colS + j, kb));
         });
     }
     KP c3 = kpzero();
     const int64_t rowGt = (int64_t)m * T1, rowSt = (int64_t)n * T1;
-    greg_for(W, T, T, [&](int j, double w) {
+    greg_for_u<NG_F32P_UNROLL>(W, T, T, [&](int j, double w) {
         kpfma_db(c3, pscal((float)w, ldp(G32.tv, rowGt + j, kb)), ldp(S32.tv, rowSt + T - j, kb));
     });
     KP hist = kpzero();
     const int64_t rowS = tri(n), colM = tri(m);
-    greg_for(W, n, n - 1, [&](int l, double w) {
+    greg_for_u<NG_F32P_UNROLL>(W, n, n - 1, [&](int l, double w) {
         P32 gl = (l >= m) ? ldp(G32.les, tri(l) + m, kb) : pndag(ldp(G32.les, colM + l, kb));
         kpfma_db(hist, pscal((float)w, gl), ldp(S32.ret, rowS + l, kb));
     });
@@ -422,7 +447,7 @@ __device__ __forceinline__ void les_item32p(const NgWeights& W, const Grid& g, c
 }
 
 // nf = 1, nb even: items are (column, problem pair), pair index fastest
-__global__ void __launch_bounds__(128, 8) k_step_bulk32p(Grid g, int n, HermV G, HermV S, HermV32 G32, HermV32 S32,
+__global__ void __launch_bounds__(128, NG_F32P_MINB) k_step_bulk32p(Grid g, int n, HermV G, HermV S, HermV32 G32, HermV32 S32,
                                                       const cplx* minv_ws, int nb_les, int nb_tv, int nb_ret,
                                                       const cplx* tvq, int* status) {
     const NgWeights& W = c_W[g.k - 1];
