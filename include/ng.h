@@ -247,8 +247,9 @@ ng_status ng_precision_reset(ng_ctx *ctx);
  * given kernel, Fcc = F^ddagger its hermitian partner (the values of F outside the stored
  * triangles; pass F itself when F is hermitian symmetric), Q a hermitian source; G is hermitian
  * when F * Q = Q * F^ddagger (Eq. ,masbX,.), e.g. F = -G0 * Sigma, Fcc = -Sigma * G0, Q = G0 for
- * the Dyson series.  G: ldk = nbatch; F, Fcc, Q: ldk 1 or nbatch.  nf = 1, 2 (NG_EUNSUPPORTED
- * otherwise).  grid.sig = +1 solves for bosonic functions (e.g. the susceptibility of Eq.
+ * the Dyson series.  G: ldk = nbatch; F, Fcc, Q: ldk 1 or nbatch.  nf = 1, 2, 4
+ * (NG_EUNSUPPORTED otherwise; nf = 4 keeps its 4 x 4 blocks per thread and is meant for small
+ * batches such as a real-space cluster).  grid.sig = +1 solves for bosonic functions (e.g. the susceptibility of Eq.
  * dyson_chi).  Preconditions follow Table tab:vie2. */
 
 /* Matsubara slice: the k-th order discretised G^M + [F * G]^M = Q^M (Eqs. cm1, cm2), solved
@@ -511,7 +512,7 @@ ng_status ng_gw_sigma_timestep(ng_ctx *ctx, const ng_grid *grid, int tstp, ng_he
  * in the bootstrapping, ng_vie2_timestep(n) in every corrector pass), then dW and Sigma.
  * Chi: caller-owned bosonic herm (ldk = 1, whole contour) receiving chi; P, K, K^ddagger are
  * kept in the context, so a run continued with do_setup = 0 must follow a GW run on the same
- * context and grid.  nf = 1, 2.  Otherwise as ng_run_2b. */
+ * context and grid.  nf = 1, 2, 4.  Otherwise as ng_run_2b. */
 ng_status ng_run_gw(ng_ctx *ctx, const ng_grid *grid, ng_herm G, ng_herm Gloc, ng_herm Sigma, ng_herm Chi,
                     ng_func eps0, ng_func eps_mf, ng_func U, const ng_run_params *p, int *iters_out, void *stream);
 

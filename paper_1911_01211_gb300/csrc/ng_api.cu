@@ -574,6 +574,16 @@ ng_status launch_vie2_mat(ng_ctx* c, const Grid& g, const HermV& G, const HermV&
     return check_launch(c, "k_mat_store");
 }
 
+ng_status vie2_mat_d(ng_ctx* c, const Grid& g, const HermV& G, const HermV& F, const HermV& Q, cudaStream_t s,
+                     void** ws, size_t* ws_bytes) {
+    switch (g.nf) {
+    case 1: return launch_vie2_mat<1>(c, g, G, F, Q, s, ws, ws_bytes);
+    case 2: return launch_vie2_mat<2>(c, g, G, F, Q, s, ws, ws_bytes);
+    case 4: return launch_vie2_mat<4>(c, g, G, F, Q, s, ws, ws_bytes);
+    default: return fail(c, NG_EUNSUPPORTED, "the vie2 solver supports nf = 1, 2, 4");
+    }
+}
+
 template <int D>
 ng_status launch_free(ng_ctx* c, const Grid& g, const HermV& G, const cplx* eps_dev, double scale, cudaStream_t s) {
     const int64_t nel = (g.ntau + 1) + 2 * tri(g.nt + 1) + (int64_t)(g.nt + 1) * (g.ntau + 1);
@@ -1073,7 +1083,7 @@ static ng_status vie2_args(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm F,
                            Grid* g, HermV* Gv, HermV* Fv, HermV* Fccv, HermV* Qv) {
     ng_status st;
     if ((st = check_grid(c, grid, g, true))) return st;
-    if (g->nf > 2) return fail(c, NG_EUNSUPPORTED, "the vie2 solver supports nf <= 2");
+    if (g->nf > 4) return fail(c, NG_EUNSUPPORTED, "the vie2 solver supports nf = 1, 2, 4");
     if ((st = check_herm(c, *g, G, "G", rt, Gv, g->nb))) return st;
     if ((st = check_herm(c, *g, F, "F", rt, Fv, 0))) return st;
     if ((st = check_herm(c, *g, Fcc, "Fcc", rt, Fccv, 0))) return st;
@@ -1086,8 +1096,7 @@ ng_status ng_vie2_mat(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm F, ng_h
     ng_status st;
     if ((st = vie2_args(c, grid, G, F, F, Q, false, &g, &Gv, &Fv, &Fccv, &Qv))) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    return g.nf == 1 ? launch_vie2_mat<1>(c, g, Gv, Fv, Qv, s, &c->ws_mat, &c->ws_mat_bytes)
-                     : launch_vie2_mat<2>(c, g, Gv, Fv, Qv, s, &c->ws_mat, &c->ws_mat_bytes);
+    return vie2_mat_d(c, g, Gv, Fv, Qv, s, &c->ws_mat, &c->ws_mat_bytes);
 }
 
 ng_status ng_vie2_start(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm F, ng_herm Fcc, ng_herm Q, void* stream) {
@@ -1430,8 +1439,7 @@ static ng_status run_2b_impl(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm 
         }
         cudaError_t e = cudaSuccess;
         if (from < 0) {
-            r = g.nf == 1 ? launch_vie2_mat<1>(c, gw->gb, gw->X, gw->K, gw->P, s, &c->ws_gwmat, &c->ws_gwmat_bytes)
-                          : launch_vie2_mat<2>(c, gw->gb, gw->X, gw->K, gw->P, s, &c->ws_gwmat, &c->ws_gwmat_bytes);
+            r = vie2_mat_d(c, gw->gb, gw->X, gw->K, gw->P, s, &c->ws_gwmat, &c->ws_gwmat_bytes);
             if (r) return r;
         } else if (from == 0) {
             e = vie2_start_launch(gw->gb, gw->X, gw->K, gw->Kcc, gw->P, (cplx*)c->ws_st, c->d_status, s);
@@ -1606,7 +1614,7 @@ static ng_status gwk_slice_buffers(ng_ctx* c, const Grid& g, GwRt* gw) {
 // the ring, the compact real-space slice buffers
 static ng_status gw_prepare(ng_ctx* c, const Grid& g, ng_herm Chi, bool kspace, GwRt* gw) {
     ng_status st;
-    if (g.nf > 2) return fail(c, NG_EUNSUPPORTED, "the GW driver supports nf <= 2");
+    if (g.nf > 4) return fail(c, NG_EUNSUPPORTED, "the GW driver supports nf = 1, 2, 4");
     if (kspace && g.nf != 1) return fail(c, NG_EUNSUPPORTED, "the k-space GW is one-band (nf = 1)");
     if (kspace && g.nb > 4096) return fail(c, NG_EUNSUPPORTED, "the k-space GW supports at most 4096 momenta");
     const int L = kspace ? g.nb : 1;

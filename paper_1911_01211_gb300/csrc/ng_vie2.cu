@@ -37,10 +37,20 @@ cudaError_t vie2_load_weights(const NgWeights* all) {
 
 cudaError_t vie2_start_launch(const Grid& g, const HermV& G, const HermV& F, const HermV& Fcc, const HermV& Q,
                               cplx* ws, int* status, cudaStream_t s) {
-    return g.nf == 1 ? start_d<1>(g, G, F, Fcc, Q, ws, status, s) : start_d<2>(g, G, F, Fcc, Q, ws, status, s);
+    switch (g.nf) {
+    case 1: return start_d<1>(g, G, F, Fcc, Q, ws, status, s);
+    case 2: return start_d<2>(g, G, F, Fcc, Q, ws, status, s);
+    case 4: return start_d<4>(g, G, F, Fcc, Q, ws, status, s);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t vie2_step_launch(const Grid& g, int n, const HermV& G, const HermV& F, const HermV& Fcc, const HermV& Q,
                              const cplx* tvq, int* status, cudaStream_t s) {
-    return g.nf == 1 ? step_d<1>(g, n, G, F, Fcc, Q, tvq, status, s) : step_d<2>(g, n, G, F, Fcc, Q, tvq, status, s);
+    switch (g.nf) {
+    case 1: return step_d<1>(g, n, G, F, Fcc, Q, tvq, status, s);
+    case 2: return step_d<2>(g, n, G, F, Fcc, Q, tvq, status, s);
+    case 4: return step_d<4>(g, n, G, F, Fcc, Q, tvq, status, s);
+    default: return cudaErrorInvalidValue;
+    }
 }

@@ -61,6 +61,20 @@ def hubbard_dimer(nt=1000, ntau=400, beta=20.0, h=0.02, korder=5, J=1.0, U0=1.0,
     return Workload("hubbard_dimer", nt, ntau, 2, 1, korder, h, beta, corrector=corrector, eps0=eps0, U=U)
 
 
+def hubbard_chain(M=4, nt=1000, ntau=400, beta=20.0, h=0.02, korder=5, J=1.0, U=1.5, w0=5.0, mu=0.0, nbar=0.5,
+                  corrector=3):
+    """Open Hubbard chain of M sites in real space (nf = M, one problem), hopping -J between
+    neighbours, excited at t = 0 by the quench of the first site's on-site energy to w0
+    (eps0_n = eps + w0 |1><1| for n >= 0, eps0_{-1} = eps)."""
+    eps = np.zeros((M, M), dtype=complex)
+    for i in range(M - 1):
+        eps[i, i + 1] = eps[i + 1, i] = -J
+    eps0 = np.broadcast_to(eps[None, :, :, None], (nt + 2, M, M, 1)).copy()
+    eps0[1:, 0, 0, 0] += w0
+    return Workload("hubbard_chain", nt, ntau, M, 1, korder, h, beta, corrector=corrector, eps0=eps0,
+                    U=np.full(nt + 2, U), mu=mu, nbar=nbar)
+
+
 def chain_kspace(nk=512, nt=2000, ntau=800, beta=10.0, h=0.01, korder=5, U=2.0, corrector=3,
                  A0=0.5, omega=2.0, t0=5.0, sigma=1.5):
     k = 2 * np.pi * np.arange(nk) / nk

@@ -4,11 +4,12 @@
   chi (d = 1, 2; the random equal-time G^< is not anti-hermitian, so the diagonal rule is
   exercised) at 1e-14 relative;
 * the bosonic convolution P * P (grid.sig = +1) at 1e-12;
-* the self-consistent ng_run_gw for the Hubbard dimer after an interaction quench and for a
-  k-space chain (local GW), G, Sigma and chi compared on every stored element at 1e-10;
+* the self-consistent ng_run_gw for the Hubbard dimer after an interaction quench, the open
+  4-site chain (nf = 4) and a k-space chain (local GW), G, Sigma and chi compared on every
+  stored element at 1e-10;
 * the k-space GW (Eqs. Sigmak, Pol): the FFT-based slice calls against the oracle's momentum
-  sums (nk = 4 radix-2, nk = 6 direct transform) at 1e-13, and ng_run_gw_kspace against
-  drivers.run_gw_kspace at 1e-10.
+  sums (nk = 4, 32, 128 radix-2, nk = 6, 12 direct transform) at 1e-13, and ng_run_gw_kspace
+  against drivers.run_gw_kspace at 1e-10.
 """
 import numpy as np
 import pytest
@@ -137,6 +138,31 @@ def test_run_gw_hubbard_dimer(ng):
     _check(herm_to_oracle(X, g, 0), chain.chi)
 
 
+def test_run_gw_four_site_chain(ng):
+    """Real-space GW of the open 4-site Hubbard chain at quarter filling after the quench of the
+    first site (the paper's M = 4 chain example: U = 1.5, nbar = 1/4, w0 = 5; nf = 4 contour
+    functions, chi by the nf = 4 vie2) against drivers.run_gw on every stored element."""
+    w = wl.hubbard_chain(M=4, nt=20, ntau=16, beta=5.0, h=0.05, U=1.5, w0=5.0, mu=-1.0, nbar=0.25)
+    g = _grid(ng, w)
+    ctx = ng.Context(w.korder)
+    G = ng.Herm(g)
+    L, S, X = ng.Herm(g, ldk=1), ng.Herm(g, ldk=1), ng.Herm(g, ldk=1)
+    e0 = ng.Func(g, values=torch.from_numpy(w.eps0))
+    mf = ng.Func(g)
+    U = ng.Func(g, scalar=True)
+    U.val[:, 0, 0, 0] = torch.from_numpy(w.U.astype(complex))
+    ctx.run_gw(g, G, L, S, X, e0, mf, U, corrector=w.corrector, nbar=w.nbar)
+    _status_ok(ctx, ng)
+    ctx.close()
+    Uo = OFunc(w.nt, 1)
+    Uo.val[:, 0, 0] = w.U
+    st, chain = drivers.run_gw([_ofunc(w.eps0, 0)], Uo, w.nt, w.ntau, w.beta, w.h, Weights(w.korder), mu=w.mu,
+                               nbar=w.nbar, corrector=w.corrector)
+    _check(herm_to_oracle(G, g, 0), st.G[0])
+    _check(herm_to_oracle(S, g, 0), st.S)
+    _check(herm_to_oracle(X, g, 0), chain.chi)
+
+
 def test_run_gw_local_on_kspace_chain(ng):
     """A k-space chain (nk = 4, nf = 1) with the local GW self-energy of Gloc."""
     w = wl.chain_kspace(nk=4, nt=24, ntau=20, beta=4.0, h=0.05)
@@ -148,10 +174,11 @@ def test_run_gw_local_on_kspace_chain(ng):
 
 
 # ---- k-space GW (Eqs. Sigmak, Pol): FFTs along k on the GPU, momentum sums in the oracle ----
-@pytest.mark.parametrize("nk", [4, 6])
+@pytest.mark.parametrize("nk", [4, 6, 12, 32, 128])
 def test_gw_kspace_slices_match_oracle(ng, nk):
-    """ng_gw_kspace_polarization_timestep / _sigma_timestep (radix-2 FFT for nk = 4, the direct
-    transform for nk = 6) against the oracle's momentum sums from seeded random G_k and chi_k."""
+    """ng_gw_kspace_polarization_timestep / _sigma_timestep (radix-2 FFT for nk = 4, 32 and the
+    benchmark's 128, the direct transform for nk = 6, 12) against the oracle's momentum sums from
+    seeded random G_k and chi_k."""
     N, T, beta, h, k = 12, 14, 2.0, 0.05, 5
     rng = np.random.default_rng(1900 + nk)
     Gk = [_random_herm(rng, N, T, 1, 1.0) for _ in range(nk)]

@@ -38,7 +38,7 @@ def _compare(G, ref, N, upto=None):
             "les": _rel(G.les[low.T], ref.les[low.T]), "tv": _rel(G.tv[:upto + 1], ref.tv[:upto + 1])}
 
 
-@pytest.mark.parametrize("d", [1, 2])
+@pytest.mark.parametrize("d", [1, 2, 4])
 def test_vie2_downfolding_solve(ng, d):
     k, N, T, beta, h, nb = 5, 24, 30, 1.5, 0.05, 2
     W = Weights(k)
@@ -85,7 +85,7 @@ def _random_herm(rng, N, T, d, scale):
 
 
 @pytest.mark.parametrize("tvsrc", ["fft", "direct"])
-@pytest.mark.parametrize("d", [1, 2])
+@pytest.mark.parametrize("d", [1, 2, 4])
 def test_vie2_steps_from_random_data(ng, d, tvsrc):
     """Matsubara, start-up and the steps n = k+1, 2k+1, 2k+2, N from a random history, with F,
     Fcc and Q drawn independently (single steps are linear in their inputs); the left-mixing
