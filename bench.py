@@ -764,9 +764,9 @@ def run_adjoint(a):
     A0[0] = 0.0
     Ut = torch.full((nt + 2,), U, dtype=torch.float64, device="cuda")
 
-    def loss(A):
+    def loss(A, segment=0):
         e0 = -2.0 * torch.cos(kx[None, :] - A[:, None]) - 2.0 * torch.cos(ky[None, :])
-        rho = densities(e0, ctx, g, Ut)
+        rho = densities(e0, ctx, g, Ut, segment=segment)
         return (rho[nt].real * e0[nt + 1]).mean()
 
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
@@ -784,6 +784,23 @@ def run_adjoint(a):
     clk = clocks.stop()
     t_fwd, t_bwd = ev[0].elapsed_time(ev[1]) / 1e3, ev[1].elapsed_time(ev[2]) / 1e3
     grad = At.grad.cpu().numpy()
+    # the same gradient with every corrector iterate kept by the forward (no recomputation)
+    Ar = torch.tensor(A0, dtype=torch.float64, device="cuda", requires_grad=True)
+    torch.cuda.synchronize()
+    ev[0].record()
+    Lr = loss(Ar, segment=ng.NG_ADJ_RECORDED)
+    ev[1].record()
+    Lr.backward()
+    ev[2].record()
+    torch.cuda.synchronize()
+    t_fwd_rec, t_bwd_rec = ev[0].elapsed_time(ev[1]) / 1e3, ev[1].elapsed_time(ev[2]) / 1e3
+    grad_rec = Ar.grad.cpu().numpy()
+    recorded = {"forward_s": t_fwd_rec, "backward_s": t_bwd_rec, "backward_over_forward": t_bwd_rec / t_fwd_rec,
+                "max_abs_diff_vs_checkpointed": float(np.abs(grad_rec - grad).max()),
+                "iterate_store_gb": 16e-9 * (nt - 5) * 3 * ((L * L + 2) * (2 * nt + ntau + 3) + L * L),
+                "what": "ng_adjoint_forward keeps every corrector iterate; ng_adjoint_2b(segment=NG_ADJ_RECORDED) "
+                        "walks back without recomputing the forward"}
+    del Lr, Ar
     rng = np.random.default_rng(191101211)
     idx = sorted(rng.choice(np.arange(2, nt + 2), a.fd_slices, replace=False).tolist()) if a.fd_slices > 0 else []
     # Finite differences of the GPU forward.  A(t_n) (index i = n + 1) enters the run from step
@@ -849,6 +866,7 @@ def run_adjoint(a):
                                    "loss E_kin(t_N), parameters A(t_1..t_N)",
                        "segment_steps": int(np.ceil(np.sqrt(nt - 5)))},
             "forward_s": t_fwd, "backward_s": t_bwd, "backward_over_forward": t_bwd / t_fwd,
+            "recorded_iterates": recorded,
             "loss": Lv.item(),
             "fd_check": {"slices": [int(i) - 1 for i in idx],
                          "how": "central differences of the GPU forward at each delta and the fourth-order stencil "

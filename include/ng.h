@@ -559,7 +559,8 @@ ng_status ng_solve_fixed(ng_ctx *ctx, const ng_grid *grid, ng_herm G, ng_herm Si
  * (mat unused), overwritten with the cotangents of the final history.
  * The corrector iterates are recomputed from the kept history in segments of `segment` steps
  * (0: ceil(sqrt(nt - k))), each re-run forward with its iterates held in the context, then
- * walked backwards.  The start slices are a fixed point of the bootstrapping; their adjoint
+ * walked backwards; segment = NG_ADJ_RECORDED uses the iterates that ng_adjoint_forward kept
+ * for this G (no recomputation).  The start slices are a fixed point of the bootstrapping; their adjoint
  * is iterated to |change| <= p->boot_tol |mu| (default 1e-14), at most p->boot_maxiter times.
  * grad_eps0 (device, [nt+2][nbatch] double): dL/deps0_kb(t_n) at index n+1 (row 0 unused).
  * G, Sigma and eps_mf are rewritten with bitwise-equal values by the recomputation; Gloc is
@@ -567,6 +568,18 @@ ng_status ng_solve_fixed(ng_ctx *ctx, const ng_grid *grid, ng_herm G, ng_herm Si
  * info (host, may be NULL) receives {start-slice iterations, segments, segment length}.
  * Errors: NG_EUNSUPPORTED for nf != 1; NG_EINVAL for bad layouts; NG_ENOCONV if the start-slice
  * adjoint did not converge; NG_ENOMEM if the context workspace cannot be allocated. */
+#define NG_ADJ_RECORDED (-1)
+
+/* ng_run_2b (do_setup = 1, stepping k+1..nt, FP64) that also keeps every corrector iterate of
+ * every step (G_k, Gloc and Sigma slices, eps_mf) in the context for a following
+ * ng_adjoint_2b(segment = NG_ADJ_RECORDED), which then needs no forward recomputation: it
+ * trades (nt - k) p->corrector ((nbatch + 2)(2 nt + ntau + 3) + nbatch) complex values of device
+ * memory for one forward run.  Same arguments, checks and results as ng_run_2b; nf = 1.  Any other
+ * adjoint call on the context (segment >= 0) releases the record. */
+ng_status ng_adjoint_forward(ng_ctx *ctx, const ng_grid *grid, ng_herm G, ng_herm Gloc, ng_herm Sigma,
+                             ng_func eps0, ng_func eps_mf, ng_func U, const ng_run_params *p, int *iters_out,
+                             void *stream);
+
 ng_status ng_adjoint_2b(ng_ctx *ctx, const ng_grid *grid, ng_herm G, ng_herm Gloc, ng_herm Sigma,
                         ng_func eps0, ng_func eps_mf, ng_func U, const ng_run_params *p,
                         const void *seed, ng_herm cG, ng_herm cS, int segment, double *grad_eps0,

@@ -26,6 +26,7 @@ LIB_PATH = os.path.join(_HERE, "libng.so")
 NG_FP64, NG_F32C, NG_DF64 = 0, 1, 2
 NG_MIXED, NG_SERIAL = 0, 1
 NG_TVSRC_AUTO, NG_TVSRC_DIRECT = 0, 1
+NG_ADJ_RECORDED = -1
 _STATUS_NAMES = ["NG_OK", "NG_EINVAL", "NG_ENOMEM", "NG_ECUDA", "NG_ENOCONV", "NG_ETIMEOUT",
                  "NG_ENONFINITE", "NG_EUNSUPPORTED", "NG_ESCRATCH", "NG_ECOMM", "NG_ESINGULAR"]
 
@@ -133,6 +134,8 @@ SIGNATURES = {
     "ng_adjoint_2b": (ctypes.c_int, [_P, _G, ng_herm, ng_herm, ng_herm, ng_func, ng_func, ng_func,
                                      ctypes.POINTER(ng_run_params), _P, ng_herm, ng_herm, ctypes.c_int, _P,
                                      ctypes.POINTER(ctypes.c_int), _P]),
+    "ng_adjoint_forward": (ctypes.c_int, [_P, _G, ng_herm, ng_herm, ng_herm, ng_func, ng_func, ng_func,
+                                          ctypes.POINTER(ng_run_params), ctypes.POINTER(ctypes.c_int), _P]),
 }
 
 _lib = None
@@ -525,6 +528,17 @@ class Context:
             raise exchange.error
         if not (allow_noconv and st == NG_ENOCONV):
             self._chk(st)
+        return list(iters)
+
+    def adjoint_forward(self, grid, G, Gloc, S, eps0, eps_mf, U, corrector=3, mats_tol=1e-14, mats_maxiter=200,
+                        boot_tol=1e-14, boot_maxiter=200, nbar=0.5, stream=None):
+        """ng_adjoint_forward: ng_run_2b keeping every corrector iterate for
+        adjoint_2b(segment=NG_ADJ_RECORDED)."""
+        p = ng_run_params(corrector, mats_tol, mats_maxiter, boot_tol, boot_maxiter, nbar, grid.korder + 1, grid.nt,
+                          1, NG_FP64)
+        iters = (ctypes.c_int * 2)()
+        self._chk(self.lib.ng_adjoint_forward(self.h, ctypes.byref(grid.c()), G.c(), Gloc.c(), S.c(), eps0.c(),
+                                              eps_mf.c(), U.c(), ctypes.byref(p), iters, _stream(stream)))
         return list(iters)
 
     def adjoint_2b(self, grid, G, Gloc, S, eps0, eps_mf, U, seed, cG, cS, grad_eps0, corrector=3, nbar=0.5,

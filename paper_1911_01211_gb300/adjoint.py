@@ -10,7 +10,7 @@ directions run in the CUDA kernels of libng.so.
 """
 import torch
 
-from . import Func, Herm, NG_FP64, tri
+from . import NG_ADJ_RECORDED, NG_FP64, Func, Herm, tri
 
 
 class Dyson2B(torch.autograd.Function):
@@ -25,8 +25,11 @@ class Dyson2B(torch.autograd.Function):
         G = Herm(g, zero=False)
         Gl, S = Herm(g, ldk=1), Herm(g, ldk=1)
         mf = Func(g)
-        ngctx.run_2b(g, G, Gl, S, e0, mf, uf, corrector=corrector, nbar=nbar, mats_tol=1e-14, boot_tol=1e-14,
-                     precision=NG_FP64)
+        if segment == NG_ADJ_RECORDED:   # keep every corrector iterate: no recomputation backwards
+            ngctx.adjoint_forward(g, G, Gl, S, e0, mf, uf, corrector=corrector, nbar=nbar)
+        else:
+            ngctx.run_2b(g, G, Gl, S, e0, mf, uf, corrector=corrector, nbar=nbar, mats_tol=1e-14, boot_tol=1e-14,
+                         precision=NG_FP64)
         diag = torch.tensor([tri(n) + n for n in range(g.nt + 1)], device=eps0.device)
         rho = -1j * G.les[diag, 0, 0, :]
         ctx.saved = (ngctx, g, G, Gl, S, e0, mf, uf, corrector, nbar, segment)
@@ -48,5 +51,7 @@ class Dyson2B(torch.autograd.Function):
 
 
 def densities(eps0, ngctx, grid, U, corrector=3, nbar=0.5, segment=0, state=None):
-    """rho_kb(t_n) for n = 0..nt, differentiable with respect to eps0."""
+    """rho_kb(t_n) for n = 0..nt, differentiable with respect to eps0.  segment: steps per
+    recomputed segment of the backward pass (0: ceil(sqrt(nt - k))), or NG_ADJ_RECORDED to keep
+    every corrector iterate of the forward in device memory instead."""
     return Dyson2B.apply(eps0, ngctx, grid, U, corrector, nbar, segment, state)

@@ -83,6 +83,11 @@ struct ng_ctx {
     size_t ws_usrc_bytes = 0;
     void* ws_adj = nullptr;          // adjoint: iterate store, work vectors, start-slice buffers
     size_t ws_adj_bytes = 0;
+    // the corrector iterates of every step held in ws_adj by ng_adjoint_forward, for
+    // ng_adjoint_2b(segment = NG_ADJ_RECORDED); the shape they were recorded for
+    bool adj_rec = false;
+    int adj_rec_nt = 0, adj_rec_ntau = 0, adj_rec_nb = 0, adj_rec_corr = 0;
+    const void* adj_rec_G = nullptr;
     // tuned bulk block sizes of earlier batches, by batch shape (problems per nf, largest
     // ntau, largest nt in steps of 256)
     std::vector<std::pair<std::vector<int>, int>> tune_cache;
@@ -2309,6 +2314,54 @@ ng_status adj_boot(ng_ctx* c, const Grid& g, const HermV& Gv, const HermV& Lv, c
 
 }  // namespace
 
+// the second-Born forward run with every corrector iterate kept for the adjoint: the setup of
+// ng_run_2b, then each time step through the capturing forward step of the recomputation
+extern "C" ng_status ng_adjoint_forward(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm Gloc, ng_herm S,
+                                        ng_func eps0, ng_func epsmf, ng_func U, const ng_run_params* p,
+                                        int* iters_out, void* stream) {
+    Grid g;
+    HermV Gv, Lv, Sv;
+    FuncV e0, mf, uv;
+    ng_status st;
+    if ((st = check_grid(c, grid, &g))) return st;
+    if (g.nf != 1) return fail(c, NG_EUNSUPPORTED, "ng_adjoint_forward supports nf = 1 (nf = %d)", g.nf);
+    if (!p) return fail(c, NG_EINVAL, "params is NULL");
+    if (p->corrector < 1) return fail(c, NG_EINVAL, "corrector must be >= 1");
+    if (G.ldk != g.nb) return fail(c, NG_EINVAL, "G must have ldk = nbatch");
+    if ((st = check_herm(c, g, G, "G", true, &Gv, g.nb))) return st;
+    if (Gloc.ldk != 1 || S.ldk != 1) return fail(c, NG_EINVAL, "Gloc and Sigma must have ldk = 1");
+    if ((st = check_herm(c, g, Gloc, "Gloc", true, &Lv, 1))) return st;
+    if ((st = check_herm(c, g, S, "Sigma", true, &Sv, 1))) return st;
+    if ((st = check_func(c, g, eps0, "eps0", &e0))) return st;
+    if ((st = check_func(c, g, epsmf, "eps_mf", &mf))) return st;
+    if ((st = check_func(c, g, U, "U", &uv))) return st;
+    if (U.ldk != 1 || epsmf.ldk != g.nb || eps0.ldk != g.nb)
+        return fail(c, NG_EINVAL, "U.ldk must be 1 and eps0.ldk, eps_mf.ldk must be nbatch");
+    c->adj_rec = false;
+    const int k = g.k, nsteps = g.nt - k;
+    AdjLayout A;
+    const size_t need = adj_layout(g, nsteps, p->corrector, &A, nullptr);
+    if ((st = ensure(c, &c->ws_adj, &c->ws_adj_bytes, need))) return st;
+    adj_layout(g, nsteps, p->corrector, &A, (char*)c->ws_adj);
+    ng_run_params q = *p;
+    q.n_from = k + 1;
+    q.n_to = k;            // setup only: Matsubara loop and bootstrapping
+    q.do_setup = 1;
+    q.precision = NG_FP64;
+    if ((st = run_2b_impl(c, grid, G, Gloc, S, eps0, epsmf, U, &q, nullptr, nullptr, iters_out, stream))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int n = k + 1; n <= g.nt; ++n)
+        if ((st = adj_forward_step(c, g, n, p->corrector, Gv, Lv, Sv, mf, e0, uv, p->nbar, A, n - (k + 1), s)))
+            return st;
+    c->adj_rec = true;
+    c->adj_rec_nt = g.nt;
+    c->adj_rec_ntau = g.ntau;
+    c->adj_rec_nb = g.nb;
+    c->adj_rec_corr = p->corrector;
+    c->adj_rec_G = G.ret;
+    return NG_OK;
+}
+
 extern "C" ng_status ng_adjoint_2b(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm Gloc, ng_herm S, ng_func eps0,
                                    ng_func epsmf, ng_func U, const ng_run_params* p, const void* seed, ng_herm cG,
                                    ng_herm cS, int segment, double* grad_eps0, int* info, void* stream) {
@@ -2336,8 +2389,14 @@ extern "C" ng_status ng_adjoint_2b(ng_ctx* c, const ng_grid* grid, ng_herm G, ng
     cudaStream_t s = (cudaStream_t)stream;
     const int k = g.k, nb = g.nb, T = g.ntau, N = g.nt;
     const int nsteps = N - k;
-    int seg = segment > 0 ? segment : (int)std::ceil(std::sqrt((double)nsteps));
+    const bool recorded = segment == NG_ADJ_RECORDED;
+    if (recorded && !(c->adj_rec && c->adj_rec_nt == N && c->adj_rec_ntau == T && c->adj_rec_nb == nb &&
+                      c->adj_rec_corr == p->corrector && c->adj_rec_G == G.ret))
+        return fail(c, NG_EINVAL, "segment = NG_ADJ_RECORDED needs a preceding ng_adjoint_forward of this G and shape");
+    if (segment < 0 && !recorded) return fail(c, NG_EINVAL, "segment = %d invalid", segment);
+    int seg = recorded ? nsteps : (segment > 0 ? segment : (int)std::ceil(std::sqrt((double)nsteps)));
     seg = std::max(1, std::min(seg, nsteps));
+    if (!recorded) c->adj_rec = false;   // the recomputation reuses the store
     AdjLayout A;
     const size_t need = adj_layout(g, seg, p->corrector, &A, nullptr);
     if ((st = ensure(c, &c->ws_adj, &c->ws_adj_bytes, need))) return st;
@@ -2357,7 +2416,7 @@ extern "C" ng_status ng_adjoint_2b(ng_ctx* c, const ng_grid* grid, ng_herm G, ng
     int nseg = 0;
     for (int s1 = N; s1 > k; s1 -= seg, ++nseg) {
         const int s0 = std::max(k + 1, s1 - seg + 1);
-        for (int n = s0; n <= s1; ++n)
+        for (int n = s0; n <= s1 && !recorded; ++n)
             if ((st = adj_forward_step(c, g, n, p->corrector, Gv, Lv, Sv, mf, e0, uv, p->nbar, A, n - s0, s)))
                 return st;
         for (int n = s1; n >= s0; --n)

@@ -129,6 +129,18 @@ def test_adjoint_segment_length_does_not_change_the_gradient(ng):
     _, g0 = p.grad(A, segment=0)       # ceil(sqrt(nt - k)) steps per segment
     _, g1 = p.grad(A, segment=1)
     _, g2 = p.grad(A, segment=nt)
+    _, g3 = p.grad(A, segment=ng.NG_ADJ_RECORDED)   # iterates kept by the forward, none recomputed
     scale = np.abs(g0).max()
     assert np.abs(g1 - g0).max() <= 1e-13 * scale
     assert np.abs(g2 - g0).max() <= 1e-13 * scale
+    assert np.abs(g3 - g0).max() <= 1e-13 * scale
+    # a checkpointed backward reuses the store and releases the record: a recorded backward
+    # after it is refused
+    p.grad(A, segment=0)
+    with pytest.raises(ng.NgError):
+        p.ctx.adjoint_2b(p.g, ng.Herm(p.g), ng.Herm(p.g, ldk=1), ng.Herm(p.g, ldk=1), ng.Func(p.g), ng.Func(p.g),
+                         ng.Func(p.g, scalar=True), torch.zeros((nt + 1, L * L), dtype=torch.complex128,
+                                                                device="cuda"),
+                         ng.Herm(p.g), ng.Herm(p.g, ldk=1), torch.zeros((nt + 2, L * L), dtype=torch.float64,
+                                                                        device="cuda"),
+                         segment=ng.NG_ADJ_RECORDED)
