@@ -112,6 +112,13 @@ typedef enum { NG_FP64 = 0, NG_F32C = 1, NG_DF64 = 2 } ng_precision;
  * Both evaluate the same quadrature; they differ by rounding only. */
 typedef enum { NG_TVSRC_AUTO = 0, NG_TVSRC_DIRECT = 1 } ng_tv_source;
 
+/* Parallel decomposition of the FP64 time-step bulk (ng_set_bulk_split): NG_BULK_THREAD, one
+ * thread per (column, problem) item; NG_BULK_WARP, one warp per item, its history and source
+ * sums split over the 32 lanes and added in a fixed butterfly order (small batches: a dimer,
+ * a real-space cluster); NG_BULK_AUTO (default), the warp form when the batch has fewer items
+ * than 128 per SM.  The two differ by the order of additions only. */
+typedef enum { NG_BULK_AUTO = 0, NG_BULK_THREAD = 1, NG_BULK_WARP = 2 } ng_bulk_split;
+
 /* Schedule of a time step (Sec. "Time stepping"): NG_MIXED is the paper's parallel variant
  * (implementation (B) for the bulk of the retarded row and lesser column, (A) near the
  * diagonal); NG_SERIAL is its serial variant, implementation (A) along the whole retarded row
@@ -232,6 +239,10 @@ ng_status ng_dyson_timestep(ng_ctx *ctx, const ng_grid *grid, int tstp, ng_herm 
  * Arguments as for ng_dyson_start (G with ldk = nbatch; Sigma and eps with ldk = 1 or
  * nbatch); runs on the device that is current when it is called, stream-ordered on `stream`. */
 ng_status ng_dyson_start_noalloc(const ng_grid *grid, ng_herm G, ng_herm Sigma, ng_func eps, void *stream);
+
+/* Choose the decomposition of the FP64 time-step bulk (and of the vie2 time step) on ctx
+ * (ng_bulk_split). */
+ng_status ng_set_bulk_split(ng_ctx *ctx, int mode);
 
 /* Choose the evaluation of the left-mixing source for later time steps on ctx (ng_tv_source). */
 ng_status ng_set_tv_source(ng_ctx *ctx, int mode);

@@ -27,6 +27,7 @@ NG_FP64, NG_F32C, NG_DF64 = 0, 1, 2
 NG_MIXED, NG_SERIAL = 0, 1
 NG_TVSRC_AUTO, NG_TVSRC_DIRECT = 0, 1
 NG_ADJ_RECORDED = -1
+NG_BULK_AUTO, NG_BULK_THREAD, NG_BULK_WARP = 0, 1, 2
 _STATUS_NAMES = ["NG_OK", "NG_EINVAL", "NG_ENOMEM", "NG_ECUDA", "NG_ENOCONV", "NG_ETIMEOUT",
                  "NG_ENONFINITE", "NG_EUNSUPPORTED", "NG_ESCRATCH", "NG_ECOMM", "NG_ESINGULAR"]
 
@@ -127,6 +128,7 @@ SIGNATURES = {
                                                ng_herm, _P]),
     "ng_observables": (ctypes.c_int, [_P, _G, ctypes.c_int, ng_herm, ng_herm, ng_func, ng_func, _P, _P]),
     "ng_dyson_start_noalloc": (ctypes.c_int, [_G, ng_herm, ng_herm, ng_func, _P]),
+    "ng_set_bulk_split": (ctypes.c_int, [_P, ctypes.c_int]),
     "ng_set_tv_source": (ctypes.c_int, [_P, ctypes.c_int]),
     "ng_fp64_probe": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), _P]),
     "ng_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
@@ -352,6 +354,10 @@ class Context:
         self._chk(self.lib.ng_profile_read(self.h, out))
         return dict(zip(("bulk_ms", "bulk_launches", "bulk_flops", "boundary_ms", "boundary_launches", "tvfft_ms",
                          "tvfft_launches", "gw_ms", "gw_evals"), list(out)))
+
+    def set_bulk_split(self, mode):
+        """NG_BULK_AUTO, NG_BULK_THREAD (one thread per bulk item) or NG_BULK_WARP (one warp)."""
+        self._chk(self.lib.ng_set_bulk_split(self.h, mode))
 
     def set_tv_source(self, mode):
         """NG_TVSRC_AUTO (FFT where supported) or NG_TVSRC_DIRECT."""

@@ -9,6 +9,7 @@
 #include "ng_setup.cuh"
 #include "ng_slice.cuh"
 #include "ng_step32.cuh"
+#include "ng_stepsplit.cuh"
 #include "ng_obs.cuh"
 #include "ng_ubatch.cuh"
 #include "ng_stepdf.cuh"
@@ -92,6 +93,7 @@ struct ng_ctx {
     // ntau, largest nt in steps of 256)
     std::vector<std::pair<std::vector<int>, int>> tune_cache;
     int tvsrc = NG_TVSRC_AUTO;       // evaluation of the left-mixing Matsubara source
+    int bulk_split = NG_BULK_AUTO;   // one thread or one warp per bulk item (ng_set_bulk_split)
     void* ws_tvq = nullptr;          // FFT correlation of the source, [m][a][b][kb]
     size_t ws_tvq_bytes = 0;
     void* ws_tw = nullptr;           // twiddle table of length tw_L
@@ -307,9 +309,17 @@ ng_status launch_timestep(ng_ctx* c, const Grid& g, int n, const HermV& G, const
     long e0 = prof_pair(c, 0);
     if (e0 >= 0) cudaEventRecord(c->ev_pool[e0], s);
     if ((sm = launch_minv<D>(c, g, n, S, eps, s))) return sm;
-    k_step_bulk<D><<<b_les + b_tv + b_ret, thr, 0, s>>>(g, n, G, S, eps, (const cplx*)c->ws_minv, b_les, b_tv, b_ret,
-                                                        tvq, c->d_status);
-    ng_status st = check_launch(c, "k_step_bulk");
+    // small batches: one warp per item when one thread per item would not give each SM a block
+    const int64_t items = it_les + it_tv + it_ret;
+    const bool warp = c->bulk_split == NG_BULK_WARP || (c->bulk_split == NG_BULK_AUTO && items < (int64_t)c->sms * thr);
+    if (warp) {
+        k_step_bulk_w<D><<<nblocks(items * 32, thr), thr, 0, s>>>(g, n, G, S, (const cplx*)c->ws_minv, it_les, it_tv,
+                                                                 it_ret, tvq, c->d_status);
+    } else {
+        k_step_bulk<D><<<b_les + b_tv + b_ret, thr, 0, s>>>(g, n, G, S, eps, (const cplx*)c->ws_minv, b_les, b_tv,
+                                                            b_ret, tvq, c->d_status);
+    }
+    ng_status st = check_launch(c, warp ? "k_step_bulk_w" : "k_step_bulk");
     if (st) return st;
     if (e0 >= 0) {
         cudaEventRecord(c->ev_pool[e0 + 1], s);
@@ -553,9 +563,13 @@ __global__ void k_v2_mat_fill(Grid g, HermV F, HermV Q, cplx* ws_g, cplx* ws_K) 
         }
 }
 
+// refine_steps > 0: refine the current G^M with the LU factors kept in *ws from the previous
+// solve (the operator of a self-consistency loop changes little between iterations), as the
+// Dyson Matsubara solve does; *refined_ok tells whether the residual reached ref_tol
 template <int D>
 ng_status launch_vie2_mat(ng_ctx* c, const Grid& g, const HermV& G, const HermV& F, const HermV& Q, cudaStream_t s,
-                          void** ws, size_t* ws_bytes) {
+                          void** ws, size_t* ws_bytes, int refine_steps = 0, double ref_tol = 0.0,
+                          bool* refined_ok = nullptr) {
     const int T = g.ntau, N = (T + 1) * D, ld = N + D;
     const size_t b_g = sizeof(cplx) * (size_t)g.nb * (T + 1) * D * D;
     const size_t b_A = sizeof(cplx) * (size_t)g.nb * N * ld;
@@ -564,11 +578,33 @@ ng_status launch_vie2_mat(ng_ctx* c, const Grid& g, const HermV& G, const HermV&
     if ((st = ensure(c, ws, ws_bytes, 3 * b_g + b_A + b_piv))) return st;
     cplx* ws_g = (cplx*)*ws;
     cplx* ws_K = ws_g + b_g / sizeof(cplx);
+    cplx* ws_r = ws_K + b_g / sizeof(cplx);
     cplx* ws_A = ws_K + 2 * (b_g / sizeof(cplx));
     int* ws_piv = (int*)(ws_A + b_A / sizeof(cplx));
     const int64_t items = (int64_t)(T + 1) * g.nb;
     k_v2_mat_fill<D><<<nblocks(items, 128), 128, 0, s>>>(g, F, Q, ws_g, ws_K);
     if ((st = check_launch(c, "k_v2_mat_fill"))) return st;
+    if (refine_steps > 0) {
+        *refined_ok = false;
+        double prev = 1e300;
+        for (int r = 0; r < refine_steps; ++r) {
+            k_mat_resid<D><<<nblocks(items, 128), 128, 0, s>>>(g, ws_g, ws_K, G, ws_r);
+            if ((st = check_launch(c, "k_mat_resid"))) return st;
+            CUDA_TRY(c, cudaMemsetAsync(c->d_scalar, 0, sizeof(double), s));
+            k_lu_resolve<<<g.nb, NG_LU_THREADS, 0, s>>>(g, N, D, ws_A, ws_piv, ws_r, G, c->d_scalar);
+            if ((st = check_launch(c, "k_lu_resolve"))) return st;
+            double dsum = 0.0;
+            CUDA_TRY(c, cudaMemcpyAsync(&dsum, c->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, s));
+            CUDA_TRY(c, cudaStreamSynchronize(s));
+            if (!(dsum == dsum)) return NG_OK;               // non-finite: a fresh solve follows
+            if (dsum == 0.0 || dsum > 0.5 * prev) {           // at the round-off floor, or stalled
+                *refined_ok = dsum < ref_tol;
+                return NG_OK;
+            }
+            prev = dsum;
+        }
+        return NG_OK;
+    }
     k_mat_assemble<D><<<nblocks((int64_t)(T + 1) * (T + 2) * g.nb, 256), 256, 0, s>>>(g, ws_g, ws_K, ws_A);
     if ((st = check_launch(c, "k_mat_assemble"))) return st;
     const size_t smem = sizeof(cplx) * (size_t)(ld + N) + NG_LU_THREADS * (sizeof(double) + sizeof(int));
@@ -579,12 +615,18 @@ ng_status launch_vie2_mat(ng_ctx* c, const Grid& g, const HermV& G, const HermV&
     return check_launch(c, "k_mat_store");
 }
 
+// one warp per vie2 bulk item: forced, or for batches with fewer items than 128 per SM
+bool vie2_warp(const ng_ctx* c, const Grid& g, int n) {
+    const int64_t items = (int64_t)g.nb * ((n - 1) + (g.ntau + 1) + n);
+    return c->bulk_split == NG_BULK_WARP || (c->bulk_split == NG_BULK_AUTO && items < (int64_t)c->sms * 128);
+}
+
 ng_status vie2_mat_d(ng_ctx* c, const Grid& g, const HermV& G, const HermV& F, const HermV& Q, cudaStream_t s,
-                     void** ws, size_t* ws_bytes) {
+                     void** ws, size_t* ws_bytes, int refine_steps = 0, double ref_tol = 0.0, bool* ok = nullptr) {
     switch (g.nf) {
-    case 1: return launch_vie2_mat<1>(c, g, G, F, Q, s, ws, ws_bytes);
-    case 2: return launch_vie2_mat<2>(c, g, G, F, Q, s, ws, ws_bytes);
-    case 4: return launch_vie2_mat<4>(c, g, G, F, Q, s, ws, ws_bytes);
+    case 1: return launch_vie2_mat<1>(c, g, G, F, Q, s, ws, ws_bytes, refine_steps, ref_tol, ok);
+    case 2: return launch_vie2_mat<2>(c, g, G, F, Q, s, ws, ws_bytes, refine_steps, ref_tol, ok);
+    case 4: return launch_vie2_mat<4>(c, g, G, F, Q, s, ws, ws_bytes, refine_steps, ref_tol, ok);
     default: return fail(c, NG_EUNSUPPORTED, "the vie2 solver supports nf = 1, 2, 4");
     }
 }
@@ -971,6 +1013,14 @@ ng_status ng_status_sync(ng_ctx* c, void* stream, int* flags) {
     return NG_OK;
 }
 
+ng_status ng_set_bulk_split(ng_ctx* c, int mode) {
+    if (!c) return NG_EINVAL;
+    if (mode != NG_BULK_AUTO && mode != NG_BULK_THREAD && mode != NG_BULK_WARP)
+        return fail(c, NG_EINVAL, "unknown bulk mode %d", mode);
+    c->bulk_split = mode;
+    return NG_OK;
+}
+
 ng_status ng_set_tv_source(ng_ctx* c, int mode) {
     if (!c) return NG_EINVAL;
     if (mode != NG_TVSRC_AUTO && mode != NG_TVSRC_DIRECT) return fail(c, NG_EINVAL, "unknown source mode %d", mode);
@@ -1128,7 +1178,8 @@ ng_status ng_vie2_timestep(ng_ctx* c, const ng_grid* grid, int tstp, ng_herm G, 
     if (schedule != NG_MIXED) return fail(c, NG_EINVAL, "unknown schedule %d", schedule);
     const cplx* tvq = nullptr;
     if ((st = prep_tvfft(c, g, tstp, Gv, Fv, (cudaStream_t)stream, &tvq))) return st;
-    if (vie2_step_launch(g, tstp, Gv, Fv, Fccv, Qv, tvq, c->d_status, (cudaStream_t)stream) != cudaSuccess) {
+    if (vie2_step_launch(g, tstp, Gv, Fv, Fccv, Qv, tvq, vie2_warp(c, g, tstp), c->d_status, (cudaStream_t)stream) !=
+        cudaSuccess) {
         cudaGetLastError();
         return fail(c, NG_ECUDA, "launch of the vie2 time-step kernels failed");
     }
@@ -1414,6 +1465,7 @@ static ng_status run_2b_impl(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm 
     // Sigma slices from..to from Gloc: from = to = -1 the Matsubara slice, 0..k the start-up
     // slices, n > k one time step.  GW: P, K and K^ddagger on those slices, then the chi
     // equation (vie2 Matsubara, start-up or time step), then dW and Sigma.
+    int gw_mats_calls = 0;   // Matsubara chi solves of this run (refinement after the first two)
     auto sigma_slices = [&](int from, int to) -> ng_status {
         ng_status r;
         if (!gw) {
@@ -1444,15 +1496,24 @@ static ng_status run_2b_impl(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm 
         }
         cudaError_t e = cudaSuccess;
         if (from < 0) {
-            r = vie2_mat_d(c, gw->gb, gw->X, gw->K, gw->P, s, &c->ws_gwmat, &c->ws_gwmat_bytes);
-            if (r) return r;
+            // after two fresh solves, refine chi^M with the kept LU factors; refactor if that stalls
+            bool refined = false;
+            const double nel = (double)(T + 1) * dd * gw->gb.nb;
+            if (gw_mats_calls >= 2 &&
+                (r = vie2_mat_d(c, gw->gb, gw->X, gw->K, gw->P, s, &c->ws_gwmat, &c->ws_gwmat_bytes, 30, 1e-13 * nel,
+                                &refined)))
+                return r;
+            if (!refined && (r = vie2_mat_d(c, gw->gb, gw->X, gw->K, gw->P, s, &c->ws_gwmat, &c->ws_gwmat_bytes)))
+                return r;
+            ++gw_mats_calls;
         } else if (from == 0) {
             e = vie2_start_launch(gw->gb, gw->X, gw->K, gw->Kcc, gw->P, (cplx*)c->ws_st, c->d_status, s);
         } else {
             for (int n = from; n <= to && e == cudaSuccess; ++n) {
                 const cplx* tvq = nullptr;
                 if ((r = prep_tvfft(c, gw->gb, n, gw->X, gw->K, s, &tvq, false))) return r;
-                e = vie2_step_launch(gw->gb, n, gw->X, gw->K, gw->Kcc, gw->P, tvq, c->d_status, s);
+                e = vie2_step_launch(gw->gb, n, gw->X, gw->K, gw->Kcc, gw->P, tvq, vie2_warp(c, gw->gb, n), c->d_status,
+                                     s);
             }
         }
         if (e != cudaSuccess) {

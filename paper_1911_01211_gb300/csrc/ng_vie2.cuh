@@ -20,6 +20,7 @@
 #pragma once
 
 #include "ng_step.cuh"
+#include "ng_stepsplit.cuh"
 
 // F~^R(n, l): stored for l <= n, continued by -[Fcc^R(l, n)]^dagger for l > n (Eq. Cretmod)
 template <int D>
@@ -170,6 +171,82 @@ __device__ __forceinline__ Mat<D> v2_les_solve(const NgWeights& W, const Grid& g
     const Mat<D> Mi = minv<D>(v2_one_plus<D>(g.h * gw(W, n, n), ld<D>(F.ret, tri(n) + n, kb)), &sing);
     if (sing) atomicOr(status, NGF_SINGULAR);
     return mmul<D>(rhs, mdag<D>(Mi));   // [M^dagger]^-1 = [M^-1]^dagger
+}
+
+// ---- the same items with one warp each (small batches): lane partials of every sum added
+// by the fixed butterfly of warp_msum, lane 0 finishes the item ------------------------------
+template <int D>
+__device__ __forceinline__ void v2_ret_item_w(const NgWeights& W, const Grid& g, const HermV& G, const HermV& F,
+                                              const HermV& Q, int n, int m, int kb, int lane, int* status) {
+    const int k = W.k, L = n - m;
+    Mat<D> acc = mzero<D>();
+    double wd;
+    if (L > k) {
+        for (int l = lane; l < L; l += 32)
+            mfma<D>(acc, mscal<D>(gw(W, L, l), ld<D>(F.ret, tri(n) + m + l, kb)), gret<D>(G, m + l, m, kb));
+        wd = gw(W, L, L);
+    } else {
+        for (int j = 1 + lane; j <= k; j += 32)
+            mfma<D>(acc, mscal<D>(W.greg[L][j], ld<D>(F.ret, tri(n) + n - j, kb)), gretx<D>(G, n - j, m, kb));
+        wd = W.greg[L][0];
+    }
+    acc = warp_msum<D>(acc);
+    if (lane != 0) return;
+    int sing = 0;
+    const Mat<D> Mi = minv<D>(v2_one_plus<D>(g.h * wd, ld<D>(F.ret, tri(n) + n, kb)), &sing);
+    const Mat<D> y = mmul<D>(Mi, msub<D>(ld<D>(Q.ret, tri(n) + m, kb), mscal<D>(g.h, acc)));
+    if (sing) atomicOr(status, NGF_SINGULAR);
+    if (!mfinite<D>(y)) atomicOr(status, NGF_NONFINITE);
+    st<D>(G.ret, tri(n) + m, kb, y);
+}
+
+template <int D>
+__device__ __forceinline__ void v2_tv_item_w(const NgWeights& W, const Grid& g, const HermV& G, const HermV& F,
+                                             const HermV& Q, int n, int m, int kb, const cplx* tvq, int lane,
+                                             int* status) {
+    Mat<D> acc = mzero<D>();
+    for (int j = lane; j < n; j += 32)
+        mfma<D>(acc, mscal<D>(gw(W, n, j), ld<D>(F.ret, tri(n) + j, kb)), gtv<D>(G, g, j, m, kb));
+    acc = warp_msum<D>(acc);
+    if (lane != 0) return;
+    Mat<D> rhs = msub<D>(gtv<D>(Q, g, n, m, kb), v2_ctv23<D>(W, g, G, F, n, m, kb, tvq));
+    rhs = msub<D>(rhs, mscal<D>(g.h, acc));
+    int sing = 0;
+    const Mat<D> y = mmul<D>(minv<D>(v2_one_plus<D>(g.h * gw(W, n, n), ld<D>(F.ret, tri(n) + n, kb)), &sing), rhs);
+    if (sing) atomicOr(status, NGF_SINGULAR);
+    if (!mfinite<D>(y)) atomicOr(status, NGF_NONFINITE);
+    st<D>(G.tv, (int64_t)n * (g.ntau + 1) + m, kb, y);
+}
+
+template <int D>
+__global__ void __launch_bounds__(128, 1)
+    k_v2_bulk_w(Grid g, int n, HermV G, HermV F, HermV Fcc, HermV Q, int64_t w_les, int64_t w_tv, int64_t w_ret,
+                const cplx* tvq, int* status) {
+    const NgWeights& W = c_W[g.k - 1];
+    int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    int task;
+    if (item < w_les) task = 0;
+    else if ((item -= w_les) < w_tv) task = 1;
+    else if ((item -= w_tv) < w_ret) task = 2;
+    else return;
+    const int kb = (int)(item % g.nb), col = (int)(item / g.nb);
+    if (task == 1) {
+        v2_tv_item_w<D>(W, g, G, F, Q, n, col, kb, tvq, lane, status);
+    } else if (task == 2) {
+        v2_ret_item_w<D>(W, g, G, F, Q, n, col, kb, lane, status);
+    } else {
+        const int m = col + 1;
+        Mat<D> c1 = mzero<D>(), c3 = mzero<D>(), hist = mzero<D>();
+        v2_les_parts_strided<D>(W, g, G, F, Fcc, n, m, kb, lane, 32, c1, c3, hist);
+        c1 = warp_msum<D>(c1);
+        c3 = warp_msum<D>(c3);
+        hist = warp_msum<D>(hist);
+        if (lane != 0) return;
+        const Mat<D> y = v2_les_solve<D>(W, g, F, Q, n, m, kb, c1, c3, hist, status);
+        if (!mfinite<D>(y)) atomicOr(status, NGF_NONFINITE);
+        st<D>(G.les, tri(n) + m, kb, y);
+    }
 }
 
 // Time step n: one launch over the retarded items (m = 0..n-1), the left-mixing items

@@ -122,17 +122,21 @@ def _oracle_problem_set(d, nb, N, T, beta, h, k, seed):
     return W, Gs, Ss, epss
 
 
-@pytest.mark.parametrize("schedule,tvsrc", [("mixed", "auto"), ("mixed", "direct"), ("serial", "auto")])
+@pytest.mark.parametrize("schedule,tvsrc,bulk", [("mixed", "auto", "thread"), ("mixed", "auto", "warp"),
+                                                 ("mixed", "direct", "thread"), ("mixed", "direct", "warp"),
+                                                 ("serial", "auto", "auto")])
 @pytest.mark.parametrize("d", [1, 2])
-def test_timestep_from_oracle_history(ng, d, schedule, tvsrc):
+def test_timestep_from_oracle_history(ng, d, schedule, tvsrc, bulk):
     """ng_dyson_timestep on the oracle's history reproduces the oracle's step in the same
     schedule for n in {k+1, 2k, 2k+1, 2k+2, N} (all branches of the mixed schedule), with
-    per-problem Sigma, with the left-mixing source by FFT (auto) and by the direct sums."""
+    per-problem Sigma, with the left-mixing source by FFT (auto) and by the direct sums, with
+    one thread or one warp per bulk item."""
     k, N, T, beta, h, nb = 5, 26, 18, 2.5, 0.06, 3
     W, Gs, Ss, epss = _oracle_problem_set(d, nb, N, T, beta, h, k, seed=11 + d)
     g = ng.Grid(nt=N, ntau=T, nf=d, nbatch=nb, korder=k, h=h, beta=beta)
     ctx = ng.Context(k)
     ctx.set_tv_source(ng.NG_TVSRC_DIRECT if tvsrc == "direct" else ng.NG_TVSRC_AUTO)
+    ctx.set_bulk_split({"auto": ng.NG_BULK_AUTO, "thread": ng.NG_BULK_THREAD, "warp": ng.NG_BULK_WARP}[bulk])
     G, S, eps = ng.Herm(g), ng.Herm(g), ng.Func(g)
     oracle_to_herm(Ss, S, g)
     funcs_to_device(epss, eps)
@@ -298,9 +302,11 @@ def test_slice_operations(ng):
         assert np.abs(got.tv[11] - ref.tv[11]).max() < 1e-12
 
 
-def _run_2b_both(ng, w, nmax=None):
+def _run_2b_both(ng, w, nmax=None, bulk=None):
     g = _grid(ng, w)
     ctx = ng.Context(w.korder)
+    if bulk is not None:
+        ctx.set_bulk_split(bulk)
     G = ng.Herm(g)
     L, S = ng.Herm(g, ldk=1), ng.Herm(g, ldk=1)
     e0 = ng.Func(g, values=torch.from_numpy(w.eps0))
@@ -363,10 +369,12 @@ def test_observables_against_oracle(ng):
     _status_ok(ctx, ng)
 
 
-def test_2b_hubbard_dimer_small(ng):
-    """hubbard_dimer workload on a small grid (nf = 2, quench U: 1 -> 2)."""
+@pytest.mark.parametrize("bulk", ["thread", "warp"])
+def test_2b_hubbard_dimer_small(ng, bulk):
+    """hubbard_dimer workload on a small grid (nf = 2, quench U: 1 -> 2), one thread or one warp
+    per bulk item."""
     w = wl.hubbard_dimer(nt=30, ntau=24, beta=5.0, h=0.05)
-    g, G, st, iters = _run_2b_both(ng, w)
+    g, G, st, iters = _run_2b_both(ng, w, bulk=ng.NG_BULK_THREAD if bulk == "thread" else ng.NG_BULK_WARP)
     assert_close(herm_to_oracle(G, g, 0), st.G[0])
 
 

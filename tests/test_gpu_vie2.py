@@ -84,9 +84,9 @@ def _random_herm(rng, N, T, d, scale):
     return X
 
 
-@pytest.mark.parametrize("tvsrc", ["fft", "direct"])
+@pytest.mark.parametrize("tvsrc,bulk", [("fft", "thread"), ("fft", "warp"), ("direct", "thread")])
 @pytest.mark.parametrize("d", [1, 2, 4])
-def test_vie2_steps_from_random_data(ng, d, tvsrc):
+def test_vie2_steps_from_random_data(ng, d, tvsrc, bulk):
     """Matsubara, start-up and the steps n = k+1, 2k+1, 2k+2, N from a random history, with F,
     Fcc and Q drawn independently (single steps are linear in their inputs); the left-mixing
     source from the FFT pre-pass with its corrections, or from the direct sums."""
@@ -104,6 +104,7 @@ def test_vie2_steps_from_random_data(ng, d, tvsrc):
     oracle_to_herm(Q, dQ, g)
     ctx = ng.Context(k)
     ctx.set_tv_source(ng.NG_TVSRC_AUTO if tvsrc == "fft" else ng.NG_TVSRC_DIRECT)
+    ctx.set_bulk_split(ng.NG_BULK_THREAD if bulk == "thread" else ng.NG_BULK_WARP)
     # Matsubara and start-up
     G = ng.Herm(g)
     ctx.vie2_mat(g, G, dF, dQ)
