@@ -60,6 +60,8 @@ struct ng_ctx {
     size_t ws_prev_bytes = 0;
     void* ws_gw = nullptr;           // GW driver: bosonic P, K, K^ddagger on the whole contour
     size_t ws_gw_bytes = 0;
+    void* ws_bnd = nullptr;          // small-batch boundary: chunk partials of the (A)-row sums
+    size_t ws_bnd_bytes = 0;
     void* ws_gwk = nullptr;          // k-space GW: compact real-space slice buffers
     size_t ws_gwk_bytes = 0;
     void* ws_gwmat = nullptr;        // GW driver: Matsubara workspace of the chi solve (ws_mat
@@ -327,6 +329,22 @@ ng_status launch_timestep(ng_ctx* c, const Grid& g, int n, const HermV& G, const
     }
     long e1 = prof_pair(c, 1);
     if (e1 >= 0) cudaEventRecord(c->ev_pool[e1], s);
+    // small batches: the boundary's (A)-row sums spread over (row, problem, chunk) blocks
+    const int nq = (n <= 2 * k) ? n : k + 1;
+    if (c->bulk_split == NG_BULK_WARP || (c->bulk_split == NG_BULK_AUTO && (int64_t)nq * g.nb < 2 * (int64_t)c->sms)) {
+        const int64_t terms = std::max(n, g.ntau) + 1;
+        const int64_t want = (4 * (int64_t)c->sms + (int64_t)nq * g.nb - 1) / ((int64_t)nq * g.nb);
+        const int nchunk = (int)std::max<int64_t>(1, std::min<int64_t>({want, (terms + NG_BND_THREADS - 1) / NG_BND_THREADS, 64}));
+        const size_t need = sizeof(cplx) * (size_t)nq * g.nb * nchunk * 2 * D * D;
+        if ((st = ensure(c, &c->ws_bnd, &c->ws_bnd_bytes, need))) return st;
+        k_bnd_pre<D><<<nblocks(g.nb, 64), 64, 0, s>>>(g, n, G, S, eps, c->d_status);
+        if ((st = check_launch(c, "k_bnd_pre"))) return st;
+        k_bnd_src<D><<<dim3(nq, g.nb, nchunk), NG_BND_THREADS, 0, s>>>(g, n, G, S, nchunk, (cplx*)c->ws_bnd);
+        if ((st = check_launch(c, "k_bnd_src"))) return st;
+        k_bnd_fin<D><<<nblocks(g.nb, 64), 64, 0, s>>>(g, n, G, S, eps, nchunk, (const cplx*)c->ws_bnd, c->d_status);
+        if (e1 >= 0) cudaEventRecord(c->ev_pool[e1 + 1], s);
+        return check_launch(c, "k_bnd_fin");
+    }
     k_step_boundary<D><<<g.nb, NG_BND_THREADS, 0, s>>>(g, n, G, S, eps, c->d_status);
     if (e1 >= 0) cudaEventRecord(c->ev_pool[e1 + 1], s);
     return check_launch(c, "k_step_boundary");
@@ -985,6 +1003,7 @@ void ng_destroy(ng_ctx* c) {
     cudaFree(c->ws_gw);
     cudaFree(c->ws_gwmat);
     cudaFree(c->ws_gwk);
+    cudaFree(c->ws_bnd);
     cudaFree(c->shG.buf);
     cudaFree(c->shS.buf);
     cudaFree(c->dfG.buf);

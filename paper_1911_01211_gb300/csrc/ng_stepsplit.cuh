@@ -120,3 +120,102 @@ __global__ void __launch_bounds__(128, 1) k_step_bulk_w(Grid g, int n, HermV G, 
     else if (task == 1) tv_item_w<D>(W, g, G, S, minv_ws, n, col, kb, tvq, lane, status);
     else ret_item_w<D>(W, g, G, S, minv_ws, n, col, kb, lane, status);
 }
+
+// ---- the boundary of a time step for small batches, in three launches -----------------------
+// k_step_boundary runs one block per problem, so for a single problem its (A)-row sources, sums
+// over n and ntau terms, run on one SM.  Here: (1) per problem, the retarded (A) row start-up
+// and G^<(0,n) (k_bnd_pre); (2) the (A)-row sources and partial histories spread over blocks
+// (row, problem, chunk), each block summing its chunk's terms (k_bnd_src); (3) per problem, the
+// chunk partials added in chunk order and the serial (A) steps of the lesser column
+// (k_bnd_fin), as in k_step_boundary.
+
+template <int D>
+__global__ void k_bnd_pre(Grid g, int n, HermV G, HermV S, FuncV eps, int* status) {
+    const int kb = blockIdx.x * blockDim.x + threadIdx.x;
+    if (kb >= g.nb) return;
+    const NgWeights& W = c_W[g.k - 1];
+    cplx Ash[(NG_KMAX * D) * (NG_KMAX * D)];
+    cplx Bsh[(NG_KMAX * D) * D];
+    ret_row_startup<D>(W, g, n, G, S, eps, kb, Ash, Bsh, status);
+    // G^<(0,n) = -[G^tv(n,0)]^dagger  (Eq. dyson_ini_les)
+    st<D>(G.les, tri(n) + 0, kb, mscal<D>(-1.0, mdag<D>(gtv<D>(G, g, n, 0, kb))));
+}
+
+// block (r, kb, c): row m = m0 + r, terms j = c B + t, c B + t + nchunk B, ...; partials at
+// part[((r nb + kb) nchunk + c) 2 D^2 ...]: the source, then the partial history over l < m0
+template <int D>
+__global__ void __launch_bounds__(NG_BND_THREADS) k_bnd_src(Grid g, int n, HermV G, HermV S, int nchunk, cplx* part) {
+    const NgWeights& W = c_W[g.k - 1];
+    const int k = W.k;
+    const bool full = (n <= 2 * k);
+    const int m0 = full ? 1 : n - k;
+    const int r = blockIdx.x, kb = blockIdx.y, c = blockIdx.z, t = threadIdx.x;
+    const int m = m0 + r;
+    __shared__ cplx red[NG_BND_THREADS * D * D];
+    const int j0 = c * blockDim.x + t, js = nchunk * blockDim.x;
+    const Mat<D> q = block_sum<D>(q_lesA_part<D>(W, g, G, S, m, n, kb, j0, js), red);
+    Mat<D> hp = mzero<D>();
+    if (!full && m > k)
+        for (int l = j0; l < m0; l += js)
+            mfma<D>(hp, mscal<D>(gw(W, m, l), gret<D>(S, m, l, kb)), ld<D>(G.les, tri(n) + l, kb));
+    const Mat<D> hsum = block_sum<D>(hp, red);
+    if (t != 0) return;
+    cplx* o = part + (((int64_t)r * g.nb + kb) * nchunk + c) * 2 * D * D;
+    for (int a = 0; a < D; ++a)
+        for (int b = 0; b < D; ++b) {
+            o[a * D + b] = q.v[a][b];
+            o[D * D + a * D + b] = hsum.v[a][b];
+        }
+}
+
+template <int D>
+__global__ void k_bnd_fin(Grid g, int n, HermV G, HermV S, FuncV eps, int nchunk, const cplx* part, int* status) {
+    const int kb = blockIdx.x * blockDim.x + threadIdx.x;
+    if (kb >= g.nb) return;
+    const NgWeights& W = c_W[g.k - 1];
+    const int k = W.k;
+    const bool full = (n <= 2 * k);
+    const int m0 = full ? 1 : n - k;
+    const int nq = n - m0 + 1;
+    cplx qsrc[NG_MAXQ + 1][D][D], hsrc[NG_MAXQ + 1][D][D];
+    for (int r = 0; r < nq; ++r) {
+        Mat<D> q = mzero<D>(), h = mzero<D>();
+        for (int c = 0; c < nchunk; ++c) {   // chunk order: deterministic
+            const cplx* o = part + (((int64_t)r * g.nb + kb) * nchunk + c) * 2 * D * D;
+            for (int a = 0; a < D; ++a)
+                for (int b = 0; b < D; ++b) {
+                    q.v[a][b] = cadd(q.v[a][b], o[a * D + b]);
+                    h.v[a][b] = cadd(h.v[a][b], o[D * D + a * D + b]);
+                }
+        }
+        for (int a = 0; a < D; ++a)
+            for (int b = 0; b < D; ++b) qsrc[r][a][b] = q.v[a][b], hsrc[r][a][b] = h.v[a][b];
+    }
+    int sing = 0;
+    int mstep = m0;
+    if (full) {
+        cplx Ash[(NG_KMAX * D) * (NG_KMAX * D)];
+        cplx Bsh[(NG_KMAX * D) * D];
+        les_col_startup<D>(W, g, n, G, S, eps, kb, qsrc, Ash, Bsh, status);
+        mstep = k + 1;
+    }
+    // serial VIDE steps (Eq. MBCVSAMx_t) in the first argument, m = mstep..n
+    for (int m = mstep; m <= n; ++m) {
+        const int r = m - m0;
+        Mat<D> acc, h0;
+        for (int a = 0; a < D; ++a)
+            for (int b = 0; b < D; ++b) acc.v[a][b] = qsrc[r][a][b], h0.v[a][b] = hsrc[r][a][b];
+        const int lfrom = full ? 0 : m0;
+        for (int l = lfrom; l < m; ++l)
+            mfma<D>(h0, mscal<D>(gw(W, m, l), gret<D>(S, m, l, kb)), ld<D>(G.les, tri(n) + l, kb));
+        Mat<D> bdf = mzero<D>();
+        for (int l = 1; l <= k; ++l) bdf = madd<D>(bdf, mscal<D>(W.a[l], ld<D>(G.les, tri(n) + m - l, kb)));
+        acc = msub<D>(acc, mscal<D>(1.0 / g.h, bdf));
+        acc = msub<D>(acc, mscal<D>(g.h, mmuli<D>(h0)));
+        Mat<D> Mm = step_matrix<D>(W, g, S, eps, m, kb);
+        Mat<D> y = mmul<D>(minv<D>(Mm, &sing), acc);
+        if (!mfinite<D>(y)) atomicOr(status, NGF_NONFINITE);
+        st<D>(G.les, tri(n) + m, kb, y);
+    }
+    if (sing) atomicOr(status, NGF_SINGULAR);
+}
