@@ -497,6 +497,28 @@ ng_status launch_timestep32(ng_ctx* c, const Grid& g, int n, const HermV& G, con
 // the same grid): iterative refinement of the current G^M against the current operator with
 // the kept factors, at most refine_steps steps; *refined_ok reports convergence of the
 // refinement (update sum below ref_tol); otherwise the caller falls back to a fresh LU.
+// LU solve of nb augmented systems [A | B] (N x (N + nrhs)) in ws_A: one block per problem for
+// batches that fill the SMs (or when several solves run concurrently on streams, spread =
+// false), else column by column with the rank-1 updates over the whole GPU (the same factors
+// bitwise)
+ng_status lu_solve(ng_ctx* c, int N, int nrhs, int nb, cplx* ws_A, int* ws_piv, cudaStream_t s, bool spread = true) {
+    ng_status st;
+    if (!spread || 4 * (int64_t)nb >= c->sms) {
+        const size_t smem = sizeof(cplx) * (size_t)(2 * N + nrhs) + NG_LU_THREADS * (sizeof(double) + sizeof(int));
+        CUDA_TRY(c, cudaFuncSetAttribute(k_lu_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_lu_solve<<<nb, NG_LU_THREADS, smem, s>>>(N, nrhs, ws_A, ws_piv, c->d_status);
+        return check_launch(c, "k_lu_solve");
+    }
+    for (int col = 0; col < N; ++col) {
+        k_lu_col<<<nb, NG_LU_THREADS, 0, s>>>(N, nrhs, ws_A, ws_piv, col, c->d_status);
+        const int64_t items = (int64_t)(N - col - 1) * (N + nrhs - col - 1);
+        if (items > 0) k_lu_rank1<<<dim3(nblocks(items, 256), nb), 256, 0, s>>>(N, nrhs, ws_A, col);
+        if (col % 256 == 0 && (st = check_launch(c, "k_lu_col/k_lu_rank1"))) return st;
+    }
+    k_lu_backsub<<<nb, NG_LU_THREADS, 0, s>>>(N, nrhs, ws_A);
+    return check_launch(c, "k_lu_backsub");
+}
+
 template <int D>
 ng_status launch_mat(ng_ctx* c, const Grid& g, const HermV& G, const HermV& S, const FuncV& eps, cudaStream_t s,
                      int refine_steps = 0, double ref_tol = 0.0, bool* refined_ok = nullptr, void* ws_ext = nullptr) {
@@ -540,10 +562,7 @@ ng_status launch_mat(ng_ctx* c, const Grid& g, const HermV& G, const HermV& S, c
     const int64_t ab = (int64_t)(T + 1) * (T + 2) * g.nb;
     k_mat_assemble<D><<<nblocks(ab, 256), 256, 0, s>>>(g, ws_g, ws_K, ws_A);
     if ((st = check_launch(c, "k_mat_assemble"))) return st;
-    const size_t smem = sizeof(cplx) * (size_t)(ld + N) + NG_LU_THREADS * (sizeof(double) + sizeof(int));
-    CUDA_TRY(c, cudaFuncSetAttribute(k_lu_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_lu_solve<<<g.nb, NG_LU_THREADS, smem, s>>>(N, D, ws_A, ws_piv, c->d_status);
-    if ((st = check_launch(c, "k_lu_solve"))) return st;
+    if ((st = lu_solve(c, N, D, g.nb, ws_A, ws_piv, s, ws_ext == nullptr))) return st;
     k_mat_store<D><<<nblocks(items, 128), 128, 0, s>>>(g, ws_A, G, c->d_status);
     return check_launch(c, "k_mat_store");
 }
@@ -625,10 +644,7 @@ ng_status launch_vie2_mat(ng_ctx* c, const Grid& g, const HermV& G, const HermV&
     }
     k_mat_assemble<D><<<nblocks((int64_t)(T + 1) * (T + 2) * g.nb, 256), 256, 0, s>>>(g, ws_g, ws_K, ws_A);
     if ((st = check_launch(c, "k_mat_assemble"))) return st;
-    const size_t smem = sizeof(cplx) * (size_t)(ld + N) + NG_LU_THREADS * (sizeof(double) + sizeof(int));
-    CUDA_TRY(c, cudaFuncSetAttribute(k_lu_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_lu_solve<<<g.nb, NG_LU_THREADS, smem, s>>>(N, D, ws_A, ws_piv, c->d_status);
-    if ((st = check_launch(c, "k_lu_solve"))) return st;
+    if ((st = lu_solve(c, N, D, g.nb, ws_A, ws_piv, s))) return st;
     k_mat_store<D><<<nblocks(items, 128), 128, 0, s>>>(g, ws_A, G, c->d_status);
     return check_launch(c, "k_mat_store");
 }

@@ -331,6 +331,72 @@ __global__ void __launch_bounds__(NG_LU_THREADS) k_lu_solve(int N, int nrhs, cpl
     }
 }
 
+// The same factorisation for a few problems, spread over the GPU (blockIdx.y or blockIdx.x =
+// problem): per column c, the pivot search, row interchange and multipliers in one block per
+// problem (k_lu_col), then the rank-1 update of the trailing rows and columns over many blocks
+// (k_lu_rank1), then the back substitution (k_lu_backsub).  Every element receives the same
+// operations in the same order as in k_lu_solve, so factors and solution agree bitwise.
+__global__ void __launch_bounds__(NG_LU_THREADS) k_lu_col(int N, int nrhs, cplx* ws_A, int* piv, int c, int* status) {
+    const int ld = N + nrhs;
+    cplx* A = ws_A + (int64_t)blockIdx.x * N * ld;
+    __shared__ double rv[NG_LU_THREADS];
+    __shared__ int ri[NG_LU_THREADS];
+    const int t = threadIdx.x, nt = blockDim.x;
+    double best = -1.0;
+    int bi = c;
+    for (int r = c + t; r < N; r += nt) {
+        double v = cabs2(A[(int64_t)r * ld + c]);
+        if (v > best) { best = v; bi = r; }
+    }
+    rv[t] = best;
+    ri[t] = bi;
+    __syncthreads();
+    for (int s = nt / 2; s > 0; s >>= 1) {
+        if (t < s && (rv[t + s] > rv[t] || (rv[t + s] == rv[t] && ri[t + s] < ri[t]))) {
+            rv[t] = rv[t + s];
+            ri[t] = ri[t + s];
+        }
+        __syncthreads();
+    }
+    const int p = ri[0];
+    if (rv[0] <= 0.0 && t == 0) atomicOr(status, NGF_SINGULAR);
+    if (t == 0) piv[(int64_t)blockIdx.x * N + c] = p;
+    if (p != c)
+        for (int j = t; j < ld; j += nt) {
+            const cplx x = A[(int64_t)p * ld + j];
+            A[(int64_t)p * ld + j] = A[(int64_t)c * ld + j];
+            A[(int64_t)c * ld + j] = x;
+        }
+    __syncthreads();
+    const cplx inv = cdiv(cr(1.0), A[(int64_t)c * ld + c]);
+    for (int r = c + 1 + t; r < N; r += nt) A[(int64_t)r * ld + c] = cmul(A[(int64_t)r * ld + c], inv);
+}
+
+__global__ void k_lu_rank1(int N, int nrhs, cplx* ws_A, int c) {
+    const int ld = N + nrhs, w = ld - c - 1;
+    cplx* A = ws_A + (int64_t)blockIdx.y * N * ld;
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (int64_t)(N - c - 1) * w) return;
+    const int r = c + 1 + (int)(q / w), j = c + 1 + (int)(q % w);
+    A[(int64_t)r * ld + j] = csub(A[(int64_t)r * ld + j], cmul(A[(int64_t)r * ld + c], A[(int64_t)c * ld + j]));
+}
+
+__global__ void __launch_bounds__(NG_LU_THREADS) k_lu_backsub(int N, int nrhs, cplx* ws_A) {
+    const int ld = N + nrhs;
+    cplx* A = ws_A + (int64_t)blockIdx.x * N * ld;
+    const int t = threadIdx.x, nt = blockDim.x;
+    for (int c = N - 1; c >= 0; --c) {
+        const cplx inv = cdiv(cr(1.0), A[(int64_t)c * ld + c]);
+        if (t < nrhs) A[(int64_t)c * ld + N + t] = cmul(A[(int64_t)c * ld + N + t], inv);
+        __syncthreads();
+        for (int64_t q = t; q < (int64_t)c * nrhs; q += nt) {
+            const int r = (int)(q / nrhs), j = (int)(q % nrhs);
+            A[(int64_t)r * ld + N + j] = csub(A[(int64_t)r * ld + N + j], cmul(A[(int64_t)r * ld + c], A[(int64_t)c * ld + N + j]));
+        }
+        __syncthreads();
+    }
+}
+
 // ----------------------------------------------------------------------------------------
 // Iterative refinement of the Matsubara solve with stored LU factors (from an earlier
 // operator): residual r = g + [K * G]^M - G of the current operator (matrix-free, Eqs. cm1/cm2),
