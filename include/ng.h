@@ -118,7 +118,8 @@ typedef enum { NG_TVSRC_AUTO = 0, NG_TVSRC_DIRECT = 1 } ng_tv_source;
  * fixed butterfly order, and the boundary's (A)-row sums spread over (row, problem, chunk)
  * blocks added in chunk order (small batches: a dimer, a real-space cluster); NG_BULK_AUTO
  * (default), each warp/spread form when the batch has fewer than 128 bulk items per SM, resp.
- * fewer than 2 boundary rows per SM.  The forms differ by the order of additions only. */
+ * fewer than 2 boundary rows per SM.  The forms differ by the order of additions only.
+ * nf = 4, 8 always run the element-wise form. */
 typedef enum { NG_BULK_AUTO = 0, NG_BULK_THREAD = 1, NG_BULK_WARP = 2 } ng_bulk_split;
 
 /* Schedule of a time step (Sec. "Time stepping"): NG_MIXED is the paper's parallel variant

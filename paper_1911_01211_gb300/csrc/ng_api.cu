@@ -297,6 +297,25 @@ ng_status prep_tvfft(ng_ctx* c, const Grid& g, int n, const HermV& G, const Herm
     return NG_OK;
 }
 
+// the boundary of step n in three launches, its (A)-row sums over (row, problem, chunk) blocks
+template <int D>
+ng_status boundary_spread(ng_ctx* c, const Grid& g, int n, const HermV& G, const HermV& S, const FuncV& eps,
+                          cudaStream_t s) {
+    ng_status st;
+    const int k = g.k, nq = (n <= 2 * k) ? n : k + 1;
+    const int64_t terms = std::max(n, g.ntau) + 1;
+    const int64_t want = (4 * (int64_t)c->sms + (int64_t)nq * g.nb - 1) / ((int64_t)nq * g.nb);
+    const int nchunk = (int)std::max<int64_t>(1, std::min<int64_t>({want, (terms + NG_BND_THREADS - 1) / NG_BND_THREADS, 64}));
+    const size_t need = sizeof(cplx) * (size_t)nq * g.nb * nchunk * 2 * D * D;
+    if ((st = ensure(c, &c->ws_bnd, &c->ws_bnd_bytes, need))) return st;
+    k_bnd_pre<D><<<nblocks(g.nb, 64), 64, 0, s>>>(g, n, G, S, eps, c->d_status);
+    if ((st = check_launch(c, "k_bnd_pre"))) return st;
+    k_bnd_src<D><<<dim3(nq, g.nb, nchunk), NG_BND_THREADS, 0, s>>>(g, n, G, S, nchunk, (cplx*)c->ws_bnd);
+    if ((st = check_launch(c, "k_bnd_src"))) return st;
+    k_bnd_fin<D><<<nblocks(g.nb, 64), 64, 0, s>>>(g, n, G, S, eps, nchunk, (const cplx*)c->ws_bnd, c->d_status);
+    return check_launch(c, "k_bnd_fin");
+}
+
 template <int D>
 ng_status launch_timestep(ng_ctx* c, const Grid& g, int n, const HermV& G, const HermV& S, const FuncV& eps,
                           cudaStream_t s) {
@@ -332,18 +351,9 @@ ng_status launch_timestep(ng_ctx* c, const Grid& g, int n, const HermV& G, const
     // small batches: the boundary's (A)-row sums spread over (row, problem, chunk) blocks
     const int nq = (n <= 2 * k) ? n : k + 1;
     if (c->bulk_split == NG_BULK_WARP || (c->bulk_split == NG_BULK_AUTO && (int64_t)nq * g.nb < 2 * (int64_t)c->sms)) {
-        const int64_t terms = std::max(n, g.ntau) + 1;
-        const int64_t want = (4 * (int64_t)c->sms + (int64_t)nq * g.nb - 1) / ((int64_t)nq * g.nb);
-        const int nchunk = (int)std::max<int64_t>(1, std::min<int64_t>({want, (terms + NG_BND_THREADS - 1) / NG_BND_THREADS, 64}));
-        const size_t need = sizeof(cplx) * (size_t)nq * g.nb * nchunk * 2 * D * D;
-        if ((st = ensure(c, &c->ws_bnd, &c->ws_bnd_bytes, need))) return st;
-        k_bnd_pre<D><<<nblocks(g.nb, 64), 64, 0, s>>>(g, n, G, S, eps, c->d_status);
-        if ((st = check_launch(c, "k_bnd_pre"))) return st;
-        k_bnd_src<D><<<dim3(nq, g.nb, nchunk), NG_BND_THREADS, 0, s>>>(g, n, G, S, nchunk, (cplx*)c->ws_bnd);
-        if ((st = check_launch(c, "k_bnd_src"))) return st;
-        k_bnd_fin<D><<<nblocks(g.nb, 64), 64, 0, s>>>(g, n, G, S, eps, nchunk, (const cplx*)c->ws_bnd, c->d_status);
+        st = boundary_spread<D>(c, g, n, G, S, eps, s);
         if (e1 >= 0) cudaEventRecord(c->ev_pool[e1 + 1], s);
-        return check_launch(c, "k_bnd_fin");
+        return st;
     }
     k_step_boundary<D><<<g.nb, NG_BND_THREADS, 0, s>>>(g, n, G, S, eps, c->d_status);
     if (e1 >= 0) cudaEventRecord(c->ev_pool[e1 + 1], s);
@@ -917,6 +927,8 @@ ng_status do_timestep(ng_ctx* c, const Grid& g, int n, const HermV& G, const Her
                       int precision = NG_FP64) {
     if (g.nf > 2) {
         if (precision != NG_FP64) return fail(c, NG_EUNSUPPORTED, "NG_F32C and NG_DF64 need nf <= 2");
+        // nf = 4, 8: the element-wise batch form (a warp holding 4 x 4 blocks per lane spills and
+        // ran the 4-site chain's step at half this form's speed)
         return utimestep_uniform(c, g, n, G, S, eps, s);
     }
     if (precision == NG_DF64)

@@ -122,15 +122,16 @@ def _oracle_problem_set(d, nb, N, T, beta, h, k, seed):
     return W, Gs, Ss, epss
 
 
-@pytest.mark.parametrize("schedule,tvsrc,bulk", [("mixed", "auto", "thread"), ("mixed", "auto", "warp"),
-                                                 ("mixed", "direct", "thread"), ("mixed", "direct", "warp"),
-                                                 ("serial", "auto", "auto")])
-@pytest.mark.parametrize("d", [1, 2])
+_STEP_CASES = [(d, "mixed", "auto", "thread") for d in (1, 2, 4)] + [(d, "mixed", "auto", "warp") for d in (1, 2)] + \
+    [(d, "mixed", "direct", b) for d in (1, 2) for b in ("thread", "warp")] + [(d, "serial", "auto", "auto") for d in (1, 2)]
+
+
+@pytest.mark.parametrize("d,schedule,tvsrc,bulk", _STEP_CASES)
 def test_timestep_from_oracle_history(ng, d, schedule, tvsrc, bulk):
     """ng_dyson_timestep on the oracle's history reproduces the oracle's step in the same
     schedule for n in {k+1, 2k, 2k+1, 2k+2, N} (all branches of the mixed schedule), with
     per-problem Sigma, with the left-mixing source by FFT (auto) and by the direct sums, with
-    one thread or one warp per bulk item."""
+    one thread or one warp per bulk item (nf = 4: the element-wise form)."""
     k, N, T, beta, h, nb = 5, 26, 18, 2.5, 0.06, 3
     W, Gs, Ss, epss = _oracle_problem_set(d, nb, N, T, beta, h, k, seed=11 + d)
     g = ng.Grid(nt=N, ntau=T, nf=d, nbatch=nb, korder=k, h=h, beta=beta)
