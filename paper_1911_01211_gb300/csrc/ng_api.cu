@@ -324,18 +324,19 @@ ng_status launch_timestep(ng_ctx* c, const Grid& g, int n, const HermV& G, const
     const int64_t it_tv = (int64_t)g.nb * (g.ntau + 1);
     const int64_t it_ret = (int64_t)g.nb * (n - k);
     const int b_les = (int)nblocks(it_les, thr), b_tv = (int)nblocks(it_tv, thr), b_ret = (int)nblocks(it_ret, thr);
+    // small batches: one warp per item when one thread per item would not give each SM a block;
+    // the warp form splits the left-mixing source over its lanes instead of the FFT pre-pass
+    const int64_t items = it_les + it_tv + it_ret;
+    const bool warp = c->bulk_split == NG_BULK_WARP || (c->bulk_split == NG_BULK_AUTO && items < (int64_t)c->sms * thr);
     const cplx* tvq = nullptr;
-    ng_status sm = prep_tvfft(c, g, n, G, S, s, &tvq);
+    ng_status sm = warp ? NG_OK : prep_tvfft(c, g, n, G, S, s, &tvq);
     if (sm) return sm;
     long e0 = prof_pair(c, 0);
     if (e0 >= 0) cudaEventRecord(c->ev_pool[e0], s);
     if ((sm = launch_minv<D>(c, g, n, S, eps, s))) return sm;
-    // small batches: one warp per item when one thread per item would not give each SM a block
-    const int64_t items = it_les + it_tv + it_ret;
-    const bool warp = c->bulk_split == NG_BULK_WARP || (c->bulk_split == NG_BULK_AUTO && items < (int64_t)c->sms * thr);
     if (warp) {
         k_step_bulk_w<D><<<nblocks(items * 32, thr), thr, 0, s>>>(g, n, G, S, (const cplx*)c->ws_minv, it_les, it_tv,
-                                                                 it_ret, tvq, c->d_status);
+                                                                 it_ret, c->d_status);
     } else {
         k_step_bulk<D><<<b_les + b_tv + b_ret, thr, 0, s>>>(g, n, G, S, eps, (const cplx*)c->ws_minv, b_les, b_tv,
                                                             b_ret, tvq, c->d_status);
@@ -1224,8 +1225,9 @@ ng_status ng_vie2_timestep(ng_ctx* c, const ng_grid* grid, int tstp, ng_herm G, 
     if (schedule == NG_SERIAL) return fail(c, NG_EUNSUPPORTED, "the vie2 time step runs the mixed schedule only");
     if (schedule != NG_MIXED) return fail(c, NG_EINVAL, "unknown schedule %d", schedule);
     const cplx* tvq = nullptr;
-    if ((st = prep_tvfft(c, g, tstp, Gv, Fv, (cudaStream_t)stream, &tvq))) return st;
-    if (vie2_step_launch(g, tstp, Gv, Fv, Fccv, Qv, tvq, vie2_warp(c, g, tstp), c->d_status, (cudaStream_t)stream) !=
+    const bool w = vie2_warp(c, g, tstp);
+    if (!w && (st = prep_tvfft(c, g, tstp, Gv, Fv, (cudaStream_t)stream, &tvq))) return st;
+    if (vie2_step_launch(g, tstp, Gv, Fv, Fccv, Qv, tvq, w, c->d_status, (cudaStream_t)stream) !=
         cudaSuccess) {
         cudaGetLastError();
         return fail(c, NG_ECUDA, "launch of the vie2 time-step kernels failed");
@@ -1558,9 +1560,9 @@ static ng_status run_2b_impl(ng_ctx* c, const ng_grid* grid, ng_herm G, ng_herm 
         } else {
             for (int n = from; n <= to && e == cudaSuccess; ++n) {
                 const cplx* tvq = nullptr;
-                if ((r = prep_tvfft(c, gw->gb, n, gw->X, gw->K, s, &tvq, false))) return r;
-                e = vie2_step_launch(gw->gb, n, gw->X, gw->K, gw->Kcc, gw->P, tvq, vie2_warp(c, gw->gb, n), c->d_status,
-                                     s);
+                const bool w = vie2_warp(c, gw->gb, n);
+                if (!w && (r = prep_tvfft(c, gw->gb, n, gw->X, gw->K, s, &tvq, false))) return r;
+                e = vie2_step_launch(gw->gb, n, gw->X, gw->K, gw->Kcc, gw->P, tvq, w, c->d_status, s);
             }
         }
         if (e != cudaSuccess) {

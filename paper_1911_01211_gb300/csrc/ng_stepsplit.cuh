@@ -44,18 +44,53 @@ __device__ __forceinline__ void ret_item_w(const NgWeights& W, const Grid& g, co
     st<D>(G.ret, tri(n) + m, kb, y);
 }
 
+// The left-mixing source -i (C^tv_2 + C^tv_3)[S, 1, G^M](n, tau_m) (Eqs. ctv2, ctv3) as q_tv
+// computes it, over the terms l = l0, l0 + ls, ... of its two Gregory sums; the boundary (R)
+// formulas of m <= k and m >= ntau - k ((k+1)^2 terms each) go to the part with l0 = 0.  The
+// source is linear in the terms, so the parts add up to q_tv.
+template <int D>
+__device__ Mat<D> q_tv_part(const NgWeights& W, const Grid& g, const HermV& G, const HermV& S, int n, int m, int kb,
+                            int l0, int ls) {
+    const int k = W.k, T = g.ntau;
+    const double xi = (double)g.sig;
+    Mat<D> c2 = mzero<D>(), c3 = mzero<D>();
+    if (m <= k) {
+        if (l0 == 0)
+            for (int j = 0; j <= k; ++j) {
+                Mat<D> gm = mscal<D>(xi, gmat<D>(G, T - j, kb));
+                for (int l = 0; l <= k; ++l) mfma<D>(c2, mscal<D>(W.R[m][j][l], gtv<D>(S, g, n, l, kb)), gm);
+            }
+    } else {
+        for (int l = l0; l <= m; l += ls)
+            mfma<D>(c2, mscal<D>(gw(W, m, l), gtv<D>(S, g, n, m - l, kb)), gmat<D>(G, T - l, kb));
+        c2 = mscal<D>(xi, c2);
+    }
+    if (m >= T - k) {
+        if (l0 == 0)
+            for (int j = 0; j <= k; ++j) {
+                Mat<D> gm = gmat<D>(G, j, kb);
+                for (int l = 0; l <= k; ++l) mfma<D>(c3, mscal<D>(W.R[T - m][j][l], gtv<D>(S, g, n, T - l, kb)), gm);
+            }
+    } else {
+        for (int l = l0; l <= T - m; l += ls)
+            mfma<D>(c3, mscal<D>(gw(W, T - m, l), gtv<D>(S, g, n, m + l, kb)), gmat<D>(G, l, kb));
+    }
+    return mscal<D>(g.htau, mmuli<D>(mscal<D>(-1.0, madd<D>(c2, c3))));
+}
+
+// the left-mixing item: history and source sums over the lanes (no FFT pre-pass in this form)
 template <int D>
 __device__ __forceinline__ void tv_item_w(const NgWeights& W, const Grid& g, const HermV& G, const HermV& S,
-                                          const cplx* minv_ws, int n, int m, int kb, const cplx* tvq, int lane,
-                                          int* status) {
+                                          const cplx* minv_ws, int n, int m, int kb, int lane, int* status) {
     Mat<D> acc = mzero<D>();
     for (int j = lane; j < n; j += 32)
         mfma<D>(acc, mscal<D>(gw(W, n, j), gret<D>(S, n, j, kb)), gtv<D>(G, g, j, m, kb));
     acc = warp_msum<D>(acc);
+    const Mat<D> src = warp_msum<D>(q_tv_part<D>(W, g, G, S, n, m, kb, lane, 32));
     if (lane != 0) return;
     Mat<D> bdf = mzero<D>();
     for (int l = 1; l <= W.k; ++l) bdf = madd<D>(bdf, mscal<D>(W.a[l], gtv<D>(G, g, n - l, m, kb)));
-    Mat<D> rhs = tvq ? q_tv_fft<D>(W, g, G, S, n, m, kb, tvq) : q_tv<D>(W, g, G, S, n, m, kb);
+    Mat<D> rhs = src;
     rhs = msub<D>(rhs, mscal<D>(1.0 / g.h, bdf));
     rhs = msub<D>(rhs, mscal<D>(g.h, mmuli<D>(acc)));
     Mat<D> y = mmul<D>(ld_minv<D>(minv_ws, kb), rhs);
@@ -104,8 +139,7 @@ __device__ __forceinline__ void les_item_w(const NgWeights& W, const Grid& g, co
 // fastest); w_les, w_tv, w_ret: the items of each task.
 template <int D>
 __global__ void __launch_bounds__(128, 1) k_step_bulk_w(Grid g, int n, HermV G, HermV S, const cplx* minv_ws,
-                                                     int64_t w_les, int64_t w_tv, int64_t w_ret, const cplx* tvq,
-                                                     int* status) {
+                                                     int64_t w_les, int64_t w_tv, int64_t w_ret, int* status) {
     const NgWeights& W = c_W[g.k - 1];
     int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -117,7 +151,7 @@ __global__ void __launch_bounds__(128, 1) k_step_bulk_w(Grid g, int n, HermV G, 
     const int kb = (int)(item % g.nb);
     const int col = (int)(item / g.nb);
     if (task == 0) les_item_w<D>(W, g, G, S, minv_ws, n, col + 1, kb, lane, status);
-    else if (task == 1) tv_item_w<D>(W, g, G, S, minv_ws, n, col, kb, tvq, lane, status);
+    else if (task == 1) tv_item_w<D>(W, g, G, S, minv_ws, n, col, kb, lane, status);
     else ret_item_w<D>(W, g, G, S, minv_ws, n, col, kb, lane, status);
 }
 

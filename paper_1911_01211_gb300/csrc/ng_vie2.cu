@@ -24,7 +24,7 @@ cudaError_t step_d(const Grid& g, int n, const HermV& G, const HermV& F, const H
     if (warp) {
         const int64_t w_les = (int64_t)g.nb * (n - 1), w_tv = (int64_t)g.nb * (g.ntau + 1), w_ret = (int64_t)g.nb * n;
         k_v2_bulk_w<D><<<nblk((w_les + w_tv + w_ret) * 32, thr), thr, 0, s>>>(g, n, G, F, Fcc, Q, w_les, w_tv, w_ret,
-                                                                               tvq, status);
+                                                                               status);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         k_v2_diag<D><<<g.nb, NG_BND_THREADS, 0, s>>>(g, n, G, F, Fcc, Q, status);

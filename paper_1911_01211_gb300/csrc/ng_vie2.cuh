@@ -200,16 +200,18 @@ __device__ __forceinline__ void v2_ret_item_w(const NgWeights& W, const Grid& g,
     st<D>(G.ret, tri(n) + m, kb, y);
 }
 
+// the left-mixing item; its source (C^tv_2 + C^tv_3)[F, 1, G^M] = i q_tv with S := F is split over
+// the lanes (no FFT pre-pass in this form)
 template <int D>
 __device__ __forceinline__ void v2_tv_item_w(const NgWeights& W, const Grid& g, const HermV& G, const HermV& F,
-                                             const HermV& Q, int n, int m, int kb, const cplx* tvq, int lane,
-                                             int* status) {
+                                             const HermV& Q, int n, int m, int kb, int lane, int* status) {
     Mat<D> acc = mzero<D>();
     for (int j = lane; j < n; j += 32)
         mfma<D>(acc, mscal<D>(gw(W, n, j), ld<D>(F.ret, tri(n) + j, kb)), gtv<D>(G, g, j, m, kb));
     acc = warp_msum<D>(acc);
+    const Mat<D> src = warp_msum<D>(q_tv_part<D>(W, g, G, F, n, m, kb, lane, 32));
     if (lane != 0) return;
-    Mat<D> rhs = msub<D>(gtv<D>(Q, g, n, m, kb), v2_ctv23<D>(W, g, G, F, n, m, kb, tvq));
+    Mat<D> rhs = msub<D>(gtv<D>(Q, g, n, m, kb), mmuli<D>(src));
     rhs = msub<D>(rhs, mscal<D>(g.h, acc));
     int sing = 0;
     const Mat<D> y = mmul<D>(minv<D>(v2_one_plus<D>(g.h * gw(W, n, n), ld<D>(F.ret, tri(n) + n, kb)), &sing), rhs);
@@ -221,7 +223,7 @@ __device__ __forceinline__ void v2_tv_item_w(const NgWeights& W, const Grid& g, 
 template <int D>
 __global__ void __launch_bounds__(128, 1)
     k_v2_bulk_w(Grid g, int n, HermV G, HermV F, HermV Fcc, HermV Q, int64_t w_les, int64_t w_tv, int64_t w_ret,
-                const cplx* tvq, int* status) {
+                int* status) {
     const NgWeights& W = c_W[g.k - 1];
     int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -232,7 +234,7 @@ __global__ void __launch_bounds__(128, 1)
     else return;
     const int kb = (int)(item % g.nb), col = (int)(item / g.nb);
     if (task == 1) {
-        v2_tv_item_w<D>(W, g, G, F, Q, n, col, kb, tvq, lane, status);
+        v2_tv_item_w<D>(W, g, G, F, Q, n, col, kb, lane, status);
     } else if (task == 2) {
         v2_ret_item_w<D>(W, g, G, F, Q, n, col, kb, lane, status);
     } else {

@@ -11,6 +11,7 @@ cudaError_t vie2_start_launch(const Grid& g, const HermV& G, const HermV& F, con
                               cplx* ws, int* status, cudaStream_t s);
 // time step n > k (conjugate schedule of the lesser column), nf = 1, 2; tvq: the FFT
 // correlation of the left-mixing source of F and G^M at step n (the layout of tvfft_launch),
-// or NULL for the direct sums; warp: one warp per item (small batches) instead of one thread
+// or NULL for the direct sums; warp: one warp per item (small batches) instead of one thread,
+// its source sums split over the lanes (tvq unused)
 cudaError_t vie2_step_launch(const Grid& g, int n, const HermV& G, const HermV& F, const HermV& Fcc, const HermV& Q,
                              const cplx* tvq, bool warp, int* status, cudaStream_t s);
