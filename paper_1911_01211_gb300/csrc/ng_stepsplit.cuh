@@ -13,6 +13,25 @@
 
 #include "ng_step.cuh"
 
+// f(l, w_{L,l}) for this lane's share of the terms l = 0..lmax (L-1 <= lmax <= L) of a Gregory
+// row L.  For rows L > 2k+1 the end terms (l <= k, L-k <= l <= lmax) take one lane each from
+// lane 0 on (at most 2k+2 <= 32 of them for k <= 6), and the unit-weight middle is dealt out
+// from the next lane on with w = 1.0, which the compiler folds (no weight multiply); every
+// lane gets at most ceil((lmax+1)/32) terms, as with a plain stride over l.
+template <class F>
+__device__ __forceinline__ void greg_for_lanes(const NgWeights& W, int L, int lmax, int lane, F&& f) {
+    const int k = W.k;
+    if (L <= 2 * k + 1) {
+        for (int l = lane; l <= lmax; l += 32) f(l, W.greg[L][l]);
+        return;
+    }
+    const int ne = 2 * k + 2 - (L - lmax);  // end terms
+    if (lane <= k) f(lane, W.omega[lane]);
+    else if (lane < ne) f(L - 2 * k - 1 + lane, W.omega[2 * k + 1 - lane]);  // l = L-k .. lmax
+    const int e2 = L - k - 1;
+    for (int l = k + 1 + ((lane - ne) & 31); l <= e2; l += 32) f(l, 1.0);
+}
+
 template <int D>
 __device__ __forceinline__ Mat<D> warp_msum(Mat<D> x) {
 #pragma unroll
@@ -32,8 +51,9 @@ __device__ __forceinline__ void ret_item_w(const NgWeights& W, const Grid& g, co
                                            const cplx* minv_ws, int n, int m, int kb, int lane, int* status) {
     const int L = n - m;  // > k
     Mat<D> acc = mzero<D>();
-    for (int l = lane; l < L; l += 32)
-        mfma<D>(acc, mscal<D>(gw(W, L, l), gret<D>(S, n, m + l, kb)), gret<D>(G, m + l, m, kb));
+    greg_for_lanes(W, L, L - 1, lane, [&](int l, double w) {
+        mfma<D>(acc, mscal<D>(w, gret<D>(S, n, m + l, kb)), gret<D>(G, m + l, m, kb));
+    });
     acc = warp_msum<D>(acc);
     if (lane != 0) return;
     Mat<D> bdf = mzero<D>();
@@ -45,12 +65,13 @@ __device__ __forceinline__ void ret_item_w(const NgWeights& W, const Grid& g, co
 }
 
 // The left-mixing source -i (C^tv_2 + C^tv_3)[S, 1, G^M](n, tau_m) (Eqs. ctv2, ctv3) as q_tv
-// computes it, over the terms l = l0, l0 + ls, ... of its two Gregory sums; the boundary (R)
-// formulas of m <= k and m >= ntau - k ((k+1)^2 terms each) go to the part with l0 = 0.  The
+// computes it, over this lane's terms of its two Gregory sums; the boundary (R) formulas of
+// m <= k and m >= ntau - k ((k+1)^2 terms each) go to lane 0.  The
 // source is linear in the terms, so the parts add up to q_tv.
 template <int D>
 __device__ Mat<D> q_tv_part(const NgWeights& W, const Grid& g, const HermV& G, const HermV& S, int n, int m, int kb,
-                            int l0, int ls) {
+                            int lane) {
+    const int l0 = lane;
     const int k = W.k, T = g.ntau;
     const double xi = (double)g.sig;
     Mat<D> c2 = mzero<D>(), c3 = mzero<D>();
@@ -61,8 +82,9 @@ __device__ Mat<D> q_tv_part(const NgWeights& W, const Grid& g, const HermV& G, c
                 for (int l = 0; l <= k; ++l) mfma<D>(c2, mscal<D>(W.R[m][j][l], gtv<D>(S, g, n, l, kb)), gm);
             }
     } else {
-        for (int l = l0; l <= m; l += ls)
-            mfma<D>(c2, mscal<D>(gw(W, m, l), gtv<D>(S, g, n, m - l, kb)), gmat<D>(G, T - l, kb));
+        greg_for_lanes(W, m, m, lane, [&](int l, double w) {
+            mfma<D>(c2, mscal<D>(w, gtv<D>(S, g, n, m - l, kb)), gmat<D>(G, T - l, kb));
+        });
         c2 = mscal<D>(xi, c2);
     }
     if (m >= T - k) {
@@ -72,8 +94,9 @@ __device__ Mat<D> q_tv_part(const NgWeights& W, const Grid& g, const HermV& G, c
                 for (int l = 0; l <= k; ++l) mfma<D>(c3, mscal<D>(W.R[T - m][j][l], gtv<D>(S, g, n, T - l, kb)), gm);
             }
     } else {
-        for (int l = l0; l <= T - m; l += ls)
-            mfma<D>(c3, mscal<D>(gw(W, T - m, l), gtv<D>(S, g, n, m + l, kb)), gmat<D>(G, l, kb));
+        greg_for_lanes(W, T - m, T - m, lane, [&](int l, double w) {
+            mfma<D>(c3, mscal<D>(w, gtv<D>(S, g, n, m + l, kb)), gmat<D>(G, l, kb));
+        });
     }
     return mscal<D>(g.htau, mmuli<D>(mscal<D>(-1.0, madd<D>(c2, c3))));
 }
@@ -83,10 +106,11 @@ template <int D>
 __device__ __forceinline__ void tv_item_w(const NgWeights& W, const Grid& g, const HermV& G, const HermV& S,
                                           const cplx* minv_ws, int n, int m, int kb, int lane, int* status) {
     Mat<D> acc = mzero<D>();
-    for (int j = lane; j < n; j += 32)
-        mfma<D>(acc, mscal<D>(gw(W, n, j), gret<D>(S, n, j, kb)), gtv<D>(G, g, j, m, kb));
+    greg_for_lanes(W, n, n - 1, lane, [&](int j, double w) {
+        mfma<D>(acc, mscal<D>(w, gret<D>(S, n, j, kb)), gtv<D>(G, g, j, m, kb));
+    });
     acc = warp_msum<D>(acc);
-    const Mat<D> src = warp_msum<D>(q_tv_part<D>(W, g, G, S, n, m, kb, lane, 32));
+    const Mat<D> src = warp_msum<D>(q_tv_part<D>(W, g, G, S, n, m, kb, lane));
     if (lane != 0) return;
     Mat<D> bdf = mzero<D>();
     for (int l = 1; l <= W.k; ++l) bdf = madd<D>(bdf, mscal<D>(W.a[l], gtv<D>(G, g, n - l, m, kb)));
@@ -108,19 +132,21 @@ __device__ __forceinline__ void les_item_w(const NgWeights& W, const Grid& g, co
         for (int j = lane; j <= k; j += 32)
             mfma<D>(c1, mscal<D>(W.greg[m][j], gretx<D>(G, m, j, kb)), ld<D>(S.les, tri(n) + j, kb));
     } else {
-        for (int j = lane; j <= m; j += 32)
-            mfma<D>(c1, mscal<D>(gw(W, m, j), gret<D>(G, m, j, kb)), ld<D>(S.les, tri(n) + j, kb));
+        greg_for_lanes(W, m, m, lane, [&](int j, double w) {
+            mfma<D>(c1, mscal<D>(w, gret<D>(G, m, j, kb)), ld<D>(S.les, tri(n) + j, kb));
+        });
     }
     // sum_j w_{T,j} G^tv(m,j) [Sigma^tv(n,T-j)]^dagger
     Mat<D> c3 = mzero<D>();
-    for (int j = lane; j <= T; j += 32)
-        mfma_db<D>(c3, mscal<D>(gw(W, T, j), gtv<D>(G, g, m, j, kb)), gtv<D>(S, g, n, T - j, kb));
+    greg_for_lanes(W, T, T, lane, [&](int j, double w) {
+        mfma_db<D>(c3, mscal<D>(w, gtv<D>(G, g, m, j, kb)), gtv<D>(S, g, n, T - j, kb));
+    });
     // history sum_{l<n} w_{n,l} G^<(m,l) [Sigma^R(n,l)]^dagger
     Mat<D> hist = mzero<D>();
-    for (int l = lane; l < n; l += 32) {
+    greg_for_lanes(W, n, n - 1, lane, [&](int l, double w) {
         Mat<D> gl = (l >= m) ? ld<D>(G.les, tri(l) + m, kb) : mscal<D>(-1.0, mdag<D>(ld<D>(G.les, tri(m) + l, kb)));
-        mfma_db<D>(hist, mscal<D>(gw(W, n, l), gl), gret<D>(S, n, l, kb));
-    }
+        mfma_db<D>(hist, mscal<D>(w, gl), gret<D>(S, n, l, kb));
+    });
     c1 = warp_msum<D>(c1);
     c3 = warp_msum<D>(c3);
     hist = warp_msum<D>(hist);

@@ -182,8 +182,9 @@ __device__ __forceinline__ void v2_ret_item_w(const NgWeights& W, const Grid& g,
     Mat<D> acc = mzero<D>();
     double wd;
     if (L > k) {
-        for (int l = lane; l < L; l += 32)
-            mfma<D>(acc, mscal<D>(gw(W, L, l), ld<D>(F.ret, tri(n) + m + l, kb)), gret<D>(G, m + l, m, kb));
+        greg_for_lanes(W, L, L - 1, lane, [&](int l, double w) {
+            mfma<D>(acc, mscal<D>(w, ld<D>(F.ret, tri(n) + m + l, kb)), gret<D>(G, m + l, m, kb));
+        });
         wd = gw(W, L, L);
     } else {
         for (int j = 1 + lane; j <= k; j += 32)
@@ -206,10 +207,11 @@ template <int D>
 __device__ __forceinline__ void v2_tv_item_w(const NgWeights& W, const Grid& g, const HermV& G, const HermV& F,
                                              const HermV& Q, int n, int m, int kb, int lane, int* status) {
     Mat<D> acc = mzero<D>();
-    for (int j = lane; j < n; j += 32)
-        mfma<D>(acc, mscal<D>(gw(W, n, j), ld<D>(F.ret, tri(n) + j, kb)), gtv<D>(G, g, j, m, kb));
+    greg_for_lanes(W, n, n - 1, lane, [&](int j, double w) {
+        mfma<D>(acc, mscal<D>(w, ld<D>(F.ret, tri(n) + j, kb)), gtv<D>(G, g, j, m, kb));
+    });
     acc = warp_msum<D>(acc);
-    const Mat<D> src = warp_msum<D>(q_tv_part<D>(W, g, G, F, n, m, kb, lane, 32));
+    const Mat<D> src = warp_msum<D>(q_tv_part<D>(W, g, G, F, n, m, kb, lane));
     if (lane != 0) return;
     Mat<D> rhs = msub<D>(gtv<D>(Q, g, n, m, kb), mmuli<D>(src));
     rhs = msub<D>(rhs, mscal<D>(g.h, acc));
