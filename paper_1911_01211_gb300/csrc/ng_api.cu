@@ -297,10 +297,11 @@ ng_status prep_tvfft(ng_ctx* c, const Grid& g, int n, const HermV& G, const Herm
     return NG_OK;
 }
 
-// the boundary of step n in three launches, its (A)-row sums over (row, problem, chunk) blocks
+// the boundary of step n in three launches, its (A)-row sums over (row, problem, chunk) blocks;
+// pre_done: the retarded start-up ran in the leading warps of the bulk launch
 template <int D>
 ng_status boundary_spread(ng_ctx* c, const Grid& g, int n, const HermV& G, const HermV& S, const FuncV& eps,
-                          cudaStream_t s) {
+                          bool pre_done, cudaStream_t s) {
     ng_status st;
     const int k = g.k, nq = (n <= 2 * k) ? n : k + 1;
     const int64_t terms = std::max(n, g.ntau) + 1;
@@ -308,11 +309,13 @@ ng_status boundary_spread(ng_ctx* c, const Grid& g, int n, const HermV& G, const
     const int nchunk = (int)std::max<int64_t>(1, std::min<int64_t>({want, (terms + NG_BND_THREADS - 1) / NG_BND_THREADS, 64}));
     const size_t need = sizeof(cplx) * (size_t)nq * g.nb * nchunk * 2 * D * D;
     if ((st = ensure(c, &c->ws_bnd, &c->ws_bnd_bytes, need))) return st;
-    k_bnd_pre<D><<<nblocks(g.nb, 64), 64, 0, s>>>(g, n, G, S, eps, c->d_status);
-    if ((st = check_launch(c, "k_bnd_pre"))) return st;
+    if (!pre_done) {
+        k_bnd_pre<D><<<g.nb, 32, 0, s>>>(g, n, G, S, eps, c->d_status);
+        if ((st = check_launch(c, "k_bnd_pre"))) return st;
+    }
     k_bnd_src<D><<<dim3(nq, g.nb, nchunk), NG_BND_THREADS, 0, s>>>(g, n, G, S, nchunk, (cplx*)c->ws_bnd);
     if ((st = check_launch(c, "k_bnd_src"))) return st;
-    k_bnd_fin<D><<<nblocks(g.nb, 64), 64, 0, s>>>(g, n, G, S, eps, nchunk, (const cplx*)c->ws_bnd, c->d_status);
+    k_bnd_fin<D><<<g.nb, 32, 0, s>>>(g, n, G, S, eps, nchunk, (const cplx*)c->ws_bnd, c->d_status);
     return check_launch(c, "k_bnd_fin");
 }
 
@@ -328,6 +331,12 @@ ng_status launch_timestep(ng_ctx* c, const Grid& g, int n, const HermV& G, const
     // the warp form splits the left-mixing source over its lanes instead of the FFT pre-pass
     const int64_t items = it_les + it_tv + it_ret;
     const bool warp = c->bulk_split == NG_BULK_WARP || (c->bulk_split == NG_BULK_AUTO && items < (int64_t)c->sms * thr);
+    // small batches: the boundary's (A)-row sums spread over (row, problem, chunk) blocks, and
+    // with the warp bulk its retarded start-up in the bulk launch's leading warps
+    const int nq = (n <= 2 * k) ? n : k + 1;
+    const bool spread = c->bulk_split == NG_BULK_WARP ||
+                        (c->bulk_split == NG_BULK_AUTO && (int64_t)nq * g.nb < 2 * (int64_t)c->sms);
+    const int64_t w_pre = (warp && spread) ? g.nb : 0;
     const cplx* tvq = nullptr;
     ng_status sm = warp ? NG_OK : prep_tvfft(c, g, n, G, S, s, &tvq);
     if (sm) return sm;
@@ -335,8 +344,8 @@ ng_status launch_timestep(ng_ctx* c, const Grid& g, int n, const HermV& G, const
     if (e0 >= 0) cudaEventRecord(c->ev_pool[e0], s);
     if ((sm = launch_minv<D>(c, g, n, S, eps, s))) return sm;
     if (warp) {
-        k_step_bulk_w<D><<<nblocks(items * 32, thr), thr, 0, s>>>(g, n, G, S, (const cplx*)c->ws_minv, it_les, it_tv,
-                                                                 it_ret, c->d_status);
+        k_step_bulk_w<D><<<nblocks((w_pre + items) * 32, thr), thr, 0, s>>>(g, n, G, S, eps, (const cplx*)c->ws_minv,
+                                                                           w_pre, it_les, it_tv, it_ret, c->d_status);
     } else {
         k_step_bulk<D><<<b_les + b_tv + b_ret, thr, 0, s>>>(g, n, G, S, eps, (const cplx*)c->ws_minv, b_les, b_tv,
                                                             b_ret, tvq, c->d_status);
@@ -349,10 +358,8 @@ ng_status launch_timestep(ng_ctx* c, const Grid& g, int n, const HermV& G, const
     }
     long e1 = prof_pair(c, 1);
     if (e1 >= 0) cudaEventRecord(c->ev_pool[e1], s);
-    // small batches: the boundary's (A)-row sums spread over (row, problem, chunk) blocks
-    const int nq = (n <= 2 * k) ? n : k + 1;
-    if (c->bulk_split == NG_BULK_WARP || (c->bulk_split == NG_BULK_AUTO && (int64_t)nq * g.nb < 2 * (int64_t)c->sms)) {
-        st = boundary_spread<D>(c, g, n, G, S, eps, s);
+    if (spread) {
+        st = boundary_spread<D>(c, g, n, G, S, eps, w_pre > 0, s);
         if (e1 >= 0) cudaEventRecord(c->ev_pool[e1 + 1], s);
         return st;
     }

@@ -326,6 +326,66 @@ __device__ inline int dense_solve(cplx* A, int N, cplx* B, int nrhs) {
     return 0;
 }
 
+// The same elimination by the 32 lanes of one warp (every lane calls it; A, B and the scratch
+// f[N] visible to the warp).  Per column the pivot is the first row of largest |A[r][c]|^2, as in
+// dense_solve; the lanes swap the rows, form the factors of the rows below once and update the
+// trailing elements, each element receiving the operations of dense_solve in the same order, so
+// the reduced system is bitwise that of dense_solve.  The back substitution runs column by
+// column (x_c = B[c] / A[c][c], then B[r] -= A[r][c] x_c for the rows r < c in parallel).
+// Returns 1 on every lane when a pivot vanishes.  FP64 on this part is issued per warp
+// instruction whatever the number of active lanes, so the lanes cost nothing over one thread.
+__device__ inline int warp_dense_solve(cplx* A, int N, cplx* B, int nrhs, cplx* f, int lane) {
+    const unsigned full = 0xffffffffu;
+    for (int c = 0; c < N; ++c) {
+        double best = -1.0;
+        int p = N;
+        for (int r = c + lane; r < N; r += 32) {
+            const double v = cabs2(A[r * N + c]);
+            if (v > best) { best = v; p = r; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double bo = __shfl_xor_sync(full, best, o);
+            const int po = __shfl_xor_sync(full, p, o);
+            if (bo > best || (bo == best && po < p)) { best = bo; p = po; }
+        }
+        if (best == 0.0) return 1;
+        if (p >= N) p = c;   // no comparable entry (NaN column): keep the row, as dense_solve does
+        if (p != c) {
+            for (int j = lane; j < N; j += 32) {
+                const cplx t = A[c * N + j]; A[c * N + j] = A[p * N + j]; A[p * N + j] = t;
+            }
+            for (int j = lane; j < nrhs; j += 32) {
+                const cplx t = B[c * nrhs + j]; B[c * nrhs + j] = B[p * nrhs + j]; B[p * nrhs + j] = t;
+            }
+        }
+        __syncwarp();
+        const cplx inv = cdiv(cr(1.0), A[c * N + c]);
+        for (int r = c + 1 + lane; r < N; r += 32) f[r] = cmul(A[r * N + c], inv);
+        __syncwarp();
+        const int wa = N - c, w = wa + nrhs, cnt = (N - c - 1) * w;
+        for (int e = lane; e < cnt; e += 32) {
+            const int r = c + 1 + e / w, j = e % w;
+            const cplx fr = f[r];
+            if (fr.x == 0.0 && fr.y == 0.0) continue;
+            if (j < wa) A[r * N + c + j] = csub(A[r * N + c + j], cmul(fr, A[c * N + c + j]));
+            else B[r * nrhs + j - wa] = csub(B[r * nrhs + j - wa], cmul(fr, B[c * nrhs + j - wa]));
+        }
+        __syncwarp();
+    }
+    for (int c = N - 1; c >= 0; --c) {
+        const cplx inv = cdiv(cr(1.0), A[c * N + c]);
+        for (int j = lane; j < nrhs; j += 32) B[c * nrhs + j] = cmul(B[c * nrhs + j], inv);
+        __syncwarp();
+        for (int e = lane; e < c * nrhs; e += 32) {
+            const int r = e / nrhs, j = e % nrhs;
+            B[r * nrhs + j] = csub(B[r * nrhs + j], cmul(A[r * N + c], B[c * nrhs + j]));
+        }
+        __syncwarp();
+    }
+    return 0;
+}
+
 // block-wide sum of a Mat<D> in a fixed order (deterministic); result valid in thread 0
 template <int D>
 __device__ Mat<D> block_sum(Mat<D> x, cplx* red /* blockDim.x * D*D */) {
@@ -354,38 +414,47 @@ __device__ Mat<D> block_sum(Mat<D> x, cplx* red /* blockDim.x * D*D */) {
 #define NG_BND_THREADS 128
 #define NG_MAXQ (2 * NG_KMAX + 1)
 
+// element (a, b) of block e of a component, problem kb
+__device__ __forceinline__ cplx& cel(const Comp& c, int64_t e, int a, int b, int D, int kb) {
+    return c.p[(e * (D * D) + a * D + b) * c.ldk + (c.ldk == 1 ? 0 : kb)];
+}
+
 // Conjugate VIDE start-up along row n (implementation (A), Eq. MBCVSAMx_cc_start): G^R(n, n) = -i
-// and G^R(n, n-l), l = 1..k, by one (k nf)^2 solve.  One thread; Ash, Bsh: shared scratch.
+// and G^R(n, n-l), l = 1..k, by one (k nf)^2 solve.  One warp (all lanes call it): the lanes build
+// the k (k+1) blocks of the system, then solve it together.  Ash, Bsh, f: the warp's scratch.
 template <int D>
-__device__ void ret_row_startup(const NgWeights& W, const Grid& g, int n, const HermV& G, const HermV& S,
-                                const FuncV& eps, int kb, cplx* Ash, cplx* Bsh, int* status) {
+__device__ void ret_row_startup_w(const NgWeights& W, const Grid& g, int n, const HermV& G, const HermV& S,
+                                  const FuncV& eps, int kb, cplx* Ash, cplx* Bsh, cplx* f, int lane, int* status) {
     const int k = W.k;
     // unknowns y_1..y_k (y_j = G^R(n, n-j)), y_0 = -i; sum_{l>=1} y_l Mh[l][j] = -y_0 Mh[0][j]
     // with Mh[l][j] = D_{j,l}/h + delta_{lj} i(eps_{n-j} - mu) + h s_{j,l} i Sigma~^R(n-l, n-j).
     // Transposed: sum_l Mh[l][j]^T y_l^T = -(y_0 Mh[0][j])^T.
     const int N = k * D;
-    for (int j = 1; j <= k; ++j) {
-        for (int l = 0; l <= k; ++l) {
-            Mat<D> Mh = meye<D>(cr(W.D[j][l] / g.h));
-            Mh = madd<D>(Mh, mscal<D>(g.h * W.greg[j][l], mmuli<D>(gretx<D>(S, n - l, n - j, kb))));
-            if (l == j) {
-                Mat<D> e = ldf<D>(eps, n - j, kb);
-                for (int a = 0; a < D; ++a) e.v[a][a].x -= g.mu;
-                Mh = madd<D>(Mh, mmuli<D>(e));
-            }
-            if (l == 0) {
-                Mat<D> r = mmul<D>(meye<D>(make_double2(0.0, -1.0)), Mh);  // y_0 Mh[0][j]
-                for (int a = 0; a < D; ++a)
-                    for (int c = 0; c < D; ++c) Bsh[((j - 1) * D + a) * D + c] = cneg(r.v[c][a]);
-            } else {
-                for (int a = 0; a < D; ++a)
-                    for (int b = 0; b < D; ++b) Ash[((j - 1) * D + a) * N + (l - 1) * D + b] = Mh.v[b][a];
-            }
+    for (int p = lane; p < k * (k + 1); p += 32) {
+        const int j = 1 + p / (k + 1), l = p % (k + 1);
+        Mat<D> Mh = meye<D>(cr(W.D[j][l] / g.h));
+        Mh = madd<D>(Mh, mscal<D>(g.h * W.greg[j][l], mmuli<D>(gretx<D>(S, n - l, n - j, kb))));
+        if (l == j) {
+            Mat<D> e = ldf<D>(eps, n - j, kb);
+            for (int a = 0; a < D; ++a) e.v[a][a].x -= g.mu;
+            Mh = madd<D>(Mh, mmuli<D>(e));
+        }
+        if (l == 0) {
+            Mat<D> r = mmul<D>(meye<D>(make_double2(0.0, -1.0)), Mh);  // y_0 Mh[0][j]
+            for (int a = 0; a < D; ++a)
+                for (int c = 0; c < D; ++c) Bsh[((j - 1) * D + a) * D + c] = cneg(r.v[c][a]);
+        } else {
+            for (int a = 0; a < D; ++a)
+                for (int b = 0; b < D; ++b) Ash[((j - 1) * D + a) * N + (l - 1) * D + b] = Mh.v[b][a];
         }
     }
-    if (dense_solve(Ash, N, Bsh, D)) atomicOr(status, NGF_SINGULAR);
-    st<D>(G.ret, tri(n) + n, kb, meye<D>(make_double2(0.0, -1.0)));
-    for (int l = 1; l <= k; ++l) {
+    __syncwarp();
+    const int bad = warp_dense_solve(Ash, N, Bsh, D, f, lane);
+    if (lane == 0) {
+        if (bad) atomicOr(status, NGF_SINGULAR);
+        st<D>(G.ret, tri(n) + n, kb, meye<D>(make_double2(0.0, -1.0)));
+    }
+    for (int l = 1 + lane; l <= k; l += 32) {
         Mat<D> y;
         for (int a = 0; a < D; ++a)
             for (int c = 0; c < D; ++c) y.v[c][a] = Bsh[((l - 1) * D + a) * D + c];
@@ -395,39 +464,110 @@ __device__ void ret_row_startup(const NgWeights& W, const Grid& g, int n, const 
 }
 
 // VIDE start-up of column n for the rows m = 1..k (Eq. vdiff_start): sum_l M_{m,l} y_l =
-// q_m - M_{m,0} y_0 with y_0 = G^<(0, n) and the sources q_m in qsrc[m-1].  One thread.
+// q_m - M_{m,0} y_0 with y_0 = G^<(0, n) and the sources q_m in qsrc[m-1].  One warp: the lanes
+// build the blocks (m, l), then solve together.
 template <int D>
-__device__ void les_col_startup(const NgWeights& W, const Grid& g, int n, const HermV& G, const HermV& S,
-                                const FuncV& eps, int kb, const cplx (*qsrc)[D][D], cplx* Ash, cplx* Bsh,
-                                int* status) {
+__device__ void les_col_startup_w(const NgWeights& W, const Grid& g, int n, const HermV& G, const HermV& S,
+                                  const FuncV& eps, int kb, const cplx (*qsrc)[D][D], cplx* Ash, cplx* Bsh, cplx* f,
+                                  int lane, int* status) {
     const int k = W.k;
     const int N = k * D;
-    Mat<D> y0 = ld<D>(G.les, tri(n) + 0, kb);
-    for (int m = 1; m <= k; ++m) {
-        Mat<D> e = ldf<D>(eps, m, kb);
-        for (int a = 0; a < D; ++a) e.v[a][a].x -= g.mu;
-        Mat<D> rhs;
-        for (int a = 0; a < D; ++a)
-            for (int b = 0; b < D; ++b) rhs.v[a][b] = qsrc[m - 1][a][b];
-        for (int l = 0; l <= k; ++l) {
-            Mat<D> M = meye<D>(cr(W.D[m][l] / g.h));
-            M = madd<D>(M, mscal<D>(g.h * W.greg[m][l], mmuli<D>(gretx<D>(S, m, l, kb))));
-            if (l == m) M = madd<D>(M, mmuli<D>(e));
-            if (l == 0) rhs = msub<D>(rhs, mmul<D>(M, y0));
-            else
-                for (int a = 0; a < D; ++a)
-                    for (int b = 0; b < D; ++b) Ash[((m - 1) * D + a) * N + (l - 1) * D + b] = M.v[a][b];
+    for (int p = lane; p < k * (k + 1); p += 32) {
+        const int m = 1 + p / (k + 1), l = p % (k + 1);
+        Mat<D> M = meye<D>(cr(W.D[m][l] / g.h));
+        M = madd<D>(M, mscal<D>(g.h * W.greg[m][l], mmuli<D>(gretx<D>(S, m, l, kb))));
+        if (l == m) {
+            Mat<D> e = ldf<D>(eps, m, kb);
+            for (int a = 0; a < D; ++a) e.v[a][a].x -= g.mu;
+            M = madd<D>(M, mmuli<D>(e));
         }
-        for (int a = 0; a < D; ++a)
-            for (int c = 0; c < D; ++c) Bsh[((m - 1) * D + a) * D + c] = rhs.v[a][c];
+        if (l == 0) {
+            Mat<D> rhs;
+            for (int a = 0; a < D; ++a)
+                for (int b = 0; b < D; ++b) rhs.v[a][b] = qsrc[m - 1][a][b];
+            rhs = msub<D>(rhs, mmul<D>(M, ld<D>(G.les, tri(n) + 0, kb)));
+            for (int a = 0; a < D; ++a)
+                for (int c = 0; c < D; ++c) Bsh[((m - 1) * D + a) * D + c] = rhs.v[a][c];
+        } else {
+            for (int a = 0; a < D; ++a)
+                for (int b = 0; b < D; ++b) Ash[((m - 1) * D + a) * N + (l - 1) * D + b] = M.v[a][b];
+        }
     }
-    if (dense_solve(Ash, N, Bsh, D)) atomicOr(status, NGF_SINGULAR);
-    for (int m = 1; m <= k; ++m) {
+    __syncwarp();
+    if (warp_dense_solve(Ash, N, Bsh, D, f, lane) && lane == 0) atomicOr(status, NGF_SINGULAR);
+    for (int m = 1 + lane; m <= k; m += 32) {
         Mat<D> y;
         for (int a = 0; a < D; ++a)
             for (int c = 0; c < D; ++c) y.v[a][c] = Bsh[((m - 1) * D + a) * D + c];
         if (!mfinite<D>(y)) atomicOr(status, NGF_NONFINITE);
         st<D>(G.les, tri(n) + m, kb, y);
+    }
+    __syncwarp();
+}
+
+// Serial VIDE steps (Eq. MBCVSAMx_t) of column n in the first argument, rows m = mstep..n, with
+// the sources qsrc[m - m0] and the partial histories hsrc[m - m0] over l < lfrom.  One warp: the
+// inverse step matrices of all rows first, one lane per row (they do not depend on the column);
+// then per row, lane (grp, a, b) sums element (a, b) of the history and BDF terms l = grp,
+// grp + 32/D^2, ..., the groups are added by a butterfly, and the lanes of group 0 store the
+// elements of G^<(m, n).  Mi: the warp's scratch of NG_MAXQ + 1 blocks.
+template <int D>
+__device__ void les_steps_w(const NgWeights& W, const Grid& g, int n, const HermV& G, const HermV& S,
+                            const FuncV& eps, int kb, const cplx (*qsrc)[D][D], const cplx (*hsrc)[D][D],
+                            cplx (*Mi)[D][D], int m0, int mstep, int lfrom, int lane, int* status) {
+    static_assert(D * D <= 32, "one warp holds the elements of a block");
+    const unsigned full = 0xffffffffu;
+    const int k = W.k;
+    int sing = 0;
+    for (int m = mstep + lane; m <= n; m += 32) {
+        const Mat<D> mi = minv<D>(step_matrix<D>(W, g, S, eps, m, kb), &sing);
+        for (int a = 0; a < D; ++a)
+            for (int b = 0; b < D; ++b) Mi[m - m0][a][b] = mi.v[a][b];
+    }
+    if (__any_sync(full, sing) && lane == 0) atomicOr(status, NGF_SINGULAR);
+    __syncwarp();
+    constexpr int E = D * D, NGR = 32 / E;
+    const int grp = lane / E, e = lane % E, a = e / D, b = e % D;
+    const double hinv = 1.0 / g.h;
+    for (int m = mstep; m <= n; ++m) {
+        const int r = m - m0;
+        cplx hs = cr(0.0), bd = cr(0.0);
+        for (int l = lfrom + grp; l < m; l += NGR) {
+            const double w = gw(W, m, l);
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                const cplx sx = cel(S.ret, tri(m) + l, a, c, D, kb);
+                hs = cfma(make_double2(w * sx.x, w * sx.y), cel(G.les, tri(n) + l, c, b, D, kb), hs);
+            }
+        }
+        for (int l = 1 + grp; l <= k; l += NGR) {
+            const cplx x = cel(G.les, tri(n) + m - l, a, b, D, kb);
+            bd = cadd(bd, make_double2(W.a[l] * x.x, W.a[l] * x.y));
+        }
+#pragma unroll
+        for (int o = E; o < 32; o <<= 1) {
+            hs.x += __shfl_xor_sync(full, hs.x, o);
+            hs.y += __shfl_xor_sync(full, hs.y, o);
+            bd.x += __shfl_xor_sync(full, bd.x, o);
+            bd.y += __shfl_xor_sync(full, bd.y, o);
+        }
+        // acc = q - bdf / h - h i (h_partial + h_rows)
+        const cplx h0 = cadd(hsrc[r][a][b], hs);
+        cplx acc = csub(qsrc[r][a][b], make_double2(hinv * bd.x, hinv * bd.y));
+        acc = csub(acc, make_double2(-g.h * h0.y, g.h * h0.x));
+        cplx y = cr(0.0);
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            cplx ac;
+            ac.x = __shfl_sync(full, acc.x, c * D + b);
+            ac.y = __shfl_sync(full, acc.y, c * D + b);
+            y = cfma(Mi[r][a][c], ac, y);
+        }
+        if (grp == 0) {
+            if (!isfinite(y.x) || !isfinite(y.y)) atomicOr(status, NGF_NONFINITE);
+            cel(G.les, tri(n) + m, a, b, D, kb) = y;
+        }
+        __syncwarp();
     }
 }
 
@@ -443,14 +583,16 @@ __global__ void __launch_bounds__(NG_BND_THREADS) k_step_boundary(Grid g, int n,
     __shared__ cplx red[NG_BND_THREADS * D * D];
     __shared__ cplx qsrc[NG_MAXQ + 1][D][D];   // sources per boundary row
     __shared__ cplx hsrc[NG_MAXQ + 1][D][D];   // partial histories per boundary row
+    __shared__ cplx Mi[NG_MAXQ + 1][D][D];     // inverse step matrices of the boundary rows
     __shared__ cplx Ash[(NG_KMAX * D) * (NG_KMAX * D)];
     __shared__ cplx Bsh[(NG_KMAX * D) * D];
+    __shared__ cplx fsh[NG_KMAX * D];
 
-    // ---- retarded: conjugate start-up along row n (implementation (A)) -------------
-    if (t == 0) {
-        ret_row_startup<D>(W, g, n, G, S, eps, kb, Ash, Bsh, status);
+    // ---- retarded: conjugate start-up along row n (implementation (A)), warp 0 -------
+    if (t < 32) {
+        ret_row_startup_w<D>(W, g, n, G, S, eps, kb, Ash, Bsh, fsh, t, status);
         // G^<(0,n) = -[G^tv(n,0)]^dagger  (Eq. dyson_ini_les)
-        st<D>(G.les, tri(n) + 0, kb, mscal<D>(-1.0, mdag<D>(gtv<D>(G, g, n, 0, kb))));
+        if (t == 0) st<D>(G.les, tri(n) + 0, kb, mscal<D>(-1.0, mdag<D>(gtv<D>(G, g, n, 0, kb))));
     }
     __syncthreads();
 
@@ -474,32 +616,13 @@ __global__ void __launch_bounds__(NG_BND_THREADS) k_step_boundary(Grid g, int n,
                 for (int b = 0; b < D; ++b) { qsrc[r][a][b] = q.v[a][b]; hsrc[r][a][b] = hsum.v[a][b]; }
     }
     __syncthreads();
-    if (t != 0) return;
-    int sing = 0;
+    if (t >= 32) return;
     int mstep = m0;
     if (full) {
-        les_col_startup<D>(W, g, n, G, S, eps, kb, qsrc, Ash, Bsh, status);
+        les_col_startup_w<D>(W, g, n, G, S, eps, kb, qsrc, Ash, Bsh, fsh, t, status);
         mstep = k + 1;
     }
-    // serial VIDE steps (Eq. MBCVSAMx_t) in the first argument, m = mstep..n
-    for (int m = mstep; m <= n; ++m) {
-        const int r = m - m0;
-        Mat<D> acc, h0;
-        for (int a = 0; a < D; ++a)
-            for (int b = 0; b < D; ++b) { acc.v[a][b] = qsrc[r][a][b]; h0.v[a][b] = hsrc[r][a][b]; }
-        const int lfrom = full ? 0 : m0;
-        for (int l = lfrom; l < m; ++l)
-            mfma<D>(h0, mscal<D>(gw(W, m, l), gret<D>(S, m, l, kb)), ld<D>(G.les, tri(n) + l, kb));
-        Mat<D> bdf = mzero<D>();
-        for (int l = 1; l <= k; ++l) bdf = madd<D>(bdf, mscal<D>(W.a[l], ld<D>(G.les, tri(n) + m - l, kb)));
-        acc = msub<D>(acc, mscal<D>(1.0 / g.h, bdf));
-        acc = msub<D>(acc, mscal<D>(g.h, mmuli<D>(h0)));
-        Mat<D> Mm = step_matrix<D>(W, g, S, eps, m, kb);
-        Mat<D> y = mmul<D>(minv<D>(Mm, &sing), acc);
-        if (!mfinite<D>(y)) atomicOr(status, NGF_NONFINITE);
-        st<D>(G.les, tri(n) + m, kb, y);
-    }
-    if (sing) atomicOr(status, NGF_SINGULAR);
+    les_steps_w<D>(W, g, n, G, S, eps, kb, qsrc, hsrc, Mi, m0, mstep, full ? 0 : m0, t, status);
 }
 
 // Serial schedule of step n (the paper's dyson_timestep): the retarded row by the conjugate
@@ -520,10 +643,11 @@ __global__ void __launch_bounds__(NG_BND_THREADS) k_step_serial(Grid g, int n, H
     __shared__ cplx qsrc[NG_MAXQ + 1][D][D];
     __shared__ cplx Ash[(NG_KMAX * D) * (NG_KMAX * D)];
     __shared__ cplx Bsh[(NG_KMAX * D) * D];
+    __shared__ cplx fsh[NG_KMAX * D];
     int sing = 0;
 
     // ---- retarded row: y_l = G^R(n, n-l), kernel i Sigma^R(n-l, n-j) ----------------------
-    if (t == 0) ret_row_startup<D>(W, g, n, G, S, eps, kb, Ash, Bsh, status);
+    if (t < 32) ret_row_startup_w<D>(W, g, n, G, S, eps, kb, Ash, Bsh, fsh, t, status);
     __syncthreads();
     for (int j = k + 1; j <= n; ++j) {
         Mat<D> part = mzero<D>();
@@ -555,7 +679,7 @@ __global__ void __launch_bounds__(NG_BND_THREADS) k_step_serial(Grid g, int n, H
                 for (int b = 0; b < D; ++b) qsrc[m - 1][a][b] = q.v[a][b];
     }
     __syncthreads();
-    if (t == 0) les_col_startup<D>(W, g, n, G, S, eps, kb, qsrc, Ash, Bsh, status);
+    if (t < 32) les_col_startup_w<D>(W, g, n, G, S, eps, kb, qsrc, Ash, Bsh, fsh, t, status);
     __syncthreads();
     for (int m = k + 1; m <= n; ++m) {
         Mat<D> q = block_sum<D>(q_lesA_part<D>(W, g, G, S, m, n, kb, t, blockDim.x), red);

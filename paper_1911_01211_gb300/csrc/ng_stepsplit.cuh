@@ -161,14 +161,58 @@ __device__ __forceinline__ void les_item_w(const NgWeights& W, const Grid& g, co
     st<D>(G.les, tri(n) + m, kb, y);
 }
 
-// One warp per item, items ordered as in k_step_bulk (lesser, left-mixing, retarded; problem
-// fastest); w_les, w_tv, w_ret: the items of each task.
+// ---- the boundary of a time step for small batches, in three launches -----------------------
+// k_step_boundary runs one block per problem, so for a single problem its (A)-row sources, sums
+// over n and ntau terms, run on one SM.  Here: (1) per problem, one warp, the retarded (A) row
+// start-up (k_bnd_pre, or the leading warps of k_step_bulk_w); (2) the (A)-row sources and
+// partial histories spread over blocks (row, problem, chunk), each block summing its chunk's
+// terms (k_bnd_src); (3) per problem, one warp, G^<(0,n), the chunk partials added in chunk order
+// and the (A) steps of the lesser column (k_bnd_fin), as in k_step_boundary.  G^<(0,n) =
+// -[G^tv(n,0)]^dagger (Eq. dyson_ini_les) reads the left-mixing value of the bulk launch, so the
+// start-up warps, which may run beside that launch, leave it to k_bnd_fin, and k_bnd_src forms
+// its l = 0 term from G^tv(n,0) itself.
+
 template <int D>
-__global__ void __launch_bounds__(128, 1) k_step_bulk_w(Grid g, int n, HermV G, HermV S, const cplx* minv_ws,
-                                                     int64_t w_les, int64_t w_tv, int64_t w_ret, int* status) {
+__device__ __forceinline__ Mat<D> les0_of_tv(const Grid& g, const HermV& G, int n, int kb) {
+    return mscal<D>(-1.0, mdag<D>(gtv<D>(G, g, n, 0, kb)));
+}
+
+// the retarded start-up of problem kb by one warp; sh: the warp's scratch
+template <int D>
+__device__ __forceinline__ void bnd_pre_warp(const NgWeights& W, const Grid& g, int n, const HermV& G,
+                                             const HermV& S, const FuncV& eps, int kb, cplx* sh, int lane,
+                                             int* status) {
+    constexpr int N = NG_KMAX * D;
+    ret_row_startup_w<D>(W, g, n, G, S, eps, kb, sh, sh + N * N, sh + N * N + N * D, lane, status);
+}
+template <int D>
+__host__ __device__ constexpr int bnd_pre_scratch() { return (NG_KMAX * D) * (NG_KMAX * D) + (NG_KMAX * D) * D + NG_KMAX * D; }
+
+// one warp (block of 32) per problem
+template <int D>
+__global__ void __launch_bounds__(32) k_bnd_pre(Grid g, int n, HermV G, HermV S, FuncV eps, int* status) {
+    __shared__ cplx sh[bnd_pre_scratch<D>()];
+    bnd_pre_warp<D>(c_W[g.k - 1], g, n, G, S, eps, blockIdx.x, sh, threadIdx.x, status);
+}
+
+// One warp per item, items ordered as in k_step_bulk (lesser, left-mixing, retarded; problem
+// fastest); w_les, w_tv, w_ret: the items of each task.  With w_pre = nb the first nb warps
+// run the boundary's retarded start-up of problem kb = warp (bnd_pre_warp), which reads only
+// Sigma and eps and writes G^R(n, n-k..n), which no bulk item reads, so that it overlaps the
+// bulk instead of taking a launch of its own.
+template <int D>
+__global__ void __launch_bounds__(128, 1) k_step_bulk_w(Grid g, int n, HermV G, HermV S, FuncV eps,
+                                                     const cplx* minv_ws, int64_t w_pre, int64_t w_les,
+                                                     int64_t w_tv, int64_t w_ret, int* status) {
     const NgWeights& W = c_W[g.k - 1];
     int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
+    if (item < w_pre) {
+        __shared__ cplx sh[4][bnd_pre_scratch<D>()];   // blockDim.x = 128: four warps
+        bnd_pre_warp<D>(W, g, n, G, S, eps, (int)item, sh[threadIdx.x >> 5], lane, status);
+        return;
+    }
+    item -= w_pre;
     int task;
     if (item < w_les) task = 0;
     else if ((item -= w_les) < w_tv) task = 1;
@@ -179,26 +223,6 @@ __global__ void __launch_bounds__(128, 1) k_step_bulk_w(Grid g, int n, HermV G, 
     if (task == 0) les_item_w<D>(W, g, G, S, minv_ws, n, col + 1, kb, lane, status);
     else if (task == 1) tv_item_w<D>(W, g, G, S, minv_ws, n, col, kb, lane, status);
     else ret_item_w<D>(W, g, G, S, minv_ws, n, col, kb, lane, status);
-}
-
-// ---- the boundary of a time step for small batches, in three launches -----------------------
-// k_step_boundary runs one block per problem, so for a single problem its (A)-row sources, sums
-// over n and ntau terms, run on one SM.  Here: (1) per problem, the retarded (A) row start-up
-// and G^<(0,n) (k_bnd_pre); (2) the (A)-row sources and partial histories spread over blocks
-// (row, problem, chunk), each block summing its chunk's terms (k_bnd_src); (3) per problem, the
-// chunk partials added in chunk order and the serial (A) steps of the lesser column
-// (k_bnd_fin), as in k_step_boundary.
-
-template <int D>
-__global__ void k_bnd_pre(Grid g, int n, HermV G, HermV S, FuncV eps, int* status) {
-    const int kb = blockIdx.x * blockDim.x + threadIdx.x;
-    if (kb >= g.nb) return;
-    const NgWeights& W = c_W[g.k - 1];
-    cplx Ash[(NG_KMAX * D) * (NG_KMAX * D)];
-    cplx Bsh[(NG_KMAX * D) * D];
-    ret_row_startup<D>(W, g, n, G, S, eps, kb, Ash, Bsh, status);
-    // G^<(0,n) = -[G^tv(n,0)]^dagger  (Eq. dyson_ini_les)
-    st<D>(G.les, tri(n) + 0, kb, mscal<D>(-1.0, mdag<D>(gtv<D>(G, g, n, 0, kb))));
 }
 
 // block (r, kb, c): row m = m0 + r, terms j = c B + t, c B + t + nchunk B, ...; partials at
@@ -217,7 +241,8 @@ __global__ void __launch_bounds__(NG_BND_THREADS) k_bnd_src(Grid g, int n, HermV
     Mat<D> hp = mzero<D>();
     if (!full && m > k)
         for (int l = j0; l < m0; l += js)
-            mfma<D>(hp, mscal<D>(gw(W, m, l), gret<D>(S, m, l, kb)), ld<D>(G.les, tri(n) + l, kb));
+            mfma<D>(hp, mscal<D>(gw(W, m, l), gret<D>(S, m, l, kb)),
+                    l == 0 ? les0_of_tv<D>(g, G, n, kb) : ld<D>(G.les, tri(n) + l, kb));
     const Mat<D> hsum = block_sum<D>(hp, red);
     if (t != 0) return;
     cplx* o = part + (((int64_t)r * g.nb + kb) * nchunk + c) * 2 * D * D;
@@ -228,54 +253,32 @@ __global__ void __launch_bounds__(NG_BND_THREADS) k_bnd_src(Grid g, int n, HermV
         }
 }
 
+// one warp (block of 32) per problem
 template <int D>
-__global__ void k_bnd_fin(Grid g, int n, HermV G, HermV S, FuncV eps, int nchunk, const cplx* part, int* status) {
-    const int kb = blockIdx.x * blockDim.x + threadIdx.x;
-    if (kb >= g.nb) return;
+__global__ void __launch_bounds__(32) k_bnd_fin(Grid g, int n, HermV G, HermV S, FuncV eps, int nchunk,
+                                                const cplx* part, int* status) {
+    const int kb = blockIdx.x, lane = threadIdx.x;
     const NgWeights& W = c_W[g.k - 1];
     const int k = W.k;
     const bool full = (n <= 2 * k);
     const int m0 = full ? 1 : n - k;
     const int nq = n - m0 + 1;
-    cplx qsrc[NG_MAXQ + 1][D][D], hsrc[NG_MAXQ + 1][D][D];
-    for (int r = 0; r < nq; ++r) {
-        Mat<D> q = mzero<D>(), h = mzero<D>();
-        for (int c = 0; c < nchunk; ++c) {   // chunk order: deterministic
-            const cplx* o = part + (((int64_t)r * g.nb + kb) * nchunk + c) * 2 * D * D;
-            for (int a = 0; a < D; ++a)
-                for (int b = 0; b < D; ++b) {
-                    q.v[a][b] = cadd(q.v[a][b], o[a * D + b]);
-                    h.v[a][b] = cadd(h.v[a][b], o[D * D + a * D + b]);
-                }
-        }
-        for (int a = 0; a < D; ++a)
-            for (int b = 0; b < D; ++b) qsrc[r][a][b] = q.v[a][b], hsrc[r][a][b] = h.v[a][b];
+    __shared__ cplx qsrc[NG_MAXQ + 1][D][D], hsrc[NG_MAXQ + 1][D][D], Mi[NG_MAXQ + 1][D][D];
+    __shared__ cplx Ash[(NG_KMAX * D) * (NG_KMAX * D)], Bsh[(NG_KMAX * D) * D], fsh[NG_KMAX * D];
+    if (lane == 0) st<D>(G.les, tri(n) + 0, kb, les0_of_tv<D>(g, G, n, kb));
+    // the chunk partials of each (row, element), added in chunk order (deterministic)
+    for (int i = lane; i < nq * 2 * D * D; i += 32) {
+        const int r = i / (2 * D * D), x = i % (2 * D * D);
+        cplx v = cr(0.0);
+        for (int c = 0; c < nchunk; ++c) v = cadd(v, part[(((int64_t)r * g.nb + kb) * nchunk + c) * 2 * D * D + x]);
+        if (x < D * D) qsrc[r][x / D][x % D] = v;
+        else hsrc[r][(x - D * D) / D][(x - D * D) % D] = v;
     }
-    int sing = 0;
+    __syncwarp();
     int mstep = m0;
     if (full) {
-        cplx Ash[(NG_KMAX * D) * (NG_KMAX * D)];
-        cplx Bsh[(NG_KMAX * D) * D];
-        les_col_startup<D>(W, g, n, G, S, eps, kb, qsrc, Ash, Bsh, status);
+        les_col_startup_w<D>(W, g, n, G, S, eps, kb, qsrc, Ash, Bsh, fsh, lane, status);
         mstep = k + 1;
     }
-    // serial VIDE steps (Eq. MBCVSAMx_t) in the first argument, m = mstep..n
-    for (int m = mstep; m <= n; ++m) {
-        const int r = m - m0;
-        Mat<D> acc, h0;
-        for (int a = 0; a < D; ++a)
-            for (int b = 0; b < D; ++b) acc.v[a][b] = qsrc[r][a][b], h0.v[a][b] = hsrc[r][a][b];
-        const int lfrom = full ? 0 : m0;
-        for (int l = lfrom; l < m; ++l)
-            mfma<D>(h0, mscal<D>(gw(W, m, l), gret<D>(S, m, l, kb)), ld<D>(G.les, tri(n) + l, kb));
-        Mat<D> bdf = mzero<D>();
-        for (int l = 1; l <= k; ++l) bdf = madd<D>(bdf, mscal<D>(W.a[l], ld<D>(G.les, tri(n) + m - l, kb)));
-        acc = msub<D>(acc, mscal<D>(1.0 / g.h, bdf));
-        acc = msub<D>(acc, mscal<D>(g.h, mmuli<D>(h0)));
-        Mat<D> Mm = step_matrix<D>(W, g, S, eps, m, kb);
-        Mat<D> y = mmul<D>(minv<D>(Mm, &sing), acc);
-        if (!mfinite<D>(y)) atomicOr(status, NGF_NONFINITE);
-        st<D>(G.les, tri(n) + m, kb, y);
-    }
-    if (sing) atomicOr(status, NGF_SINGULAR);
+    les_steps_w<D>(W, g, n, G, S, eps, kb, qsrc, hsrc, Mi, m0, mstep, full ? 0 : m0, lane, status);
 }

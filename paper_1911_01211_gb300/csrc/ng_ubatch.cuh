@@ -55,25 +55,26 @@ __device__ __forceinline__ cplx ules(const HermV& X, int j, int n, int D, int a,
     return cneg(cconj(uel(X.les, tri(j) + n, D, b, a, kb)));
 }
 
-// M_n^-1 of every active problem (thread 0 of one block per problem), D x D Gauss-Jordan
-__global__ void k_uminv(const UProb* probs, UTable tab, int* status) {
-    if (blockIdx.x >= tab.np || threadIdx.x != 0) return;
+// M_n^-1 of every active problem: one warp per problem builds M_n and solves M_n X = 1
+__global__ void __launch_bounds__(32) k_uminv(const UProb* probs, UTable tab, int* status) {
+    if (blockIdx.x >= tab.np) return;
     const UProb& P = probs[tab.prob[blockIdx.x]];
     const NgWeights& W = c_W[P.g.k - 1];
-    const int D = P.g.nf, n = tab.n, kb = P.kb;
-    cplx M[NG_UMAXD * NG_UMAXD], R[NG_UMAXD * NG_UMAXD];
-    for (int a = 0; a < D; ++a)
-        for (int b = 0; b < D; ++b) {
-            cplx e = ufunc(P.eps, n, D, a, b, kb);
-            if (a == b) e.x -= P.g.mu;
-            cplx v = cmuli(e);
-            v = cadd(v, cscal(P.g.h * gw(W, n, n), cmuli(uel(P.S.ret, tri(n) + n, D, a, b, kb))));
-            if (a == b) v.x += W.a[0] / P.g.h;
-            M[a * D + b] = v;
-            R[a * D + b] = cr(a == b ? 1.0 : 0.0);
-        }
-    if (dense_solve(M, D, R, D)) atomicOr(status, NGF_SINGULAR);
-    for (int i = 0; i < D * D; ++i) P.minv[i] = R[i];
+    const int D = P.g.nf, n = tab.n, kb = P.kb, lane = threadIdx.x;
+    __shared__ cplx M[NG_UMAXD * NG_UMAXD], R[NG_UMAXD * NG_UMAXD], f[NG_UMAXD];
+    for (int i = lane; i < D * D; i += 32) {
+        const int a = i / D, b = i % D;
+        cplx e = ufunc(P.eps, n, D, a, b, kb);
+        if (a == b) e.x -= P.g.mu;
+        cplx v = cmuli(e);
+        v = cadd(v, cscal(P.g.h * gw(W, n, n), cmuli(uel(P.S.ret, tri(n) + n, D, a, b, kb))));
+        if (a == b) v.x += W.a[0] / P.g.h;
+        M[i] = v;
+        R[i] = cr(a == b ? 1.0 : 0.0);
+    }
+    __syncwarp();
+    if (warp_dense_solve(M, D, R, D, f, lane) && lane == 0) atomicOr(status, NGF_SINGULAR);
+    for (int i = lane; i < D * D; i += 32) P.minv[i] = R[i];
 }
 
 // ---------------------------------------------------------------------------------------
@@ -287,7 +288,10 @@ __device__ void u_stepmat(const NgWeights& W, const UProb& P, int m, cplx* out) 
 // The boundary of step n runs in three launches: k_uboundary_ret (retarded (A) start-up along
 // row n and G^<(0,n), one block per problem), k_usrc (sources and partial histories of the
 // lesser (A) rows, O((k+1)(n + ntau) nf^3) per problem, over many blocks), k_uboundary_les (the
-// serial lesser (A) steps, one block per problem).
+// serial lesser (A) steps, one block per problem).  The dense solves run on one warp
+// (warp_dense_solve) and the step matrices of the serial rows are inverted by the block's warps
+// before the serial chain, whose steps are then element-parallel products: FP64 is issued per
+// warp instruction on this part, so one thread doing them alone took as long as a whole warp.
 __global__ void __launch_bounds__(NG_UBND_THREADS) k_uboundary_ret(const UProb* probs, UTable tab, int* status) {
     const UProb& P = probs[tab.prob[blockIdx.x]];
     const NgWeights& W = c_W[P.g.k - 1];
@@ -322,7 +326,8 @@ __global__ void __launch_bounds__(NG_UBND_THREADS) k_uboundary_ret(const UProb* 
         B[((j - 1) * D + a) * D + c] = cmuli(v);
     }
     __syncthreads();
-    if (t == 0 && dense_solve(A, N, B, D)) atomicOr(status, NGF_SINGULAR);
+    if (t < 32 && warp_dense_solve(A, N, B, D, B + (NG_KMAX * NG_UMAXD) * NG_UMAXD, t) && t == 0)
+        atomicOr(status, NGF_SINGULAR);
     __syncthreads();
     for (int q = t; q < (k + 1) * DD; q += blockDim.x) {
         const int l = q / DD, ab = q % DD, c = ab / D, a = ab % D;   // y_l[c][a] = B[((l-1)D + a)][c]
@@ -385,8 +390,9 @@ __global__ void __launch_bounds__(NG_UBND_THREADS) k_uboundary_les(const UProb* 
     const NgWeights& W = c_W[P.g.k - 1];
     const Grid& g = P.g;
     const int D = g.nf, DD = D * D, k = W.k, n = tab.n, kb = P.kb, t = threadIdx.x;
-    // dynamic shared memory (NG_UBND_SMEM bytes): A[(kD)^2], B[kD x D], (unused)[threads],
-    // qs/hs[(2k+1) x D^2] (sources and partial histories of the (A) rows)
+    // dynamic shared memory (NG_UBND_SMEM bytes): A[(kD)^2], B[kD x D], red[threads] (pivot
+    // factors, then the step's right-hand side), qs/hs[(2k+1) x D^2] (sources and partial
+    // histories of the (A) rows)
     extern __shared__ unsigned char ub_smem[];
     cplx* A = reinterpret_cast<cplx*>(ub_smem);
     cplx* B = A + (NG_KMAX * NG_UMAXD) * (NG_KMAX * NG_UMAXD);
@@ -411,67 +417,98 @@ __global__ void __launch_bounds__(NG_UBND_THREADS) k_uboundary_les(const UProb* 
         hs[r][ab] = sh;
     }
     __syncthreads();
-    if (t != 0) return;
-    int sing = 0;
     int mstep = m0;
-    cplx M[NG_UMAXD * NG_UMAXD], R[NG_UMAXD * NG_UMAXD], acc[NG_UMAXD * NG_UMAXD];
-    if (full) {   // VIDE start-up for m = 1..k
-        for (int m = 1; m <= k; ++m) {
-            for (int ab2 = 0; ab2 < DD; ++ab2) acc[ab2] = qs[m - 1][ab2];
-            for (int l = 0; l <= k; ++l)
-                for (int aa = 0; aa < D; ++aa)
-                    for (int bb = 0; bb < D; ++bb) {
-                        cplx v = cscal(g.h * W.greg[m][l], cmuli(uretx(P.S, m, l, D, aa, bb, kb)));
-                        if (aa == bb) v.x += W.D[m][l] / g.h;
-                        if (l == m) {
-                            cplx e = ufunc(P.eps, m, D, aa, bb, kb);
-                            if (aa == bb) e.x -= g.mu;
-                            v = cadd(v, cmuli(e));
-                        }
-                        if (l == 0) {   // acc -= M[m][0] y0
-                            for (int cc = 0; cc < D; ++cc)
-                                acc[aa * D + cc] = csub(acc[aa * D + cc], cmul(v, uel(P.G.les, tri(n), D, bb, cc, kb)));
-                        } else {
-                            A[((m - 1) * D + aa) * N + (l - 1) * D + bb] = v;
-                        }
-                    }
-            for (int aa = 0; aa < D; ++aa)
-                for (int cc = 0; cc < D; ++cc) B[((m - 1) * D + aa) * D + cc] = acc[aa * D + cc];
+    if (full) {   // VIDE start-up for m = 1..k: the blocks (m, l) and right-hand sides, then one solve
+        for (int q = t; q < k * k * DD; q += blockDim.x) {
+            const int m = 1 + q / (k * DD), rem = q % (k * DD), l = 1 + rem / DD, ab = rem % DD;
+            const int aa = ab / D, bb = ab % D;
+            cplx v = cscal(g.h * W.greg[m][l], cmuli(uretx(P.S, m, l, D, aa, bb, kb)));
+            if (aa == bb) v.x += W.D[m][l] / g.h;
+            if (l == m) {
+                cplx e = ufunc(P.eps, m, D, aa, bb, kb);
+                if (aa == bb) e.x -= g.mu;
+                v = cadd(v, cmuli(e));
+            }
+            A[((m - 1) * D + aa) * N + (l - 1) * D + bb] = v;
         }
-        if (dense_solve(A, N, B, D)) atomicOr(status, NGF_SINGULAR);
-        for (int m = 1; m <= k; ++m)
-            for (int aa = 0; aa < D; ++aa)
-                for (int cc = 0; cc < D; ++cc) ust(P.G.les, tri(n) + m, D, aa, cc, kb, B[((m - 1) * D + aa) * D + cc]);
+        for (int q = t; q < k * DD; q += blockDim.x) {   // q_m - M[m][0] y0, element (aa, cc)
+            const int m = 1 + q / DD, ab = q % DD, aa = ab / D, cc = ab % D;
+            cplx acc = qs[m - 1][ab];
+            for (int bb = 0; bb < D; ++bb) {
+                cplx v = cscal(g.h * W.greg[m][0], cmuli(uretx(P.S, m, 0, D, aa, bb, kb)));
+                if (aa == bb) v.x += W.D[m][0] / g.h;
+                acc = csub(acc, cmul(v, uel(P.G.les, tri(n), D, bb, cc, kb)));
+            }
+            B[((m - 1) * D + aa) * D + cc] = acc;
+        }
+        __syncthreads();
+        if (t < 32 && warp_dense_solve(A, N, B, D, red, t) && t == 0) atomicOr(status, NGF_SINGULAR);
+        __syncthreads();
+        for (int q = t; q < k * DD; q += blockDim.x) {
+            const int m = 1 + q / DD, ab = q % DD, aa = ab / D, cc = ab % D;
+            ust(P.G.les, tri(n) + m, D, aa, cc, kb, B[((m - 1) * D + aa) * D + cc]);
+        }
         mstep = k + 1;
+        __syncthreads();
     }
-    for (int m = mstep; m <= n; ++m) {   // serial VIDE steps
-        const int r = m - m0;
-        for (int ab2 = 0; ab2 < DD; ++ab2) {
-            acc[ab2] = qs[r][ab2];
-            R[ab2] = hs[r][ab2];
+    // inverse step matrices of the rows m = mstep..n, one warp per row (A is free now):
+    // Mi[r] at A + r D^2, the warps' scratch (M, X, pivot factors) after them
+    cplx* Mi = A;
+    const int warp = t >> 5, lane = t & 31, nwarp = blockDim.x >> 5;
+    cplx* Mw = A + (2 * NG_KMAX + 1) * NG_UMAXD * NG_UMAXD + warp * (2 * NG_UMAXD * NG_UMAXD + NG_UMAXD);
+    cplx* Xw = Mw + NG_UMAXD * NG_UMAXD;
+    cplx* fw = Xw + NG_UMAXD * NG_UMAXD;
+    for (int m = mstep + warp; m <= n; m += nwarp) {
+        for (int i = lane; i < DD; i += 32) {
+            const int aa = i / D, bb = i % D;
+            cplx e = ufunc(P.eps, m, D, aa, bb, kb);
+            if (aa == bb) e.x -= g.mu;
+            cplx v = cadd(cmuli(e), cscal(g.h * gw(W, m, m), cmuli(uel(P.S.ret, tri(m) + m, D, aa, bb, kb))));
+            if (aa == bb) v.x += W.a[0] / g.h;
+            Mw[i] = v;
+            Xw[i] = cr(aa == bb ? 1.0 : 0.0);
         }
-        const int lfrom = full ? 0 : m0;
-        for (int l = lfrom; l < m; ++l)
-            for (int aa = 0; aa < D; ++aa)
-                for (int bb = 0; bb < D; ++bb) {
-                    cplx s = R[aa * D + bb];
-                    for (int cc = 0; cc < D; ++cc)
-                        s = cfma(cscal(gw(W, m, l), uel(P.S.ret, tri(m) + l, D, aa, cc, kb)), uel(P.G.les, tri(n) + l, D, cc, bb, kb), s);
-                    R[aa * D + bb] = s;
-                }
-        for (int aa = 0; aa < D; ++aa)
-            for (int bb = 0; bb < D; ++bb) {
-                cplx bdf = cz();
-                for (int l = 1; l <= k; ++l) bdf = cadd(bdf, cscal(W.a[l], uel(P.G.les, tri(n) + m - l, D, aa, bb, kb)));
-                acc[aa * D + bb] = csub(csub(acc[aa * D + bb], cscal(1.0 / g.h, bdf)), cscal(g.h, cmuli(R[aa * D + bb])));
-            }
-        u_stepmat(W, P, m, M);
-        if (dense_solve(M, D, acc, D)) sing = 1;
-        for (int aa = 0; aa < D; ++aa)
-            for (int bb = 0; bb < D; ++bb) {
-                if (!cfinite(acc[aa * D + bb])) atomicOr(status, NGF_NONFINITE);
-                ust(P.G.les, tri(n) + m, D, aa, bb, kb, acc[aa * D + bb]);
-            }
+        __syncwarp();
+        if (warp_dense_solve(Mw, D, Xw, D, fw, lane) && lane == 0) atomicOr(status, NGF_SINGULAR);
+        for (int i = lane; i < DD; i += 32) Mi[(m - m0) * DD + i] = Xw[i];
+        __syncwarp();
     }
-    if (sing) atomicOr(status, NGF_SINGULAR);
+    __syncthreads();
+    // serial VIDE steps: thread (grp, ab) sums element ab of the history and BDF terms
+    // l = grp, grp + ngr, ...; the group partials (in B) are added in group order
+    const int ngr = blockDim.x / DD, grp = t / DD, ab = t % DD, aa = ab / D, bb = ab % D;
+    cplx* part = B;            // 2 ngr DD <= 2 blockDim.x values
+    cplx* accv = red;          // DD values
+    const int lfrom = full ? 0 : m0;
+    for (int m = mstep; m <= n; ++m) {
+        const int r = m - m0;
+        if (grp < ngr) {
+            cplx hsum = cz(), bdf = cz();
+            for (int l = lfrom + grp; l < m; l += ngr) {
+                const double w = gw(W, m, l);
+                for (int cc = 0; cc < D; ++cc)
+                    hsum = cfma(cscal(w, uel(P.S.ret, tri(m) + l, D, aa, cc, kb)), uel(P.G.les, tri(n) + l, D, cc, bb, kb), hsum);
+            }
+            for (int l = 1 + grp; l <= k; l += ngr) bdf = cadd(bdf, cscal(W.a[l], uel(P.G.les, tri(n) + m - l, D, aa, bb, kb)));
+            part[grp * DD + ab] = hsum;
+            part[(ngr + grp) * DD + ab] = bdf;
+        }
+        __syncthreads();
+        if (t < DD) {
+            cplx hsum = hs[r][t], bdf = cz();
+            for (int q = 0; q < ngr; ++q) {
+                hsum = cadd(hsum, part[q * DD + t]);
+                bdf = cadd(bdf, part[(ngr + q) * DD + t]);
+            }
+            accv[t] = csub(csub(qs[r][t], cscal(1.0 / g.h, bdf)), cscal(g.h, cmuli(hsum)));
+        }
+        __syncthreads();
+        if (t < DD) {
+            cplx y = cz();
+            for (int cc = 0; cc < D; ++cc) y = cfma(Mi[r * DD + aa * D + cc], accv[cc * D + bb], y);
+            if (!cfinite(y)) atomicOr(status, NGF_NONFINITE);
+            ust(P.G.les, tri(n) + m, D, aa, bb, kb, y);
+        }
+        __syncthreads();
+    }
 }
