@@ -46,6 +46,53 @@ __device__ __forceinline__ Mat<D> warp_msum(Mat<D> x) {
     return x;
 }
 
+// Lane sum scattered over the elements: lane l returns the sum over the 32 lanes of element
+// rs_elem<D>(l) = l >> (5 - log2 D^2) of x.  The first log2 D^2 rounds halve what each lane
+// carries (a lane keeps one half and adds its partner's copy of that half), the remaining rounds
+// add the single value left: 2 (D^2 - 1) + 2 (5 - log2 D^2) FP64 additions per lane against
+// 10 D^2 for warp_msum, and the item's closing step then runs one element per lane.
+template <int D>
+struct RsLog { static constexpr int v = (D == 1) ? 0 : (D == 2) ? 2 : (D == 4) ? 4 : -1; };
+template <int D>
+__device__ __forceinline__ int rs_elem(int lane) { return lane >> (5 - RsLog<D>::v); }
+template <int D>
+__device__ __forceinline__ bool rs_leader(int lane) { return (lane & ((32 >> RsLog<D>::v) - 1)) == 0; }
+template <int D>
+__device__ __forceinline__ cplx rs_get(cplx x, int e) { return make_double2(
+    __shfl_sync(0xffffffffu, x.x, e << (5 - RsLog<D>::v)), __shfl_sync(0xffffffffu, x.y, e << (5 - RsLog<D>::v))); }
+
+template <int D>
+__device__ __forceinline__ cplx warp_rsum(const Mat<D>& x, int lane) {
+    constexpr int E = D * D, LG = RsLog<D>::v;
+    static_assert(LG >= 0, "D = 1, 2 or 4");
+    cplx v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = x.v[e / D][e % D];
+#pragma unroll
+    for (int r = 0; r < LG; ++r) {
+        const int off = 16 >> r, h = E >> (r + 1);
+        const bool up = (lane & off) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const cplx keep = up ? v[i + h] : v[i];
+            const cplx give = up ? v[i] : v[i + h];
+            v[i] = make_double2(keep.x + __shfl_xor_sync(0xffffffffu, give.x, off),
+                                keep.y + __shfl_xor_sync(0xffffffffu, give.y, off));
+        }
+    }
+#pragma unroll
+    for (int off = 16 >> LG; off > 0; off >>= 1) {
+        v[0].x += __shfl_xor_sync(0xffffffffu, v[0].x, off);
+        v[0].y += __shfl_xor_sync(0xffffffffu, v[0].y, off);
+    }
+    return v[0];
+}
+
+// element (a, b) of a stored block
+__device__ __forceinline__ cplx elw(const Comp& c, int64_t e, int a, int b, int D, int kb) {
+    return c.p[(e * (D * D) + a * D + b) * c.ldk + (c.ldk == 1 ? 0 : kb)];
+}
+
 template <int D>
 __device__ __forceinline__ void ret_item_w(const NgWeights& W, const Grid& g, const HermV& G, const HermV& S,
                                            const cplx* minv_ws, int n, int m, int kb, int lane, int* status) {
@@ -54,20 +101,25 @@ __device__ __forceinline__ void ret_item_w(const NgWeights& W, const Grid& g, co
     greg_for_lanes(W, L, L - 1, lane, [&](int l, double w) {
         mfma<D>(acc, mscal<D>(w, gret<D>(S, n, m + l, kb)), gret<D>(G, m + l, m, kb));
     });
-    acc = warp_msum<D>(acc);
-    if (lane != 0) return;
-    Mat<D> bdf = mzero<D>();
-    for (int l = 1; l <= W.k; ++l) bdf = madd<D>(bdf, mscal<D>(W.a[l], gret<D>(G, n - l, m, kb)));
-    Mat<D> rhs = msub<D>(mscal<D>(-1.0 / g.h, bdf), mscal<D>(g.h, mmuli<D>(acc)));
-    Mat<D> y = mmul<D>(ld_minv<D>(minv_ws, kb), rhs);
-    if (!mfinite<D>(y)) atomicOr(status, NGF_NONFINITE);
-    st<D>(G.ret, tri(n) + m, kb, y);
+    // closing step, one element (a, b) per lane: rhs = -(1/h) bdf - h i acc, y = M_n^-1 rhs
+    const cplx ae = warp_rsum<D>(acc, lane);
+    const int e = rs_elem<D>(lane), a = e / D, b = e % D;
+    cplx bdf = cz();
+    for (int l = 1; l <= W.k; ++l) bdf = cadd(bdf, cscal(W.a[l], elw(G.ret, tri(n - l) + m, a, b, D, kb)));
+    const cplx rhs = csub(cscal(-1.0 / g.h, bdf), cscal(g.h, cmuli(ae)));
+    cplx y = cz();
+#pragma unroll
+    for (int c = 0; c < D; ++c) y = cfma(minv_ws[((int64_t)kb * D + a) * D + c], rs_get<D>(rhs, c * D + b), y);
+    if (rs_leader<D>(lane)) {
+        if (!cfinite(y)) atomicOr(status, NGF_NONFINITE);
+        G.ret.p[((tri(n) + m) * (D * D) + a * D + b) * G.ret.ldk + (G.ret.ldk == 1 ? 0 : kb)] = y;
+    }
 }
 
 // The left-mixing source -i (C^tv_2 + C^tv_3)[S, 1, G^M](n, tau_m) (Eqs. ctv2, ctv3) as q_tv
-// computes it, over this lane's terms of its two Gregory sums; the boundary (R) formulas of
-// m <= k and m >= ntau - k ((k+1)^2 terms each) go to lane 0.  The
-// source is linear in the terms, so the parts add up to q_tv.
+// computes it, over this lane's terms of its two Gregory sums and of the boundary (R) formulas
+// of m <= k and m >= ntau - k ((k+1)^2 terms each).  The source is linear in the terms, so the
+// lanes' parts add up to q_tv.
 template <int D>
 __device__ Mat<D> q_tv_part(const NgWeights& W, const Grid& g, const HermV& G, const HermV& S, int n, int m, int kb,
                             int lane) {
@@ -76,11 +128,10 @@ __device__ Mat<D> q_tv_part(const NgWeights& W, const Grid& g, const HermV& G, c
     const double xi = (double)g.sig;
     Mat<D> c2 = mzero<D>(), c3 = mzero<D>();
     if (m <= k) {
-        if (l0 == 0)
-            for (int j = 0; j <= k; ++j) {
-                Mat<D> gm = mscal<D>(xi, gmat<D>(G, T - j, kb));
-                for (int l = 0; l <= k; ++l) mfma<D>(c2, mscal<D>(W.R[m][j][l], gtv<D>(S, g, n, l, kb)), gm);
-            }
+        for (int p = l0; p < (k + 1) * (k + 1); p += 32) {
+            const int j = p / (k + 1), l = p % (k + 1);
+            mfma<D>(c2, mscal<D>(W.R[m][j][l], gtv<D>(S, g, n, l, kb)), mscal<D>(xi, gmat<D>(G, T - j, kb)));
+        }
     } else {
         greg_for_lanes(W, m, m, lane, [&](int l, double w) {
             mfma<D>(c2, mscal<D>(w, gtv<D>(S, g, n, m - l, kb)), gmat<D>(G, T - l, kb));
@@ -88,11 +139,10 @@ __device__ Mat<D> q_tv_part(const NgWeights& W, const Grid& g, const HermV& G, c
         c2 = mscal<D>(xi, c2);
     }
     if (m >= T - k) {
-        if (l0 == 0)
-            for (int j = 0; j <= k; ++j) {
-                Mat<D> gm = gmat<D>(G, j, kb);
-                for (int l = 0; l <= k; ++l) mfma<D>(c3, mscal<D>(W.R[T - m][j][l], gtv<D>(S, g, n, T - l, kb)), gm);
-            }
+        for (int p = l0; p < (k + 1) * (k + 1); p += 32) {
+            const int j = p / (k + 1), l = p % (k + 1);
+            mfma<D>(c3, mscal<D>(W.R[T - m][j][l], gtv<D>(S, g, n, T - l, kb)), gmat<D>(G, j, kb));
+        }
     } else {
         greg_for_lanes(W, T - m, T - m, lane, [&](int l, double w) {
             mfma<D>(c3, mscal<D>(w, gtv<D>(S, g, n, m + l, kb)), gmat<D>(G, l, kb));
@@ -109,17 +159,22 @@ __device__ __forceinline__ void tv_item_w(const NgWeights& W, const Grid& g, con
     greg_for_lanes(W, n, n - 1, lane, [&](int j, double w) {
         mfma<D>(acc, mscal<D>(w, gret<D>(S, n, j, kb)), gtv<D>(G, g, j, m, kb));
     });
-    acc = warp_msum<D>(acc);
-    const Mat<D> src = warp_msum<D>(q_tv_part<D>(W, g, G, S, n, m, kb, lane));
-    if (lane != 0) return;
-    Mat<D> bdf = mzero<D>();
-    for (int l = 1; l <= W.k; ++l) bdf = madd<D>(bdf, mscal<D>(W.a[l], gtv<D>(G, g, n - l, m, kb)));
-    Mat<D> rhs = src;
-    rhs = msub<D>(rhs, mscal<D>(1.0 / g.h, bdf));
-    rhs = msub<D>(rhs, mscal<D>(g.h, mmuli<D>(acc)));
-    Mat<D> y = mmul<D>(ld_minv<D>(minv_ws, kb), rhs);
-    if (!mfinite<D>(y)) atomicOr(status, NGF_NONFINITE);
-    st<D>(G.tv, (int64_t)n * (g.ntau + 1) + m, kb, y);
+    // closing step, one element (a, b) per lane: rhs = src - bdf / h - h i acc, y = M_n^-1 rhs
+    const cplx ae = warp_rsum<D>(acc, lane);
+    const cplx se = warp_rsum<D>(q_tv_part<D>(W, g, G, S, n, m, kb, lane), lane);
+    const int e = rs_elem<D>(lane), a = e / D, b = e % D;
+    cplx bdf = cz();
+    for (int l = 1; l <= W.k; ++l)
+        bdf = cadd(bdf, cscal(W.a[l], elw(G.tv, (int64_t)(n - l) * (g.ntau + 1) + m, a, b, D, kb)));
+    cplx rhs = csub(se, cscal(1.0 / g.h, bdf));
+    rhs = csub(rhs, cscal(g.h, cmuli(ae)));
+    cplx y = cz();
+#pragma unroll
+    for (int c = 0; c < D; ++c) y = cfma(minv_ws[((int64_t)kb * D + a) * D + c], rs_get<D>(rhs, c * D + b), y);
+    if (rs_leader<D>(lane)) {
+        if (!cfinite(y)) atomicOr(status, NGF_NONFINITE);
+        G.tv.p[(((int64_t)n * (g.ntau + 1) + m) * (D * D) + a * D + b) * G.tv.ldk + (G.tv.ldk == 1 ? 0 : kb)] = y;
+    }
 }
 
 template <int D>
@@ -147,18 +202,22 @@ __device__ __forceinline__ void les_item_w(const NgWeights& W, const Grid& g, co
         Mat<D> gl = (l >= m) ? ld<D>(G.les, tri(l) + m, kb) : mscal<D>(-1.0, mdag<D>(ld<D>(G.les, tri(m) + l, kb)));
         mfma_db<D>(hist, mscal<D>(w, gl), gret<D>(S, n, l, kb));
     });
-    c1 = warp_msum<D>(c1);
-    c3 = warp_msum<D>(c3);
-    hist = warp_msum<D>(hist);
-    if (lane != 0) return;
-    Mat<D> q = msub<D>(mscal<D>(g.h, mmuli<D>(c1)), mscal<D>((double)g.sig * g.htau, c3));
-    Mat<D> bdf = mzero<D>();
-    for (int l = 1; l <= k; ++l) bdf = madd<D>(bdf, mscal<D>(W.a[l], ld<D>(G.les, tri(n - l) + m, kb)));
-    Mat<D> rhs = msub<D>(q, mscal<D>(1.0 / g.h, bdf));
-    rhs = madd<D>(rhs, mscal<D>(g.h, mmuli<D>(hist)));
-    Mat<D> y = mmul<D>(rhs, mdag<D>(ld_minv<D>(minv_ws, kb)));
-    if (!mfinite<D>(y)) atomicOr(status, NGF_NONFINITE);
-    st<D>(G.les, tri(n) + m, kb, y);
+    // closing step, one element (a, b) per lane: rhs = h i c1 - xi htau c3 - bdf / h + h i hist,
+    // y = rhs [M_n^-1]^dagger
+    const cplx c1e = warp_rsum<D>(c1, lane), c3e = warp_rsum<D>(c3, lane), he = warp_rsum<D>(hist, lane);
+    const int e = rs_elem<D>(lane), a = e / D, b = e % D;
+    const cplx q = csub(cscal(g.h, cmuli(c1e)), cscal((double)g.sig * g.htau, c3e));
+    cplx bdf = cz();
+    for (int l = 1; l <= k; ++l) bdf = cadd(bdf, cscal(W.a[l], elw(G.les, tri(n - l) + m, a, b, D, kb)));
+    cplx rhs = csub(q, cscal(1.0 / g.h, bdf));
+    rhs = cadd(rhs, cscal(g.h, cmuli(he)));
+    cplx y = cz();
+#pragma unroll
+    for (int c = 0; c < D; ++c) y = cfma(rs_get<D>(rhs, a * D + c), cconj(minv_ws[((int64_t)kb * D + b) * D + c]), y);
+    if (rs_leader<D>(lane)) {
+        if (!cfinite(y)) atomicOr(status, NGF_NONFINITE);
+        G.les.p[((tri(n) + m) * (D * D) + a * D + b) * G.les.ldk + (G.les.ldk == 1 ? 0 : kb)] = y;
+    }
 }
 
 // ---- the boundary of a time step for small batches, in three launches -----------------------

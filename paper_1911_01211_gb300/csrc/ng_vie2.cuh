@@ -173,11 +173,50 @@ __device__ __forceinline__ Mat<D> v2_les_solve(const NgWeights& W, const Grid& g
     return mmul<D>(rhs, mdag<D>(Mi));   // [M^dagger]^-1 = [M^-1]^dagger
 }
 
-// ---- the same items with one warp each (small batches): lane partials of every sum added
-// by the fixed butterfly of warp_msum, lane 0 finishes the item ------------------------------
+// ---- the same items with one warp each (small batches): the lane partials of every sum are
+// added by warp_rsum, which leaves element rs_elem(lane) of each sum on the lanes, and the item's
+// closing solve runs one element per lane --------------------------------------------------------
+
+// row i of [1 + c F^R(n,n)]^-1 on every lane of the warp (all lanes call it): by the adjugate for
+// D <= 2; for D = 4 the warp solves M X = 1 in its scratch sh (2 D^2 + D values)
+template <int D>
+__device__ __forceinline__ void v2_inv_row(double c, const HermV& F, int n, int kb, int i, cplx (&row)[D], cplx* sh,
+                                           int lane, int* status) {
+    const int64_t e = tri(n) + n;
+    auto mel = [&](int r, int q) {
+        cplx x = cscal(c, elw(F.ret, e, r, q, D, kb));
+        if (r == q) x.x += 1.0;
+        return x;
+    };
+    if constexpr (D == 1) {
+        const cplx m = mel(0, 0);
+        if (cabs2(m) == 0.0 && lane == 0) atomicOr(status, NGF_SINGULAR);
+        row[0] = cdiv(cr(1.0), m);
+    } else if constexpr (D == 2) {
+        const cplx p = mel(0, 0), q = mel(0, 1), r = mel(1, 0), t = mel(1, 1);
+        const cplx det = csub(cmul(p, t), cmul(q, r));
+        if (cabs2(det) == 0.0 && lane == 0) atomicOr(status, NGF_SINGULAR);
+        const cplx idet = cdiv(cr(1.0), det);
+        row[0] = cmul(i == 0 ? t : cneg(r), idet);
+        row[1] = cmul(i == 0 ? cneg(q) : p, idet);
+    } else {
+        cplx* M = sh;
+        cplx* X = sh + D * D;
+        for (int x = lane; x < D * D; x += 32) {
+            M[x] = mel(x / D, x % D);
+            X[x] = cr(x / D == x % D ? 1.0 : 0.0);
+        }
+        __syncwarp();
+        if (warp_dense_solve(M, D, X, D, sh + 2 * D * D, lane) && lane == 0) atomicOr(status, NGF_SINGULAR);
+#pragma unroll
+        for (int q = 0; q < D; ++q) row[q] = X[i * D + q];
+        __syncwarp();
+    }
+}
+
 template <int D>
 __device__ __forceinline__ void v2_ret_item_w(const NgWeights& W, const Grid& g, const HermV& G, const HermV& F,
-                                              const HermV& Q, int n, int m, int kb, int lane, int* status) {
+                                              const HermV& Q, int n, int m, int kb, int lane, cplx* sh, int* status) {
     const int k = W.k, L = n - m;
     Mat<D> acc = mzero<D>();
     double wd;
@@ -191,35 +230,67 @@ __device__ __forceinline__ void v2_ret_item_w(const NgWeights& W, const Grid& g,
             mfma<D>(acc, mscal<D>(W.greg[L][j], ld<D>(F.ret, tri(n) + n - j, kb)), gretx<D>(G, n - j, m, kb));
         wd = W.greg[L][0];
     }
-    acc = warp_msum<D>(acc);
-    if (lane != 0) return;
-    int sing = 0;
-    const Mat<D> Mi = minv<D>(v2_one_plus<D>(g.h * wd, ld<D>(F.ret, tri(n) + n, kb)), &sing);
-    const Mat<D> y = mmul<D>(Mi, msub<D>(ld<D>(Q.ret, tri(n) + m, kb), mscal<D>(g.h, acc)));
-    if (sing) atomicOr(status, NGF_SINGULAR);
-    if (!mfinite<D>(y)) atomicOr(status, NGF_NONFINITE);
-    st<D>(G.ret, tri(n) + m, kb, y);
+    // y = [1 + h wd F^R(n,n)]^-1 (Q^R(n,m) - h acc), element (a, b) per lane
+    const cplx ae = warp_rsum<D>(acc, lane);
+    const int e = rs_elem<D>(lane), a = e / D, b = e % D;
+    const cplx rhs = csub(elw(Q.ret, tri(n) + m, a, b, D, kb), cscal(g.h, ae));
+    cplx mi[D];
+    v2_inv_row<D>(g.h * wd, F, n, kb, a, mi, sh, lane, status);
+    cplx y = cz();
+#pragma unroll
+    for (int c = 0; c < D; ++c) y = cfma(mi[c], rs_get<D>(rhs, c * D + b), y);
+    if (rs_leader<D>(lane)) {
+        if (!cfinite(y)) atomicOr(status, NGF_NONFINITE);
+        G.ret.p[((tri(n) + m) * (D * D) + a * D + b) * G.ret.ldk + (G.ret.ldk == 1 ? 0 : kb)] = y;
+    }
 }
 
 // the left-mixing item; its source (C^tv_2 + C^tv_3)[F, 1, G^M] = i q_tv with S := F is split over
 // the lanes (no FFT pre-pass in this form)
 template <int D>
 __device__ __forceinline__ void v2_tv_item_w(const NgWeights& W, const Grid& g, const HermV& G, const HermV& F,
-                                             const HermV& Q, int n, int m, int kb, int lane, int* status) {
+                                             const HermV& Q, int n, int m, int kb, int lane, cplx* sh, int* status) {
     Mat<D> acc = mzero<D>();
     greg_for_lanes(W, n, n - 1, lane, [&](int j, double w) {
         mfma<D>(acc, mscal<D>(w, ld<D>(F.ret, tri(n) + j, kb)), gtv<D>(G, g, j, m, kb));
     });
-    acc = warp_msum<D>(acc);
-    const Mat<D> src = warp_msum<D>(q_tv_part<D>(W, g, G, F, n, m, kb, lane));
-    if (lane != 0) return;
-    Mat<D> rhs = msub<D>(gtv<D>(Q, g, n, m, kb), mmuli<D>(src));
-    rhs = msub<D>(rhs, mscal<D>(g.h, acc));
-    int sing = 0;
-    const Mat<D> y = mmul<D>(minv<D>(v2_one_plus<D>(g.h * gw(W, n, n), ld<D>(F.ret, tri(n) + n, kb)), &sing), rhs);
-    if (sing) atomicOr(status, NGF_SINGULAR);
-    if (!mfinite<D>(y)) atomicOr(status, NGF_NONFINITE);
-    st<D>(G.tv, (int64_t)n * (g.ntau + 1) + m, kb, y);
+    // y = [1 + h w_{n,n} F^R(n,n)]^-1 (Q^tv(n,m) - i src - h acc), element (a, b) per lane
+    const cplx ae = warp_rsum<D>(acc, lane);
+    const cplx se = warp_rsum<D>(q_tv_part<D>(W, g, G, F, n, m, kb, lane), lane);
+    const int e = rs_elem<D>(lane), a = e / D, b = e % D;
+    cplx rhs = csub(elw(Q.tv, (int64_t)n * (g.ntau + 1) + m, a, b, D, kb), cmuli(se));
+    rhs = csub(rhs, cscal(g.h, ae));
+    cplx mi[D];
+    v2_inv_row<D>(g.h * gw(W, n, n), F, n, kb, a, mi, sh, lane, status);
+    cplx y = cz();
+#pragma unroll
+    for (int c = 0; c < D; ++c) y = cfma(mi[c], rs_get<D>(rhs, c * D + b), y);
+    if (rs_leader<D>(lane)) {
+        if (!cfinite(y)) atomicOr(status, NGF_NONFINITE);
+        G.tv.p[(((int64_t)n * (g.ntau + 1) + m) * (D * D) + a * D + b) * G.tv.ldk + (G.tv.ldk == 1 ? 0 : kb)] = y;
+    }
+}
+
+// the conjugate lesser item: y = [Q^<(m,n) - h (c1 + hist) - i xi h_tau c3] [1 + h w_{n,n} F^R(n,n)]^-dagger
+template <int D>
+__device__ __forceinline__ void v2_les_item_w(const NgWeights& W, const Grid& g, const HermV& G, const HermV& F,
+                                              const HermV& Fcc, const HermV& Q, int n, int m, int kb, int lane,
+                                              cplx* sh, int* status) {
+    Mat<D> c1 = mzero<D>(), c3 = mzero<D>(), hist = mzero<D>();
+    v2_les_parts_strided<D>(W, g, G, F, Fcc, n, m, kb, lane, 32, c1, c3, hist);
+    const cplx c1e = warp_rsum<D>(c1, lane), c3e = warp_rsum<D>(c3, lane), he = warp_rsum<D>(hist, lane);
+    const int e = rs_elem<D>(lane), a = e / D, b = e % D;
+    cplx rhs = csub(elw(Q.les, tri(n) + m, a, b, D, kb), cscal(g.h, cadd(c1e, he)));
+    rhs = csub(rhs, cmul(make_double2(0.0, (double)g.sig * g.htau), c3e));
+    cplx mi[D];   // row b of M^-1: y_ab = sum_c rhs_ac conj(M^-1_bc)
+    v2_inv_row<D>(g.h * gw(W, n, n), F, n, kb, b, mi, sh, lane, status);
+    cplx y = cz();
+#pragma unroll
+    for (int c = 0; c < D; ++c) y = cfma(rs_get<D>(rhs, a * D + c), cconj(mi[c]), y);
+    if (rs_leader<D>(lane)) {
+        if (!cfinite(y)) atomicOr(status, NGF_NONFINITE);
+        G.les.p[((tri(n) + m) * (D * D) + a * D + b) * G.les.ldk + (G.les.ldk == 1 ? 0 : kb)] = y;
+    }
 }
 
 template <int D>
@@ -227,30 +298,19 @@ __global__ void __launch_bounds__(128, 1)
     k_v2_bulk_w(Grid g, int n, HermV G, HermV F, HermV Fcc, HermV Q, int64_t w_les, int64_t w_tv, int64_t w_ret,
                 int* status) {
     const NgWeights& W = c_W[g.k - 1];
+    __shared__ cplx sh[4][D <= 2 ? 1 : 2 * D * D + D];   // blockDim.x = 128: four warps
     int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
+    cplx* ws = sh[threadIdx.x >> 5];
     int task;
     if (item < w_les) task = 0;
     else if ((item -= w_les) < w_tv) task = 1;
     else if ((item -= w_tv) < w_ret) task = 2;
     else return;
     const int kb = (int)(item % g.nb), col = (int)(item / g.nb);
-    if (task == 1) {
-        v2_tv_item_w<D>(W, g, G, F, Q, n, col, kb, lane, status);
-    } else if (task == 2) {
-        v2_ret_item_w<D>(W, g, G, F, Q, n, col, kb, lane, status);
-    } else {
-        const int m = col + 1;
-        Mat<D> c1 = mzero<D>(), c3 = mzero<D>(), hist = mzero<D>();
-        v2_les_parts_strided<D>(W, g, G, F, Fcc, n, m, kb, lane, 32, c1, c3, hist);
-        c1 = warp_msum<D>(c1);
-        c3 = warp_msum<D>(c3);
-        hist = warp_msum<D>(hist);
-        if (lane != 0) return;
-        const Mat<D> y = v2_les_solve<D>(W, g, F, Q, n, m, kb, c1, c3, hist, status);
-        if (!mfinite<D>(y)) atomicOr(status, NGF_NONFINITE);
-        st<D>(G.les, tri(n) + m, kb, y);
-    }
+    if (task == 1) v2_tv_item_w<D>(W, g, G, F, Q, n, col, kb, lane, ws, status);
+    else if (task == 2) v2_ret_item_w<D>(W, g, G, F, Q, n, col, kb, lane, ws, status);
+    else v2_les_item_w<D>(W, g, G, F, Fcc, Q, n, col + 1, kb, lane, ws, status);
 }
 
 // Time step n: one launch over the retarded items (m = 0..n-1), the left-mixing items
