@@ -505,19 +505,33 @@ __device__ void les_col_startup_w(const NgWeights& W, const Grid& g, int n, cons
     __syncwarp();
 }
 
+// scratch of les_steps_w: the weighted Sigma^R(m, l) of the chain's rows (at most k+1 rows of at
+// most 2k terms) and the column values G^<(l, n) it reads (at most 2k+1)
+#define NG_LS_ROWS (NG_KMAX + 1)
+#define NG_LS_TERMS (2 * NG_KMAX)
+#define NG_LS_COL (2 * NG_KMAX + 1)
+template <int D>
+__host__ __device__ constexpr int les_steps_scratch() { return (NG_LS_ROWS * NG_LS_TERMS + NG_LS_COL) * D * D; }
+
 // Serial VIDE steps (Eq. MBCVSAMx_t) of column n in the first argument, rows m = mstep..n, with
 // the sources qsrc[m - m0] and the partial histories hsrc[m - m0] over l < lfrom.  One warp: the
-// inverse step matrices of all rows first, one lane per row (they do not depend on the column);
-// then per row, lane (grp, a, b) sums element (a, b) of the history and BDF terms l = grp,
-// grp + 32/D^2, ..., the groups are added by a butterfly, and the lanes of group 0 store the
-// elements of G^<(m, n).  Mi: the warp's scratch of NG_MAXQ + 1 blocks.
+// inverse step matrices of all rows first, one lane per row (they do not depend on the column),
+// and every value the chain reads from memory (w_{m,l} Sigma^R(m,l), the column below mstep) is
+// staged in shared memory at once, so that the serial part waits on no global load; then per row,
+// lane (grp, a, b) sums element (a, b) of the history and BDF terms l = grp, grp + 32/D^2, ...,
+// the groups are added by a butterfly, and the lanes of group 0 store the elements of G^<(m, n).
+// Mi: NG_MAXQ + 1 blocks; scr: les_steps_scratch<D>() values.
 template <int D>
 __device__ void les_steps_w(const NgWeights& W, const Grid& g, int n, const HermV& G, const HermV& S,
                             const FuncV& eps, int kb, const cplx (*qsrc)[D][D], const cplx (*hsrc)[D][D],
-                            cplx (*Mi)[D][D], int m0, int mstep, int lfrom, int lane, int* status) {
+                            cplx (*Mi)[D][D], cplx* scr, int m0, int mstep, int lfrom, int lane, int* status) {
     static_assert(D * D <= 32, "one warp holds the elements of a block");
     const unsigned full = 0xffffffffu;
+    constexpr int E = D * D, NGR = 32 / E;
     const int k = W.k;
+    const int lo = min(lfrom, mstep - k);   // lowest column row the chain reads
+    cplx* wS = scr;                                  // [row m - mstep][l - lfrom][E]
+    cplx* col = scr + NG_LS_ROWS * NG_LS_TERMS * E;  // [l - lo][E]
     int sing = 0;
     for (int m = mstep + lane; m <= n; m += 32) {
         const Mat<D> mi = minv<D>(step_matrix<D>(W, g, S, eps, m, kb), &sing);
@@ -525,23 +539,27 @@ __device__ void les_steps_w(const NgWeights& W, const Grid& g, int n, const Herm
             for (int b = 0; b < D; ++b) Mi[m - m0][a][b] = mi.v[a][b];
     }
     if (__any_sync(full, sing) && lane == 0) atomicOr(status, NGF_SINGULAR);
+    for (int i = lane; i < (n - mstep + 1) * NG_LS_TERMS * E; i += 32) {
+        const int r = i / (NG_LS_TERMS * E), rem = i % (NG_LS_TERMS * E), l = lfrom + rem / E, e = rem % E;
+        const int m = mstep + r;
+        if (l < m) wS[i] = cscal(gw(W, m, l), cel(S.ret, tri(m) + l, e / D, e % D, D, kb));
+    }
+    for (int i = lane; i < (mstep - lo) * E; i += 32)
+        col[i] = cel(G.les, tri(n) + lo + i / E, (i % E) / D, (i % E) % D, D, kb);
     __syncwarp();
-    constexpr int E = D * D, NGR = 32 / E;
     const int grp = lane / E, e = lane % E, a = e / D, b = e % D;
     const double hinv = 1.0 / g.h;
     for (int m = mstep; m <= n; ++m) {
         const int r = m - m0;
+        const cplx* wrow = wS + (m - mstep) * NG_LS_TERMS * E;
         cplx hs = cr(0.0), bd = cr(0.0);
         for (int l = lfrom + grp; l < m; l += NGR) {
-            const double w = gw(W, m, l);
 #pragma unroll
-            for (int c = 0; c < D; ++c) {
-                const cplx sx = cel(S.ret, tri(m) + l, a, c, D, kb);
-                hs = cfma(make_double2(w * sx.x, w * sx.y), cel(G.les, tri(n) + l, c, b, D, kb), hs);
-            }
+            for (int c = 0; c < D; ++c)
+                hs = cfma(wrow[(l - lfrom) * E + a * D + c], col[(l - lo) * E + c * D + b], hs);
         }
         for (int l = 1 + grp; l <= k; l += NGR) {
-            const cplx x = cel(G.les, tri(n) + m - l, a, b, D, kb);
+            const cplx x = col[(m - l - lo) * E + e];
             bd = cadd(bd, make_double2(W.a[l] * x.x, W.a[l] * x.y));
         }
 #pragma unroll
@@ -566,6 +584,7 @@ __device__ void les_steps_w(const NgWeights& W, const Grid& g, int n, const Herm
         if (grp == 0) {
             if (!isfinite(y.x) || !isfinite(y.y)) atomicOr(status, NGF_NONFINITE);
             cel(G.les, tri(n) + m, a, b, D, kb) = y;
+            col[(m - lo) * E + e] = y;
         }
         __syncwarp();
     }
@@ -587,6 +606,7 @@ __global__ void __launch_bounds__(NG_BND_THREADS) k_step_boundary(Grid g, int n,
     __shared__ cplx Ash[(NG_KMAX * D) * (NG_KMAX * D)];
     __shared__ cplx Bsh[(NG_KMAX * D) * D];
     __shared__ cplx fsh[NG_KMAX * D];
+    __shared__ cplx lsc[les_steps_scratch<D>()];
 
     // ---- retarded: conjugate start-up along row n (implementation (A)), warp 0 -------
     if (t < 32) {
@@ -622,7 +642,7 @@ __global__ void __launch_bounds__(NG_BND_THREADS) k_step_boundary(Grid g, int n,
         les_col_startup_w<D>(W, g, n, G, S, eps, kb, qsrc, Ash, Bsh, fsh, t, status);
         mstep = k + 1;
     }
-    les_steps_w<D>(W, g, n, G, S, eps, kb, qsrc, hsrc, Mi, m0, mstep, full ? 0 : m0, t, status);
+    les_steps_w<D>(W, g, n, G, S, eps, kb, qsrc, hsrc, Mi, lsc, m0, mstep, full ? 0 : m0, t, status);
 }
 
 // Serial schedule of step n (the paper's dyson_timestep): the retarded row by the conjugate

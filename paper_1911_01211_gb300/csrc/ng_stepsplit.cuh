@@ -324,6 +324,7 @@ __global__ void __launch_bounds__(32) k_bnd_fin(Grid g, int n, HermV G, HermV S,
     const int nq = n - m0 + 1;
     __shared__ cplx qsrc[NG_MAXQ + 1][D][D], hsrc[NG_MAXQ + 1][D][D], Mi[NG_MAXQ + 1][D][D];
     __shared__ cplx Ash[(NG_KMAX * D) * (NG_KMAX * D)], Bsh[(NG_KMAX * D) * D], fsh[NG_KMAX * D];
+    __shared__ cplx lsc[les_steps_scratch<D>()];
     if (lane == 0) st<D>(G.les, tri(n) + 0, kb, les0_of_tv<D>(g, G, n, kb));
     // the chunk partials of each (row, element), added in chunk order (deterministic)
     for (int i = lane; i < nq * 2 * D * D; i += 32) {
@@ -339,5 +340,5 @@ __global__ void __launch_bounds__(32) k_bnd_fin(Grid g, int n, HermV G, HermV S,
         les_col_startup_w<D>(W, g, n, G, S, eps, kb, qsrc, Ash, Bsh, fsh, lane, status);
         mstep = k + 1;
     }
-    les_steps_w<D>(W, g, n, G, S, eps, kb, qsrc, hsrc, Mi, m0, mstep, full ? 0 : m0, lane, status);
+    les_steps_w<D>(W, g, n, G, S, eps, kb, qsrc, hsrc, Mi, lsc, m0, mstep, full ? 0 : m0, lane, status);
 }
