@@ -17,8 +17,9 @@
   K^ddagger on its slices, then solves the susceptibility (vie2_mat in the Matsubara loop,
   vie2_start over slices 0..k in the bootstrapping, vie2_timestep(n) in each corrector pass),
   then forms dW and Sigma.
-  The second-Born dynamics has no closed form: its parity with the CUDA path is pinned
-  only by invariants and by the pinned building blocks (parity partially unpinned).
+  The second-Born and GW dynamics have no closed form; they are pinned by their conservation
+  laws, by their pinned building blocks, and against exact diagonalisation of the Hubbard dimer
+  to the order in U at which the approximations are exact (tests/test_oracle_ed.py).
 """
 import numpy as np
 

@@ -1,0 +1,105 @@
+"""Pins for the oracle's self-consistent dynamics (drivers.run_2b, drivers.run_gw) against exact
+diagonalisation of the Hubbard dimer (tests/ed_hubbard.py).
+
+The second-Born self-energy (Eq. sigma_hubb_2b) with the Hartree term is the exact self-energy
+to second order in U, and so is GW (Eq. SigmaGW: its second-order term is the same bubble).
+With U scaled as s U, the deviation of the self-consistent solution from the exact one is
+therefore O(s^3): it falls by 8 when s halves.  At particle-hole symmetry (mu = 0, nbar = 1/2)
+the odd orders of the exact self-energy vanish and the Hartree shift is zero, so second Born is
+exact through third order there and its deviation falls by 16; GW keeps third-order terms of
+its own, and its deviation falls by 8.  A dropped or mis-signed term of Sigma leaves an O(s^2)
+deviation (ratio 4), a wrong mean-field term an O(s) one (ratio 2): both fail the windows.
+
+Dimer eps = [[0, -1], [-1, 0]], U_{-1} = 0.5 s (the initial equilibrium), U_n = s for n >= 0
+(the quench), beta = 2, ntau = 60, h = 0.05, 30 steps, k = 5, 3 corrector passes.  The
+discretisation floor (the U = 0 run against the exact free evolution) is below 1e-6, two orders
+under the smallest deviation used.
+"""
+import numpy as np
+import pytest
+
+from oracle import bubble, drivers, observables
+from oracle.contour import Func
+from oracle.weights import Weights
+from tests.ed_hubbard import HubbardED
+
+EPS = np.array([[0.0, -1.0], [-1.0, 0.0]])
+BETA, NTAU, NT, H = 2.0, 60, 30, 0.05
+
+
+def _deviation(kind, s, mu=0.0):
+    """max |G^M - G^M_exact| over tau in [0, beta) and max |rho(t) - rho_exact(t)| over the steps."""
+    W = Weights(5)
+    e0 = Func(NT, 2)
+    e0.val[:] = EPS
+    U = Func(NT, 1)
+    U.val[:] = s
+    U.set(-1, np.array([[0.5 * s]]))
+    if kind == "2b":
+        st = drivers.run_2b([e0], U, NT, NTAU, BETA, H, W, mu=mu, corrector=3)
+    else:
+        st, _ = drivers.run_gw([e0], U, NT, NTAU, BETA, H, W, mu=mu, corrector=3)
+    G = st.G[0]
+    ed = HubbardED(EPS, mu=mu, nbar=0.5)
+    taus = np.arange(NTAU) * BETA / NTAU
+    em = np.abs(G.mat[:NTAU] - ed.gmat(0.5 * s, BETA, taus)).max()
+    rho = ed.density(0.5 * s, s, BETA, np.arange(NT + 1) * H)
+    er = max(np.abs(observables.density_matrix(n, G) - rho[n]).max() for n in range(NT + 1))
+    return em, er
+
+
+def test_ed_reference_is_the_free_solution_at_zero_u():
+    """U = 0: the oracle's free dimer equals the exact one (Matsubara exactly, real time to the
+    discretisation)."""
+    em, er = _deviation("2b", 0.0)
+    assert em < 1e-14 and er < 1e-6, (em, er)
+
+
+def test_second_born_exact_through_third_order_at_half_filling():
+    a, b = _deviation("2b", 0.5), _deviation("2b", 0.25)
+    rm, rr = a[0] / b[0], a[1] / b[1]
+    assert 12.0 < rm < 20.0 and 12.0 < rr < 20.0, (a, b, rm, rr)
+    assert b[1] < 5e-5, b
+
+
+def test_second_born_exact_to_second_order_off_half_filling():
+    a, b = _deviation("2b", 0.5, mu=0.3), _deviation("2b", 0.25, mu=0.3)
+    rm = a[0] / b[0]
+    assert 6.0 < rm < 10.5, (a, b, rm)
+    assert b[1] < 5e-5, b
+
+
+def test_gw_exact_to_second_order():
+    a, b = _deviation("gw", 0.5), _deviation("gw", 0.25)
+    rm, rr = a[0] / b[0], a[1] / b[1]
+    assert 6.0 < rm < 10.5 and 6.0 < rr < 10.5, (a, b, rm, rr)
+
+
+def test_pin_detects_a_mis_signed_self_energy(monkeypatch):
+    """Planted on the CPU, in the oracle: Sigma_2B with the wrong overall sign.  The deviation
+    becomes O(U^2), and the half-filling window of the second-Born pin rejects it."""
+    orig = bubble.sigma_2b
+
+    def flipped(n, G, U, S):
+        orig(n, G, U, S)
+        if n == -1:
+            S.mat[...] = -S.mat
+            return
+        S.ret[n, :n + 1] = -S.ret[n, :n + 1]
+        S.les[:n + 1, n] = -S.les[:n + 1, n]
+        S.tv[n] = -S.tv[n]
+
+    monkeypatch.setattr(bubble, "sigma_2b", flipped)
+    a, b = _deviation("2b", 0.5), _deviation("2b", 0.25)
+    rm, rr = a[0] / b[0], a[1] / b[1]
+    assert not (12.0 < rm < 20.0 and 12.0 < rr < 20.0), (rm, rr)
+    assert rm < 6.0, rm
+
+
+def test_pin_detects_a_wrong_mean_field_reference(monkeypatch):
+    """Planted: the mean-field term taken about nbar = 0.4 instead of the Hamiltonian's 0.5, an
+    O(U) error: the deviation falls only by about 2 when U halves."""
+    orig = bubble.hartree
+    monkeypatch.setattr(bubble, "hartree", lambda n, rho, e0, U, nbar: orig(n, rho, e0, U, 0.4))
+    a, b = _deviation("2b", 0.5), _deviation("2b", 0.25)
+    assert a[0] / b[0] < 4.0, (a, b)
