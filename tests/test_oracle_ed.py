@@ -13,7 +13,8 @@ deviation (ratio 4), a wrong mean-field term an O(s) one (ratio 2): both fail th
 Dimer eps = [[0, -1], [-1, 0]], U_{-1} = 0.5 s (the initial equilibrium), U_n = s for n >= 0
 (the quench), beta = 2, ntau = 60, h = 0.05, 30 steps, k = 5, 3 corrector passes.  The
 discretisation floor (the U = 0 run against the exact free evolution) is below 1e-6, two orders
-under the smallest deviation used.
+under the smallest deviation used.  The 4-site ring (hopping -1, periodic; ntau = 40, 20 steps)
+pins the multi-orbital real-space GW and the k-space GW (nk = 4) the same way.
 """
 import numpy as np
 import pytest
@@ -71,6 +72,60 @@ def test_second_born_exact_to_second_order_off_half_filling():
 
 def test_gw_exact_to_second_order():
     a, b = _deviation("gw", 0.5), _deviation("gw", 0.25)
+    rm, rr = a[0] / b[0], a[1] / b[1]
+    assert 6.0 < rm < 10.5 and 6.0 < rr < 10.5, (a, b, rm, rr)
+
+
+# ---- the 4-site ring: the multi-orbital real-space GW (d = 4) and the k-space GW (nk = 4) ----
+RING_NTAU, RING_NT = 40, 20
+
+
+def _ring_eps(M=4):
+    eps = np.zeros((M, M))
+    for i in range(M):
+        eps[i, (i + 1) % M] = eps[(i + 1) % M, i] = -1.0
+    return eps
+
+
+def _ring_deviation(s, kspace):
+    """Deviation of G^M_ij(tau) and rho_ij(t) from the exact ring (256-state Fock space; at
+    half filling rho_ii stays 1/2, the bond densities rho_{i,i+1} carry the dynamics): the
+    real-space run (one problem, d = 4 sites) or the k-space run (nk = 4 one-band problems,
+    eps_k = -2 cos k, Sigma_k by Eqs. Sigmak, Pol), taken to sites by
+    X_ij = (1/N_k) sum_k exp(i k (r_i - r_j)) X_k."""
+    from oracle import gw
+    M, N, T = 4, RING_NT, RING_NTAU
+    W = Weights(5)
+    U = Func(N, 1)
+    U.val[:] = s
+    U.set(-1, np.array([[0.5 * s]]))
+    if kspace:
+        e0 = []
+        for kk in range(M):
+            f = Func(N, 1)
+            f.val[:] = -2.0 * np.cos(2 * np.pi * kk / M)
+            e0.append(f)
+        st, _ = drivers.run_gw_kspace(e0, U, N, T, BETA, H, W, *gw.ring_tables(M), corrector=3)
+        r = np.arange(M)
+        ph = np.exp(2j * np.pi * np.arange(M)[None, None, :] * (r[:, None, None] - r[None, :, None]) / M) / M
+        gm = np.einsum("tk,ijk->tij", np.stack([g.mat[:T, 0, 0] for g in st.G], axis=-1), ph)
+        rho = [np.einsum("k,ijk->ij", np.array([observables.density_matrix(n, g)[0, 0] for g in st.G]), ph)
+               for n in range(N + 1)]
+    else:
+        e0 = Func(N, M)
+        e0.val[:] = _ring_eps(M)
+        st, _ = drivers.run_gw([e0], U, N, T, BETA, H, W, corrector=3)
+        gm = st.G[0].mat[:T]
+        rho = [observables.density_matrix(n, st.G[0]) for n in range(N + 1)]
+    ed = HubbardED(_ring_eps(M), mu=0.0, nbar=0.5)
+    em = np.abs(gm - ed.gmat(0.5 * s, BETA, np.arange(T) * BETA / T)).max()
+    ex = ed.density(0.5 * s, s, BETA, np.arange(N + 1) * H)
+    return em, max(np.abs(rho[n] - ex[n]).max() for n in range(N + 1))
+
+
+@pytest.mark.parametrize("kspace", [False, True], ids=["real_space_d4", "kspace_nk4"])
+def test_ring_gw_exact_to_second_order(kspace):
+    a, b = _ring_deviation(0.5, kspace), _ring_deviation(0.25, kspace)
     rm, rr = a[0] / b[0], a[1] / b[1]
     assert 6.0 < rm < 10.5 and 6.0 < rr < 10.5, (a, b, rm, rr)
 
