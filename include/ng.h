@@ -115,12 +115,14 @@ typedef enum { NG_TVSRC_AUTO = 0, NG_TVSRC_DIRECT = 1 } ng_tv_source;
 /* Parallel decomposition of the FP64 time step (ng_set_bulk_split): NG_BULK_THREAD, one thread
  * per (column, problem) bulk item and one block per problem for the boundary; NG_BULK_WARP,
  * one warp per bulk item, its history and source sums (the left-mixing source by its direct
- * quadrature, no FFT pre-pass) split over the 32 lanes and added in a fixed butterfly order,
- * and the boundary's (A)-row sums spread over (row, problem, chunk)
- * blocks added in chunk order (small batches: a dimer, a real-space cluster); NG_BULK_AUTO
- * (default), each warp/spread form when the batch has fewer than 128 bulk items per SM, resp.
- * fewer than 2 boundary rows per SM.  The forms differ by the order of additions only.
- * nf = 4, 8 always run the element-wise form. */
+ * quadrature, no FFT pre-pass) split over the 32 lanes and added in a fixed butterfly order
+ * that leaves one element of the nf x nf result per lane for the closing solve, the
+ * boundary's (A)-row sums spread over (row, problem, chunk) blocks added in chunk order, and
+ * the boundary's retarded start-up run by extra warps of the bulk launch (small batches: a
+ * dimer, a real-space cluster); NG_BULK_AUTO (default), each warp/spread form when the batch
+ * has fewer than 128 bulk items per SM, resp. fewer than 2 boundary rows per SM.  In every
+ * mode the boundary's dense solves and serial steps run on one warp per problem.  The forms
+ * differ by the order of additions only.  nf = 4, 8 always run the element-wise form. */
 typedef enum { NG_BULK_AUTO = 0, NG_BULK_THREAD = 1, NG_BULK_WARP = 2 } ng_bulk_split;
 
 /* Schedule of a time step (Sec. "Time stepping"): NG_MIXED is the paper's parallel variant
