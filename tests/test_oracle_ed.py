@@ -87,7 +87,7 @@ def _ring_eps(M=4):
     return eps
 
 
-def _ring_deviation(s, kspace):
+def _ring_deviation(s, kspace, kind="gw"):
     """Deviation of G^M_ij(tau) and rho_ij(t) from the exact ring (256-state Fock space; at
     half filling rho_ii stays 1/2, the bond densities rho_{i,i+1} carry the dynamics): the
     real-space run (one problem, d = 4 sites) or the k-space run (nk = 4 one-band problems,
@@ -114,7 +114,10 @@ def _ring_deviation(s, kspace):
     else:
         e0 = Func(N, M)
         e0.val[:] = _ring_eps(M)
-        st, _ = drivers.run_gw([e0], U, N, T, BETA, H, W, corrector=3)
+        if kind == "2b":
+            st = drivers.run_2b([e0], U, N, T, BETA, H, W, corrector=3)
+        else:
+            st, _ = drivers.run_gw([e0], U, N, T, BETA, H, W, corrector=3)
         gm = st.G[0].mat[:T]
         rho = [observables.density_matrix(n, st.G[0]) for n in range(N + 1)]
     ed = HubbardED(_ring_eps(M), mu=0.0, nbar=0.5)
@@ -128,6 +131,15 @@ def test_ring_gw_exact_to_second_order(kspace):
     a, b = _ring_deviation(0.5, kspace), _ring_deviation(0.25, kspace)
     rm, rr = a[0] / b[0], a[1] / b[1]
     assert 6.0 < rm < 10.5 and 6.0 < rr < 10.5, (a, b, rm, rr)
+
+
+def test_ring_second_born_exact_through_third_order():
+    """The multi-orbital second Born (d = 4) of the half-filled ring: O(U^4) deviation.  U is
+    taken twice as large as for GW so that the smaller deviation (2e-5) stays well above the
+    time-stepping floor of this grid (1.4e-6 at U = 0)."""
+    a, b = _ring_deviation(1.0, False, "2b"), _ring_deviation(0.5, False, "2b")
+    rm, rr = a[0] / b[0], a[1] / b[1]
+    assert 12.0 < rm < 20.0 and 12.0 < rr < 20.0, (a, b, rm, rr)
 
 
 def test_pin_detects_a_mis_signed_self_energy(monkeypatch):
