@@ -32,25 +32,12 @@ __device__ __forceinline__ void greg_for_lanes(const NgWeights& W, int L, int lm
     for (int l = k + 1 + ((lane - ne) & 31); l <= e2; l += 32) f(l, 1.0);
 }
 
-template <int D>
-__device__ __forceinline__ Mat<D> warp_msum(Mat<D> x) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1)
-#pragma unroll
-        for (int a = 0; a < D; ++a)
-#pragma unroll
-            for (int b = 0; b < D; ++b) {
-                x.v[a][b].x += __shfl_xor_sync(0xffffffffu, x.v[a][b].x, off);
-                x.v[a][b].y += __shfl_xor_sync(0xffffffffu, x.v[a][b].y, off);
-            }
-    return x;
-}
-
 // Lane sum scattered over the elements: lane l returns the sum over the 32 lanes of element
 // rs_elem<D>(l) = l >> (5 - log2 D^2) of x.  The first log2 D^2 rounds halve what each lane
 // carries (a lane keeps one half and adds its partner's copy of that half), the remaining rounds
 // add the single value left: 2 (D^2 - 1) + 2 (5 - log2 D^2) FP64 additions per lane against
-// 10 D^2 for warp_msum, and the item's closing step then runs one element per lane.
+// 10 D^2 for a butterfly of every element, and the item's closing step then runs one element per
+// lane.
 template <int D>
 struct RsLog { static constexpr int v = (D == 1) ? 0 : (D == 2) ? 2 : (D == 4) ? 4 : -1; };
 template <int D>
