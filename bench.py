@@ -582,6 +582,37 @@ def run_dimer(a):
         if pool is not None and label == "h":
             args = oracle_check_args(ng, g, w.nt, G, S, mf, [0])
             res["max_rel_err_vs_oracle_step_nt"] = pool.map(_oracle_step_check, args)[0]
+        if label == "h":
+            # the same run again on a fresh context, split into setup (Matsubara loop,
+            # bootstrapping) and time steps, the steps with the library's per-launch profile
+            # record (CUDA events on its stream): bulk launch, boundary, flops of the bulk
+            ctx2 = ng.Context(w.korder)
+            G2, L2, S2, mf2 = ng.Herm(g), ng.Herm(g, ldk=1), ng.Herm(g, ldk=1), ng.Func(g)
+            kw = dict(corrector=w.corrector, mats_tol=1e-14, boot_tol=1e-14)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx2.run_2b(g, G2, L2, S2, e0, mf2, U, n_to=w.korder, **kw)
+            torch.cuda.synchronize()
+            t_setup = time.perf_counter() - t0
+            ctx2.profile_enable(True)
+            e2a, e2b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e2a.record()
+            ctx2.run_2b(g, G2, L2, S2, e0, mf2, U, n_from=w.korder + 1, do_setup=False, **kw)
+            e2b.record()
+            torch.cuda.synchronize()
+            prof = ctx2.profile_read()
+            ctx2.profile_enable(False)
+            ms2 = e2a.elapsed_time(e2b)
+            peak = fp64_peak_tflops(clk.get("sm_mhz") or 2070.0)
+            bulk_tf = prof["bulk_flops"] / (prof["bulk_ms"] * 1e-3) / 1e12 if prof["bulk_ms"] > 0 else None
+            res["split"] = {"setup_s": t_setup, "steps_ms_per_step": ms2 / (w.nt - w.korder),
+                            "bulk_share_of_steps": prof["bulk_ms"] / ms2,
+                            "boundary_share_of_steps": prof["boundary_ms"] / ms2, "profile": prof}
+            res["roofline"] = {"bound": "alu", "achieved": bulk_tf, "peak": peak, "unit": "TFLOP/s",
+                               "frac": bulk_tf / peak if bulk_tf else None, "traffic": None,
+                               "kernel": "k_step_bulk_w<2>"}
+            ctx2.close()
+            del G2, L2, S2
         out[label] = res
         ctx.close()
         del G, L, S
@@ -594,6 +625,7 @@ def run_dimer(a):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "hubbard_dimer nf=2 J=1 U 1->2 at t=0 beta=20 ntau=400 nt=1000 h=0.02 k=5 "
                                    "corrector=3 (whole run: Matsubara loop, bootstrapping, time steps)"},
+            "roofline": out["h"].get("roofline"),
             "runs": out,
             "drift_ratio_h_over_h2": out["h"]["E_tot_drift_t_ge_0"] / max(out["h/2"]["E_tot_drift_t_ge_0"], 1e-300)}
     print(json.dumps(line), flush=True)
