@@ -76,6 +76,47 @@ def test_gw_exact_to_second_order():
     assert 6.0 < rm < 10.5 and 6.0 < rr < 10.5, (a, b, rm, rr)
 
 
+def _energy_deviation(kind, s):
+    """max_t |2 E(t) - <H(U_1)>| for t >= 0: E is the oracle's energy per spin, the one-body
+    and mean-field part (1/2) Tr rho (eps + eps^MF) plus the Galitskii-Migdal correlation energy
+    (Eq. Total_ener); the exact energy after the quench is Tr rho_0 H(U_1), constant in time.
+    At half filling the mean-field reference nbar = 1/2 adds nothing to either side."""
+    W = Weights(5)
+    e0 = Func(NT, 2)
+    e0.val[:] = EPS
+    U = Func(NT, 1)
+    U.val[:] = s
+    U.set(-1, np.array([[0.5 * s]]))
+    if kind == "2b":
+        st = drivers.run_2b([e0], U, NT, NTAU, BETA, H, W, corrector=3)
+    else:
+        st, _ = drivers.run_gw([e0], U, NT, NTAU, BETA, H, W, corrector=3)
+    G, S = st.G[0], st.S
+    ed = HubbardED(EPS, mu=0.0, nbar=0.5)
+    _, V0, p0 = ed.thermal(0.5 * s, BETA)
+    e_exact = np.real(np.trace(((V0 * p0) @ V0.conj().T) @ (ed.h0 + s * ed.vint)))
+    dev = 0.0
+    for n in range(NT + 1):
+        rho = observables.density_matrix(n, G)
+        e = 0.5 * np.real(np.trace(rho @ (e0(n) + st.epsmf[0](n)))) + observables.correlation_energy(n, G, S, W, BETA, H)
+        dev = max(dev, abs(2.0 * e - e_exact))
+    return dev
+
+
+@pytest.mark.parametrize("kind,lo,hi", [("2b", 12.0, 20.0), ("gw", 6.0, 10.5)])
+def test_total_energy_exact_to_the_order_of_the_self_energy(kind, lo, hi):
+    a, b = _energy_deviation(kind, 0.5), _energy_deviation(kind, 0.25)
+    assert lo < a / b < hi, (a, b, a / b)
+
+
+def test_pin_detects_a_wrong_correlation_energy(monkeypatch):
+    """Planted: the Galitskii-Migdal term twice too large, an O(U^2) error."""
+    orig = observables.correlation_energy
+    monkeypatch.setattr(observables, "correlation_energy", lambda *a, **k: 2.0 * orig(*a, **k))
+    a, b = _energy_deviation("2b", 0.5), _energy_deviation("2b", 0.25)
+    assert a / b < 6.0, (a, b)
+
+
 # ---- the 4-site ring: the multi-orbital real-space GW (d = 4) and the k-space GW (nk = 4) ----
 RING_NTAU, RING_NT = 40, 20
 
