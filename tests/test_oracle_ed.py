@@ -49,6 +49,21 @@ def _deviation(kind, s, mu=0.0):
     return em, er
 
 
+def test_ed_reference_hubbard_atom():
+    """The reference itself, in the atomic limit (one site, eps = 0, mu = 0): with
+    H = U (n_up - 1/2)(n_dn - 1/2) the states |0>, |up,dn> have energy U/4 and |up>, |dn> -U/4,
+    so G^M(tau) = -[exp(-beta U/4 + tau U/2) + exp(beta U/4 - tau U/2)] / Z,
+    Z = 2 exp(-beta U/4) + 2 exp(beta U/4)."""
+    U, beta = 1.3, 2.0
+    taus = np.linspace(0.0, beta, 9)[:-1]
+    ed = HubbardED(np.zeros((1, 1)), mu=0.0, nbar=0.5)
+    z = 2 * np.exp(-beta * U / 4) + 2 * np.exp(beta * U / 4)
+    exact = -(np.exp(-beta * U / 4 + taus * U / 2) + np.exp(beta * U / 4 - taus * U / 2)) / z
+    assert np.allclose(ed.gmat(U, beta, taus)[:, 0, 0], exact, atol=1e-14, rtol=0)
+    rho = ed.density(U, 2 * U, beta, np.array([0.0, 0.7]))
+    assert np.allclose(rho[:, 0, 0], 0.5, atol=1e-14)
+
+
 def test_ed_reference_is_the_free_solution_at_zero_u():
     """U = 0: the oracle's free dimer equals the exact one (Matsubara exactly, real time to the
     discretisation)."""
