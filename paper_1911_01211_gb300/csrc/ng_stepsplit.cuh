@@ -1,14 +1,16 @@
-// Time-step bulk for small batches: one warp per (column, problem) item.
+// Time step for small batches: one warp per (column, problem) bulk item, and the boundary of
+// the step spread over blocks with its serial parts on one warp per problem.
 //
 // The bulk items of a time step (Sec. "Time stepping": retarded (B) elements, the left-mixing
 // row, lesser (B) elements) each carry O(n + ntau) history and source terms.  With one thread
 // per item a batch of a few problems (a dimer, a real-space cluster) leaves almost every SM
-// idle and each thread sums its terms serially.  Here the 32 lanes of a warp take the terms
-// l = lane, lane + 32, ... of every sum of one item, with the item's Gregory weights; the lane
-// partials are added by a fixed xor butterfly (every lane ends with the same, deterministic
-// sum) and lane 0 finishes the item exactly as the one-thread kernel does: BDF terms, the
-// left-mixing source (FFT correlation with its corrections, or the direct sums), the solve with
-// M_n^-1 and the store.  The arithmetic is that of k_step_bulk up to the order of the additions.
+// idle and each thread sums its terms serially.  Here the 32 lanes of a warp take the terms of
+// every sum of one item (the Gregory end terms one per lane, the unit-weight middle dealt out
+// with no weight multiply; the left-mixing source by its direct quadrature), the lane partials
+// are added by a fixed butterfly that leaves one element of the nf x nf result on each lane
+// (warp_rsum), and the closing step (BDF terms, right-hand side, the product with M_n^-1, the
+// store) runs one element per lane.  The arithmetic is that of k_step_bulk up to the order of
+// the additions.
 #pragma once
 
 #include "ng_step.cuh"
