@@ -651,7 +651,7 @@ __global__ void __launch_bounds__(NG_BND_THREADS) k_step_boundary(Grid g, int n,
 // Eq. dyson_ini_les, start-up for m = 1..k, then single steps m = k+1..n with the sources
 // -i (C^<_2 + C^<_3)[Sigma, 1, G](m, n)).  The left-mixing row comes from the bulk launch
 // before this one.  One block per problem; every step's sums are block reductions in a fixed
-// order, the step itself runs on thread 0.
+// order, the step itself runs on thread 0, the two start-up solves on warp 0.
 template <int D>
 __global__ void __launch_bounds__(NG_BND_THREADS) k_step_serial(Grid g, int n, HermV G, HermV S, FuncV eps,
                                                                 int* status) {

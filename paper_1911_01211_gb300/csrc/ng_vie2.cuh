@@ -1,5 +1,5 @@
 // Dyson equation in integral form, (1 + F) * G = Q (Sec. "vie2: Dyson equation in integral
-// form", Sec. "Implementation: vie2"): start-up and time-step kernels for nf = 1, 2.
+// form", Sec. "Implementation: vie2"): start-up and time-step kernels for nf = 1, 2, 4.
 //
 // The Langreth rules give Volterra integral equations of the second kind (Eqs.
 // vie2_langreth_r/_tv/_les) solved with the rules of Sec. "Volterra Integral equation of the
